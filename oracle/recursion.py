@@ -1,0 +1,117 @@
+"""Weight iteration, flatness and ln Omega in float64 (test infrastructure only).
+
+Energies are held as bins b = E - e_lo of the window [e_lo, e_hi].  Plain
+loops in the order the steps are stated; no vectorised shortcuts where a
+loop reads closer to the definition.
+
+Readings of what the paper leaves open (each also listed in the design notes):
+
+* Unvisited bins (H = 0) keep their log-weight in the simple iteration; the
+  paper states W^{i+1} = W^i / H^i only where H^i > 0 makes sense.
+* The recursive scheme is named (Sec. 2) but not written out.  It is read as
+  the accumulated-statistics recursion on the ratios R(E) = W(E)/W(E_prev)
+  of consecutive energies E_prev < E of the cumulative visited set S_cum:
+  g = H(E_prev) H(E) / (H(E_prev) + H(E)) (0 if either is 0),
+  p(E) <- p(E) + g, kappa = g / p(E),
+  ln R(E) <- ln R(E) + kappa (ln H(E_prev) - ln H(E)).
+  The weights are rebuilt from the top member of S_cum downwards.  Bins
+  outside S_cum keep their log-weight offset to the nearest member above
+  them (below, if there is none above).
+* After every update lnW is shifted so that its maximum over the window is 0.
+* Flatness: min over S_cum of H / max of H, or -1 while either end of the
+  target window has not been visited (the flatness goal min/max >= 0.5).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def normalise(lnW: np.ndarray) -> np.ndarray:
+    """Shift so that max lnW = 0 (acceptance ratios are unchanged)."""
+    out = np.array(lnW, dtype=np.float64, copy=True)
+    return out - out.max()
+
+
+def simple_update(lnW: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """W^{i+1}(E) = W^i(E) / H^i(E) (Sec. 2) in logs, for bins with H > 0."""
+    new = np.array(lnW, dtype=np.float64, copy=True)
+    for b in range(len(new)):
+        if H[b] > 0:
+            new[b] = lnW[b] - math.log(float(H[b]))
+    return normalise(new)
+
+
+def recursive_update(lnW: np.ndarray, H: np.ndarray, s_cum: np.ndarray, phat: np.ndarray):
+    """Accumulated-statistics recursion (reading of the scheme cited in Sec. 2).
+
+    ``s_cum`` (bool) and ``phat`` (float64) are the recursion memory; new
+    copies are returned as (lnW_new, s_cum_new, phat_new).
+    """
+    n = len(lnW)
+    s_cum = np.array(s_cum, dtype=bool, copy=True)
+    phat = np.array(phat, dtype=np.float64, copy=True)
+    for b in range(n):
+        if H[b] > 0:
+            s_cum[b] = True
+    members = [b for b in range(n) if s_cum[b]]
+    new = np.array(lnW, dtype=np.float64, copy=True)
+    if not members:
+        return normalise(new), s_cum, phat
+    top = members[-1]
+    new[top] = lnW[top]
+    for j in range(len(members) - 1, 0, -1):
+        hi = members[j]
+        lo = members[j - 1]
+        ln_r = lnW[hi] - lnW[lo]
+        h_lo = float(H[lo])
+        h_hi = float(H[hi])
+        if h_lo > 0 and h_hi > 0:
+            g = h_lo * h_hi / (h_lo + h_hi)
+        else:
+            g = 0.0
+        phat[hi] = phat[hi] + g
+        if g > 0:
+            kappa = g / phat[hi]
+            ln_r = ln_r + kappa * (math.log(h_lo) - math.log(h_hi))
+        new[lo] = new[hi] - ln_r
+    for b in range(n):
+        if s_cum[b]:
+            continue
+        above = [m for m in members if m > b]
+        ref = above[0] if above else members[-1]
+        new[b] = lnW[b] + (new[ref] - lnW[ref])
+    return normalise(new), s_cum, phat
+
+
+def flatness(H: np.ndarray, s_cum: np.ndarray, t_lo_bin: int | None = None,
+             t_hi_bin: int | None = None) -> float:
+    """min/max of H over S_cum within the target window; -1 if an end is unvisited."""
+    members = [b for b in range(len(H)) if s_cum[b]]
+    if not members:
+        return -1.0
+    lo = members[0] if t_lo_bin is None else t_lo_bin
+    hi = members[-1] if t_hi_bin is None else t_hi_bin
+    if not s_cum[lo] or not s_cum[hi]:
+        return -1.0
+    vals = [float(H[b]) for b in members if lo <= b <= hi]
+    mx = max(vals)
+    if mx <= 0:
+        return 0.0
+    return min(vals) / mx
+
+
+def ln_omega(lnW: np.ndarray, H: np.ndarray, V: int, N: int) -> np.ndarray:
+    """ln Omega(E) = ln H(E) - lnW(E) on bins with H > 0 (W = 1/Omega gives a flat H,
+    Sec. 2), shifted so that sum_E Omega(E) = C(V, N).  NaN where H = 0."""
+    out = np.full(len(H), np.nan)
+    for b in range(len(H)):
+        if H[b] > 0:
+            out[b] = math.log(float(H[b])) - lnW[b]
+    vis = ~np.isnan(out)
+    m = out[vis].max()
+    lse = m + math.log(sum(math.exp(x - m) for x in out[vis]))
+    ln_total = math.lgamma(V + 1) - math.lgamma(N + 1) - math.lgamma(V - N + 1)
+    out[vis] += ln_total - lse
+    return out

@@ -1,0 +1,159 @@
+"""Pins of the oracle's weight iteration, flatness and ln Omega (Sec. 2).
+
+With exact histograms H ~ Omega W (what infinite statistics would give), the
+simple iteration W/H must land on W = 1/Omega in one step, the recursion must
+start as the simple iteration, keep the ideal weights fixed, and move each
+log-ratio the fraction kappa of the way to its ideal value.  The full
+multicanonical run must recover ln Omega of an enumerated lattice.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import chain, muca
+from oracle.recursion import flatness, ln_omega, normalise, recursive_update, simple_update
+
+
+def _exact_hist(om, lnW, e_lo, total=1e7):
+    """H(E) = total * Omega(E) W(E) / Z, float64, zero where Omega = 0."""
+    n = len(lnW)
+    logs = {b: math.log(om[e_lo + b]) + lnW[b] for b in range(n) if (e_lo + b) in om}
+    mx = max(logs.values())
+    z = sum(math.exp(v - mx) for v in logs.values())
+    H = np.zeros(n)
+    for b, v in logs.items():
+        H[b] = total * math.exp(v - mx) / z
+    return H
+
+
+def _ideal(om, e_lo, n):
+    return np.array([-math.log(om[e_lo + b]) if (e_lo + b) in om else np.nan for b in range(n)])
+
+
+def _agree_up_to_constant(a, b, mask, tol):
+    diff = (a - b)[mask]
+    assert np.ptp(diff) < tol
+
+
+OM = chain.enumerate_omega(2, 4, 8)
+E_LO = -16
+NB = 17
+
+
+def test_simple_update_reaches_inverse_omega_in_one_step():
+    rng = np.random.default_rng(0)
+    lnW = rng.normal(size=NB)
+    H = _exact_hist(OM, lnW, E_LO)
+    new = simple_update(lnW, H)
+    mask = H > 0
+    _agree_up_to_constant(new, _ideal(OM, E_LO, NB), mask, 1e-9)
+    assert new.max() == 0.0
+    # unvisited bins keep their weight (relative to the normalisation shift)
+    shift = new[~mask] - lnW[~mask]
+    assert np.ptp(shift) < 1e-12
+
+
+def test_recursion_first_step_equals_simple_on_visited():
+    rng = np.random.default_rng(1)
+    lnW = rng.normal(size=NB)
+    H = np.where(rng.random(NB) < 0.7, rng.integers(1, 1000, NB), 0).astype(np.float64)
+    new_r, s_cum, phat = recursive_update(lnW, H, np.zeros(NB, bool), np.zeros(NB))
+    new_s = simple_update(lnW, H)
+    mask = H > 0
+    _agree_up_to_constant(new_r, new_s, mask, 1e-10)
+    np.testing.assert_array_equal(s_cum, mask)
+
+
+def test_recursion_with_gaps_converges_and_stays_fixed():
+    """4x4, N=8 has impossible energies (-11, -2, -1): pairs skip them."""
+    lnW = np.zeros(NB)
+    s_cum = np.zeros(NB, bool)
+    phat = np.zeros(NB)
+    for _ in range(3):
+        H = _exact_hist(OM, lnW, E_LO)
+        lnW, s_cum, phat = recursive_update(lnW, H, s_cum, phat)
+    ideal = _ideal(OM, E_LO, NB)
+    mask = s_cum.copy()
+    _agree_up_to_constant(lnW, ideal, mask, 1e-9)
+    H = _exact_hist(OM, lnW, E_LO)
+    assert flatness(H, s_cum) > 1 - 1e-9
+
+
+def test_flat_histogram_is_a_fixed_point():
+    rng = np.random.default_rng(2)
+    lnW = normalise(rng.normal(size=NB))
+    H = np.full(NB, 5000.0)
+    for _ in range(3):
+        new, s_cum, phat = recursive_update(lnW, H, np.ones(NB, bool), np.ones(NB))
+        np.testing.assert_allclose(new, lnW, atol=1e-12)
+
+
+def test_recursion_moves_kappa_of_the_way():
+    """Second step with exact data: ln R <- (1 - kappa) ln R + kappa ln R_ideal,
+    kappa = g2 / (g1 + g2), the statistical weight of the new data."""
+    lnW0 = np.zeros(NB)
+    H1 = _exact_hist(OM, lnW0, E_LO, total=1e5)
+    H1 *= np.linspace(0.5, 1.5, NB)           # a noisy first estimate
+    lnW1, s1, p1 = recursive_update(lnW0, H1, np.zeros(NB, bool), np.zeros(NB))
+    H2 = _exact_hist(OM, lnW1, E_LO, total=3e5)
+    lnW2, s2, p2 = recursive_update(lnW1, H2, s1, p1)
+    members = np.nonzero(s2)[0]
+    ideal = _ideal(OM, E_LO, NB)
+    for lo, hi in zip(members[:-1], members[1:]):
+        g1 = H1[lo] * H1[hi] / (H1[lo] + H1[hi])
+        g2 = H2[lo] * H2[hi] / (H2[lo] + H2[hi])
+        kappa = g2 / (g1 + g2)
+        r1 = lnW1[hi] - lnW1[lo]
+        r_ideal = ideal[hi] - ideal[lo]
+        r2 = lnW2[hi] - lnW2[lo]
+        assert r2 == pytest.approx((1 - kappa) * r1 + kappa * r_ideal, abs=1e-9)
+
+
+def test_unvisited_bins_follow_nearest_member_above():
+    lnW = np.arange(NB, dtype=float) * 0.1
+    H = np.zeros(NB)
+    H[5] = 10
+    H[6] = 20
+    new, s_cum, _ = recursive_update(lnW, H, np.zeros(NB, bool), np.zeros(NB))
+    # bins 0..4 move with bin 5, bins 7.. move with bin 6 (the top member)
+    np.testing.assert_allclose(np.diff(new[:6]), np.diff(lnW[:6]), atol=1e-12)
+    np.testing.assert_allclose(np.diff(new[6:]), np.diff(lnW[6:]), atol=1e-12)
+    assert (new[6] - new[5]) == pytest.approx(0.1 + math.log(10) - math.log(20), abs=1e-12)
+
+
+def test_flatness_definition_cases():
+    s = np.array([False, True, True, True, False])
+    H = np.array([0, 10, 5, 8, 0])
+    assert flatness(H, s) == pytest.approx(0.5)
+    assert flatness(H, s, 0, 3) == -1.0        # target end not visited
+    assert flatness(np.array([0, 10, 0, 8, 0]), s) == 0.0
+
+
+def test_ln_omega_exact_from_exact_histogram():
+    rng = np.random.default_rng(4)
+    lnW = rng.normal(size=NB)
+    H = _exact_hist(OM, lnW, E_LO)
+    est = ln_omega(lnW, H, 16, 8)
+    for e, c in OM.items():
+        assert est[e - E_LO] == pytest.approx(math.log(c), abs=1e-9)
+    assert np.isnan(est[-11 - E_LO])
+
+
+@pytest.mark.slow
+def test_multicanonical_run_recovers_ln_omega_4x4():
+    """Full method (Sec. 2) on 4x4, N=8: iterate the recursion to a flat H,
+    then one long iteration; ln Omega within 0.02 of the enumeration."""
+    sysm = muca.System(2, 4, 8, 32, 100)
+    iters, H, f = muca.run_to_flat(sysm, 2000, 40, "recursive", t_lo=-12, t_hi=0)
+    assert f >= 0.5, (iters, f)
+    H, _, _ = sysm.iterate(80000, 1000)
+    est = ln_omega(sysm.lnW, H, 16, 8)
+    for e, c in OM.items():
+        assert abs(est[e - E_LO] - math.log(c)) < 0.02, (e, est[e - E_LO], math.log(c))
+
+
+def test_multicanonical_simple_scheme_flattens_3x3():
+    sysm = muca.System(2, 3, 4, 16, 7)
+    iters, H, f = muca.run_to_flat(sysm, 1000, 30, "simple", t_lo=-4, t_hi=-2)
+    assert f >= 0.5
