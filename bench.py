@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark: attempted moves/s of the parallel multicanonical iteration on GB300.
+
+One step = one iteration of the method (Sec. 2) over the whole workload:
+every walker performs sweeps*N attempted jump moves with fixed weights
+(walker-update kernel), the per-walker histograms are summed on the device
+(Eq. 2), and the weights are updated by the recursion and redistributed as a
+new threshold table.  Steps continue the same weight iteration from lnW = 0:
+the W warm-up steps are its first iterations, the K timed steps the next ones.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1401_4076_gb300 import workloads  # noqa: E402
+
+WORKLOADS = {
+    "small2d": workloads.SMALL_2D,
+    "medium2d": workloads.MEDIUM_2D,
+    "large3d": workloads.LARGE_3D,
+    "batched": workloads.batched_uneven(),
+}
+METRIC = "attempted moves/s"
+
+# Algorithmic integer work per attempted move (thread-instruction equivalents),
+# used for the issue-slot roofline: Philox4x32-10 (10 rounds x (4 multiplies,
+# 4 xor, 2 key adds) = 100), two multiply-high index maps (2), list reads (2),
+# neighbour sites (2 sites x 5 ops per axis), occupancy bit tests
+# (2 x 2d x 3 ops), dE and threshold compare (6), histogram run-length (2).
+def alg_ops_per_attempt(d: int) -> int:
+    return 100 + 2 + 2 + 2 * 5 * d + 2 * 2 * d * 3 + 6 + 2
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _max_over_ranks(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def shard_systems(systems, rank):
+    """Weak scaling: rank r runs an independent copy of the workload with its
+    own walker seeds (seed_base shifted past every walker of lower ranks)."""
+    total = sum(s[3] for s in systems)
+    out = []
+    for (d, L, N, W, lo, hi, seed) in systems:
+        out.append((d, L, N, W, lo, hi, seed + rank * total))
+    return out
+
+
+def cpu_oracle_rate(wl, budget_s: float, seed_offset: int = 0):
+    """Attempted moves/s of the oracle (plain C, OpenMP over walkers) on a
+    bounded sample of the workload: its first system(s), all walkers' seeds
+    from the workload, lnW = 0, as many sweeps as fit the time budget."""
+    from oracle import chain
+    # calibrate on the largest-work system with a short run
+    d, L, N, W, lo, hi, seed = max(wl.systems, key=lambda s: s[2] * s[3] * s[0])
+    seed += seed_offset
+    e_lo, e_hi = (-d * N, 0) if (lo == 0 and hi == 0) else (lo, hi)
+    nw = min(W, max(chain.num_threads() * 4, 16))
+    S, occ, E = chain.init_walkers(d, L, N, nw, seed)
+    T = chain.thresholds(d, e_lo, e_hi, np.zeros(e_hi - e_lo + 1))
+    t0 = time.perf_counter()
+    chain.run_walkers(d, L, N, seed, 0, N, e_lo, e_hi, T, S, occ, E)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    sweeps = max(1, int(budget_s / dt))
+    t0 = time.perf_counter()
+    chain.run_walkers(d, L, N, seed, 1, sweeps * N, e_lo, e_hi, T, S, occ, E)
+    dt = time.perf_counter() - t0
+    attempts = nw * sweeps * N
+    sample = (f"system d={d} L={L} N={N}: {nw} of its {W} walkers x {sweeps} sweeps "
+              f"({attempts} attempts), lnW=0, {dt:.1f} s")
+    return attempts / dt, chain.num_threads(), sample
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return 0
+    from oracle.build import build_oracle
+    build_oracle()
+    per_step = max(1.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wl, per_step * 0.2)
+    rates = []
+    samples = []
+    cores = 1
+    for _ in range(args.steps):
+        r, cores, s = cpu_oracle_rate(wl, per_step)
+        rates.append(r)
+        samples.append(s)
+    value = float(statistics.mean(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": _config(wl, args),
+        "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+                         "sample": samples[-1]},
+        "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _config(wl, args):
+    return {"workload": wl.name, "systems": len(wl.systems),
+            "walkers": sum(s[3] for s in wl.systems),
+            "sweeps_per_iteration": args.sweeps or wl.sweeps,
+            "attempts_per_step": (args.sweeps or wl.sweeps) * sum(s[2] * s[3] for s in wl.systems),
+            "weights": "recursive update from lnW=0; timed steps are iterations W..W+K-1",
+            "l2": "flushed (512 MB write) before every timed step",
+            "launch": args.launch_desc}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mucal", "reference"], default="mucal")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="medium2d")
+    ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
+    ap.add_argument("--kernel", type=int, default=-1)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--wpb", type=int, default=0)
+    ap.add_argument("--smem", type=int, default=-1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+    world, rank, local = _dist_setup()
+    args.launch_desc = None
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        rc = run_reference(args, wl, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+    from paper_1401_4076_gb300 import mucal as m
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    stream = torch.cuda.current_stream(device)
+    sweeps = args.sweeps or wl.sweeps
+    systems = shard_systems(wl.systems, rank)
+    attempts_per_step = sweeps * sum(s[2] * s[3] for s in systems)
+
+    mc = m.Mucal(systems, cuda_stream=stream.cuda_stream)
+    if args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0:
+        cur = mc.launch()
+        cfg = dict(kernel=args.kernel if args.kernel >= 0 else cur["kernel"],
+                   lanes_per_walker=args.lanes or cur["lanes_per_walker"],
+                   walkers_per_block=args.wpb or cur["walkers_per_block"],
+                   bits_in_smem=args.smem if args.smem >= 0 else cur["bits_in_smem"])
+        mc.set_launch(**cfg)
+    args.launch_desc = mc.launch()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def step(it):
+        mc.run_iteration(sweeps, it)
+        for s in range(len(systems)):
+            mc.update_weights(s, m.MUCAL_SCHEME_RECURSIVE)
+
+    for it in range(args.warmup):
+        step(it)
+    torch.cuda.synchronize(device)
+    _barrier(world)
+    torch.cuda.synchronize(device)
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step(args.warmup + i)
+        ends[i].record(stream)
+        kernel_ms.append(mc.stats(0)["kernel_ms"])
+    torch.cuda.synchronize(device)
+    wall = time.perf_counter() - wall0
+    _barrier(world)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop() if clocks else None
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    step_ms = _max_over_ranks(step_ms, world, device)
+    total_attempts = attempts_per_step * args.steps * world
+    value = total_attempts / (step_ms / 1000.0)
+
+    # dominant kernel (walker update): algorithmic integer ops per launch / its duration
+    d_max = max(s[0] for s in systems)
+    ops_launch = sum(alg_ops_per_attempt(s[0]) * s[2] * s[3] * sweeps for s in systems)
+    k_ms = statistics.mean(kernel_ms)
+    peaks, peak_kind = _peaks()
+    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+    peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6  # thread-instr/s
+    achieved = ops_launch / (k_ms / 1000.0)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                "peak_source": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz"
+                               f" ({peak_kind} max clock)",
+                "kernel": "walker_update", "kernel_ms": k_ms,
+                "alg_ops_per_attempt": alg_ops_per_attempt(d_max)}
+
+    line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": _config(wl, args), "roofline": roofline,
+            "clocks": clk, "gpu_launches": None}
+    # launches inside the timed region: per step one walker update, one memset pair
+    # per system is a driver memset, one histogram-reduce launch per system
+    line["gpu_launches"] = args.steps * (1 + len(systems))
+    mc.close()
+
+    if not args.no_e2e:
+        line["e2e"] = e2e_measure(wl, args, systems, stream, device, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle.build import build_oracle
+        build_oracle()
+        r, cores, sample = cpu_oracle_rate(wl, args.cpu_budget)
+        line["cpu_baseline"] = {"value": r, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_measure(wl, args, systems, stream, device, world):
+    """The same metric end to end through the public API from host buffers: a
+    fresh context (initial placement), then K iterations each uploading the new
+    threshold table and reading the histogram back to the host."""
+    import torch
+    from paper_1401_4076_gb300 import mucal as m
+    sweeps = args.sweeps or wl.sweeps
+    attempts = sweeps * sum(s[2] * s[3] for s in systems) * args.steps
+    torch.cuda.synchronize(device)
+    _barrier(world)
+    t0 = time.perf_counter()
+    mc = m.Mucal(systems, cuda_stream=stream.cuda_stream)
+    if args.launch_desc:
+        mc.set_launch(**args.launch_desc)
+    h2d = d2h = 0
+    for it in range(args.steps):
+        mc.run_iteration(sweeps, it)
+        for s in range(len(systems)):
+            H = mc.histogram(s)
+            lnW, _ = mc.update_weights(s, m.MUCAL_SCHEME_RECURSIVE)
+            i = mc.info[s]
+            d2h += H.nbytes
+            h2d += i["n_bins"] * i["width"] * 4
+    torch.cuda.synchronize(device)
+    dt = _max_over_ranks(time.perf_counter() - t0, world, device)
+    mc.close()
+    return {"value": attempts * world / dt, "unit": "attempts/s",
+            "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+            "includes": "context creation + initial placement, K iterations with weight updates"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

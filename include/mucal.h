@@ -1,0 +1,216 @@
+/*
+ * mucal: parallel multicanonical simulation of a fixed-N lattice gas on one GPU.
+ *
+ * C ABI of libmucal.so.  Every function returns an int status (MUCAL_OK = 0,
+ * negative on error; see the MUCAL_ERR_* codes) unless stated otherwise, and
+ * never throws.  Host buffers passed in are owned by the caller and only read
+ * or written during the call; every device buffer is owned by the library and
+ * freed by mucal_destroy.  A context is bound to the CUDA device that is
+ * current when mucal_init_systems is called and to one CUDA stream; calls on
+ * one context must not run concurrently from several host threads.
+ * There is no CPU fallback: without a usable CUDA device mucal_init_systems
+ * fails with MUCAL_ERR_NO_DEVICE.
+ *
+ * The method (Zierenberg, Wiedenmann, Janke, "Application of the parallel
+ * multicanonical method to lattice gas condensation"):
+ *   - model, Sec. 3 / Eq. 5: sites of a periodic L^d lattice (d = 2 square,
+ *     d = 3 simple cubic) hold n_i in {0,1} with sum n_i = N fixed, and
+ *     E = -J * #{occupied nearest-neighbour pairs}, J = 1;
+ *   - Sec. 2: p independent walkers run equilibrium Metropolis updates with
+ *     the same weights W(E), accepting with min(1, W(E_n)/W(E_o)); their
+ *     histograms are summed, H^i(E) = sum_j H^i_j(E) (Eq. 2), and the next
+ *     weights follow from W^i and H^i (W^{i+1} = W^i / H^i, or a recursion).
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - site s = x_0 + L x_1 (+ L^2 x_2), periodic neighbours x_k +- 1 mod L;
+ *   - move: a uniformly chosen particle jumps to a uniformly chosen empty
+ *     site.  Particle and empty-site lists are kept in one array S per walker,
+ *     S[0..N) = particle sites, S[N..V) = empty sites; an accepted move of
+ *     particle index k to empty index m swaps S[k] and S[N+m];
+ *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = 64-bit seed
+ *     of walker w = seed_base + w (low word first), counter =
+ *     (t low, t high, iteration, 0) for attempt t of an iteration;
+ *     r0 -> k = floor(r0 N / 2^32), r1 -> m = floor(r1 (V-N) / 2^32),
+ *     r2 -> acceptance variate, r3 unused.  The initial placement is a partial
+ *     Fisher-Yates shuffle drawing output j from counter (j/4 low, j/4 high,
+ *     0, 1), word j%4: for j < N, swap S[j] with S[j + floor(r (V-j) / 2^32)];
+ *   - acceptance: per window bin b = E_o - e_lo and dE in [-2d, 2d] a uint32
+ *     threshold T, built in double precision on the host from lnW:
+ *     0 if E_o + dE leaves the window, 0xFFFFFFFF if lnW(E_o+dE) >= lnW(E_o),
+ *     else min(floor(2^32 exp(lnW(E_o+dE) - lnW(E_o))), 0xFFFFFFFE);
+ *     a move is accepted iff T == 0xFFFFFFFF or r2 < T;
+ *   - every attempt, accepted or not, records the energy after the attempt.
+ *   - Walker states carry over from one iteration to the next.
+ */
+#ifndef MUCAL_H
+#define MUCAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MUCAL_OK                 0
+#define MUCAL_ERR_INVALID_ARG   -1  /* bad pointer, size, index or parameter */
+#define MUCAL_ERR_CUDA          -2  /* a CUDA runtime call failed */
+#define MUCAL_ERR_OOM           -3  /* device or pinned host allocation failed */
+#define MUCAL_ERR_NO_DEVICE     -4  /* no usable CUDA device */
+#define MUCAL_ERR_NOT_READY     -5  /* call order violated (e.g. no histogram yet) */
+#define MUCAL_ERR_STATE         -6  /* a device-side consistency check failed */
+
+/* ---- flags of mucal_init_systems ---------------------------------------- */
+/* Keep the per-walker histograms H_j(E) of the last iteration readable via
+ * mucal_get_histogram (they always exist on the device; without the flag the
+ * library may skip keeping them). */
+#define MUCAL_FLAG_PER_WALKER_HIST 0x1u
+
+/* ---- weight-update schemes of mucal_update_weights ---------------------- */
+/* W^{i+1}(E) = W^i(E) / H^i(E) where H^i(E) > 0, unchanged elsewhere (Sec. 2). */
+#define MUCAL_SCHEME_SIMPLE     0
+/* The accumulated-statistics recursion cited in Sec. 2, on consecutive
+ * visited energies E_prev < E of the cumulative visited set:
+ * g = H(E_prev) H(E) / (H(E_prev) + H(E)), p(E) += g, kappa = g / p(E),
+ * ln(W(E)/W(E_prev)) += kappa (ln H(E_prev) - ln H(E)); unvisited bins keep
+ * their log-weight offset to the nearest visited bin above them (below if
+ * none is above).  Its first step equals MUCAL_SCHEME_SIMPLE on the visited
+ * bins. */
+#define MUCAL_SCHEME_RECURSIVE  1
+
+/* ---- walker-update kernels (mucal_launch_config.kernel) ------------------ */
+/* One thread advances one walker, attempt after attempt. */
+#define MUCAL_KERNEL_THREAD     0
+/* A group of lanes advances one walker: the lanes evaluate consecutive
+ * attempts against the same state in parallel and commit them in order,
+ * re-evaluating after every accepted move, so the chain is identical to the
+ * one-thread chain. */
+#define MUCAL_KERNEL_GROUP      1
+
+typedef struct mucal_system_desc {
+    int32_t d;          /* lattice dimension, 2 or 3 */
+    int32_t L;          /* linear size, 3 <= L, L^d <= 2^24 */
+    int32_t N;          /* particles, 0 < N < L^d */
+    int32_t n_walkers;  /* independent walkers (the p processes of Sec. 2), >= 1 */
+    int32_t e_lo;       /* energy window [e_lo, e_hi]; e_lo = e_hi = 0 selects */
+    int32_t e_hi;       /*   the full range [-dN, 0]; otherwise -dN <= e_lo < e_hi <= 0 */
+    uint64_t seed_base; /* walker w uses Philox key seed_base + w */
+} mucal_system_desc;
+
+typedef struct mucal_launch_config {
+    int32_t kernel;            /* MUCAL_KERNEL_THREAD or MUCAL_KERNEL_GROUP */
+    int32_t lanes_per_walker;  /* 1 for THREAD; 2, 4, 8, 16 or 32 for GROUP */
+    int32_t walkers_per_block; /* threads per block = walkers_per_block * lanes, <= 1024 */
+    int32_t bits_in_smem;      /* 1: stage each walker's occupation bitset in shared
+                                  memory for the launch; 0: use it in global memory */
+} mucal_launch_config;
+
+typedef struct mucal_system_info {
+    int32_t d, L, N, n_walkers, e_lo, e_hi;
+    int32_t V;          /* L^d */
+    int32_t n_bins;     /* e_hi - e_lo + 1 */
+    int32_t width;      /* 4d + 1 thresholds per bin */
+    int32_t index_bytes;/* 2 if V <= 65536 else 4: bytes per entry of S */
+    uint64_t seed_base;
+} mucal_system_info;
+
+typedef struct mucal_stats {
+    uint64_t attempts;      /* attempts of the last mucal_run_iteration, all walkers */
+    uint64_t accepts;       /* accepted moves of the last iteration, all walkers */
+    double   kernel_ms;     /* device time of the last walker-update launch (CUDA events) */
+    double   iteration_ms;  /* device time of the last whole mucal_run_iteration */
+    uint64_t walker_launches; /* walker-update kernel launches so far */
+} mucal_stats;
+
+/* Create a context holding n_sys systems (Sec. 2 walkers of Sec. 3 lattice
+ * gases) and place every walker's N particles at random (initial placement
+ * above).  sys: host array of n_sys descriptors (copied).  cuda_stream: a
+ * cudaStream_t to run on, or NULL for a stream owned by the context.  The
+ * weights start at lnW = 0 (all moves inside the window accepted).
+ * Errors: INVALID_ARG (bad descriptor; an initial energy outside a
+ * user-given window), NO_DEVICE, OOM, CUDA.  *out is NULL on error. */
+int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys,
+                       void *cuda_stream, uint32_t flags);
+
+/* Release every device and host resource of the context (NULL is allowed). */
+void mucal_destroy(void *ctx);
+
+/* Text of the last error on this context (or of the last failed
+ * mucal_init_systems if ctx is NULL); valid until the next call. */
+const char *mucal_last_error(void *ctx);
+
+/* Set lnW(E) of system sys for E = e_lo .. e_hi (host float64 array of
+ * n_bins finite values, copied).  Builds the acceptance thresholds in double
+ * precision (min(1, W(E_n)/W(E_o)), Sec. 2) and uploads them.  Resets the
+ * recursion memory (cumulative visited set and accumulated weights).
+ * Errors: INVALID_ARG (index, size, non-finite value), CUDA. */
+int mucal_set_weights(void *ctx, int32_t sys, const double *lnW, int32_t n_bins);
+
+/* Read back the current lnW of system sys into lnW_out[n_bins] (host). */
+int mucal_get_weights(void *ctx, int32_t sys, double *lnW_out, int32_t n_bins);
+
+/* Read back the uint32 threshold table of system sys into T[n_bins*width]
+ * (host), laid out T[b*width + dE + 2d]. */
+int mucal_get_thresholds(void *ctx, int32_t sys, uint32_t *T, int64_t n);
+
+/* Choose the walker-update kernel and its launch shape for later
+ * iterations.  Errors: INVALID_ARG (unsupported combination, or more shared
+ * memory than a block can have for some system). */
+int mucal_set_launch_config(void *ctx, const mucal_launch_config *cfg);
+int mucal_get_launch_config(void *ctx, mucal_launch_config *cfg);
+
+/* One iteration of Sec. 2 for every system of the context, asynchronous on
+ * the context's stream: zero the histograms, let every walker perform
+ * sweeps * N attempted moves with the current weights (iteration enters the
+ * Philox counter), record H_j(E) per walker, and sum them into H(E) (Eq. 2)
+ * on the device.  sweeps >= 1; sweeps * N must be below 2^40.
+ * Errors: INVALID_ARG, CUDA. */
+int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration);
+
+/* Wait for the context's stream and copy the summed histogram H(E) of system
+ * sys into H[n_bins] (host int64).  per_walker: NULL, or host int64
+ * [n_walkers * n_bins] that receives H_j(E), walker-major (needs
+ * MUCAL_FLAG_PER_WALKER_HIST).  Errors: INVALID_ARG, NOT_READY (no
+ * iteration run yet), CUDA. */
+int mucal_get_histogram(void *ctx, int32_t sys, int64_t *H, int32_t n_bins, int64_t *per_walker);
+
+/* Weight update from the last histogram of system sys (Sec. 2):
+ * scheme MUCAL_SCHEME_SIMPLE or MUCAL_SCHEME_RECURSIVE, in double precision on
+ * the host, then lnW is shifted to max 0, the thresholds are rebuilt and
+ * uploaded (the redistribution of the weights to all walkers).  lnW_out
+ * (nullable, host float64[n_bins]) receives the new lnW; flatness_out
+ * (nullable) receives min/max of H over the cumulative visited set inside the
+ * target window, or -1 while an end of that window is unvisited.
+ * Errors: INVALID_ARG, NOT_READY, CUDA. */
+int mucal_update_weights(void *ctx, int32_t sys, int32_t scheme, double *lnW_out,
+                         double *flatness_out);
+
+/* Target window of the flatness measure of system sys (default: from the
+ * lowest visited energy to the highest).  t_lo = t_hi = 0 restores it. */
+int mucal_set_target_window(void *ctx, int32_t sys, int32_t t_lo, int32_t t_hi);
+
+/* Copy walker w's state of system sys to host buffers (any may be NULL):
+ * occ uint8[V] (n_i), S int32[V] (particle then empty sites), E (energy). */
+int mucal_get_walker_state(void *ctx, int32_t sys, int32_t walker, uint8_t *occ, int32_t *S,
+                           int32_t *E);
+
+/* Sizes and parameters of system sys. */
+int mucal_get_system_info(void *ctx, int32_t sys, mucal_system_info *info);
+
+/* Counters and timings of the last iteration of system sys (kernel_ms and
+ * iteration_ms cover the whole launch, all systems). */
+int mucal_get_stats(void *ctx, int32_t sys, mucal_stats *stats);
+
+/* Device pointer of the summed histogram H(E) of system sys (int64[n_bins],
+ * library-owned, valid until mucal_destroy; contents valid once the
+ * context's stream has finished the last mucal_run_iteration). */
+int mucal_histogram_device_ptr(void *ctx, int32_t sys, void **dptr);
+
+/* Library version string. */
+const char *mucal_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MUCAL_H */

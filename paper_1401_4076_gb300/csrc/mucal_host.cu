@@ -1,0 +1,733 @@
+// Host side of libmucal: the C ABI declared in include/mucal.h, device memory
+// management, the acceptance-threshold build and the weight iteration of
+// Sec. 2 in double precision.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "mucal.h"
+#include "mucal_internal.h"
+
+using mucal::BlockWork;
+using mucal::LaunchShape;
+using mucal::SysParams;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct System {
+    mucal_system_desc desc{};
+    SysParams p{};                  // host copy holding device pointers
+    std::vector<double> lnW;        // current log-weights over the window
+    std::vector<uint8_t> visited;   // cumulative visited set (recursion memory)
+    std::vector<double> pacc;       // accumulated pair weights (recursion memory)
+    std::vector<int64_t> H;         // last summed histogram, host copy
+    bool hist_on_host = false;
+    int32_t t_lo = 0, t_hi = 0;     // target window (bins), -1 = default
+    bool target_default = true;
+    uint32_t *thr_pinned = nullptr; // staging buffer of the threshold upload
+    size_t thr_count = 0;
+    uint64_t last_attempts = 0;
+};
+
+struct Context {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint32_t flags = 0;
+    std::vector<System> sys;
+    SysParams *d_sys = nullptr;
+    BlockWork *d_work = nullptr;
+    int n_blocks = 0;
+    int max_smem = 0;
+    LaunchShape shape{};
+    cudaEvent_t ev_it0 = nullptr, ev_k0 = nullptr, ev_k1 = nullptr, ev_it1 = nullptr;
+    bool ran = false;
+    uint64_t sweeps_last = 0;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+int fail(Context *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_init_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? MUCAL_ERR_OOM : MUCAL_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Acceptance thresholds: min(1, W(E_n)/W(E_o)) of Sec. 2 as a uint32 per
+// (E_o bin, dE).  Double precision, host libm exp; the device only compares.
+// ---------------------------------------------------------------------------
+void build_thresholds(const System &s, uint32_t *T)
+{
+    const int nb = s.p.n_bins;
+    const int width = s.p.width;
+    const int half = 2 * s.p.d;
+    for (int b = 0; b < nb; ++b) {
+        const double from = s.lnW[b];
+        uint32_t *row = T + (size_t)b * width;
+        for (int j = 0; j < width; ++j) {
+            const int to = b + (j - half);
+            if (to < 0 || to >= nb) {
+                row[j] = 0u;
+                continue;
+            }
+            const double diff = s.lnW[to] - from;
+            if (diff >= 0.0) {
+                row[j] = 0xFFFFFFFFu;
+                continue;
+            }
+            const double scaled = std::floor(std::ldexp(std::exp(diff), 32));
+            row[j] = scaled >= 4294967294.0 ? 0xFFFFFFFEu : (uint32_t)scaled;
+        }
+    }
+}
+
+int upload_thresholds(Context *c, System &s)
+{
+    // The pinned staging buffer may still feed an earlier asynchronous copy.
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    build_thresholds(s, s.thr_pinned);
+    CUDA_TRY(c, cudaMemcpyAsync((void *)s.p.thr, s.thr_pinned, s.thr_count * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, c->stream));
+    return MUCAL_OK;
+}
+
+void normalise_max_zero(std::vector<double> &w)
+{
+    double mx = -INFINITY;
+    for (double v : w) mx = std::max(mx, v);
+    for (double &v : w) v -= mx;
+}
+
+// W^{i+1} = W^i / H^i where H^i > 0 (Sec. 2), in logs.
+void update_simple(System &s)
+{
+    const int nb = s.p.n_bins;
+    for (int b = 0; b < nb; ++b) {
+        if (s.H[b] > 0) {
+            s.visited[b] = 1;
+            s.lnW[b] -= std::log((double)s.H[b]);
+        }
+    }
+    normalise_max_zero(s.lnW);
+}
+
+// Accumulated-statistics recursion on consecutive members of the cumulative
+// visited set (the recursive scheme cited in Sec. 2).
+void update_recursive(System &s)
+{
+    const int nb = s.p.n_bins;
+    for (int b = 0; b < nb; ++b)
+        if (s.H[b] > 0) s.visited[b] = 1;
+    std::vector<int> mem;
+    mem.reserve(nb);
+    for (int b = 0; b < nb; ++b)
+        if (s.visited[b]) mem.push_back(b);
+    if (mem.empty()) {
+        normalise_max_zero(s.lnW);
+        return;
+    }
+    const std::vector<double> old = s.lnW;
+    std::vector<double> &w = s.lnW;
+    // rebuild from the top member downwards
+    for (size_t j = mem.size() - 1; j >= 1; --j) {
+        const int hi = mem[j], lo = mem[j - 1];
+        double lnr = old[hi] - old[lo];
+        const double hlo = (double)s.H[lo], hhi = (double)s.H[hi];
+        const double g = (hlo > 0.0 && hhi > 0.0) ? hlo * hhi / (hlo + hhi) : 0.0;
+        s.pacc[hi] += g;
+        if (g > 0.0) lnr += (g / s.pacc[hi]) * (std::log(hlo) - std::log(hhi));
+        w[lo] = w[hi] - lnr;
+    }
+    // bins outside the visited set ride with the nearest member above
+    // (or the top member when none is above)
+    int next_member = -1;
+    for (int b = nb - 1; b >= 0; --b) {
+        if (s.visited[b]) {
+            next_member = b;
+            continue;
+        }
+        const int ref = next_member >= 0 ? next_member : mem.back();
+        w[b] = old[b] + (w[ref] - old[ref]);
+    }
+    normalise_max_zero(w);
+}
+
+double flatness(const System &s)
+{
+    const int nb = s.p.n_bins;
+    int first = -1, last = -1;
+    for (int b = 0; b < nb; ++b)
+        if (s.visited[b]) {
+            if (first < 0) first = b;
+            last = b;
+        }
+    if (first < 0) return -1.0;
+    const int lo = s.target_default ? first : s.t_lo;
+    const int hi = s.target_default ? last : s.t_hi;
+    if (!s.visited[lo] || !s.visited[hi]) return -1.0;
+    double mn = INFINITY, mx = 0.0;
+    for (int b = lo; b <= hi; ++b) {
+        if (!s.visited[b]) continue;
+        const double h = (double)s.H[b];
+        mn = std::min(mn, h);
+        mx = std::max(mx, h);
+    }
+    return mx > 0.0 ? mn / mx : 0.0;
+}
+
+int check_desc(const mucal_system_desc &d, int i)
+{
+    if (d.d != 2 && d.d != 3) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "system %d: d must be 2 or 3", i);
+    if (d.L < 3 || d.L > 4096) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "system %d: L must be in [3, 4096]", i);
+    const uint64_t V = d.d == 2 ? (uint64_t)d.L * d.L : (uint64_t)d.L * d.L * d.L;
+    if (V > (1u << 24) || V * (uint64_t)d.L >= (1ull << 32))
+        return fail(nullptr, MUCAL_ERR_INVALID_ARG, "system %d: lattice too large", i);
+    if (d.N <= 0 || (uint64_t)d.N >= V)
+        return fail(nullptr, MUCAL_ERR_INVALID_ARG, "system %d: need 0 < N < L^d", i);
+    if (d.n_walkers <= 0) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "system %d: n_walkers must be > 0", i);
+    if (!(d.e_lo == 0 && d.e_hi == 0)) {
+        if (d.e_lo < -d.d * d.N || d.e_hi > 0 || d.e_lo >= d.e_hi)
+            return fail(nullptr, MUCAL_ERR_INVALID_ARG,
+                        "system %d: window must satisfy -dN <= e_lo < e_hi <= 0", i);
+    }
+    return MUCAL_OK;
+}
+
+void free_system(System &s)
+{
+    cudaFree(s.p.bits);
+    cudaFree(s.p.S);
+    cudaFree(s.p.E);
+    cudaFree(s.p.hist);
+    cudaFree((void *)s.p.thr);
+    cudaFree(s.p.accepts);
+    cudaFree(s.p.H);
+    if (s.thr_pinned) cudaFreeHost(s.thr_pinned);
+    s.p = SysParams{};
+    s.thr_pinned = nullptr;
+}
+
+void destroy_context(Context *c)
+{
+    if (!c) return;
+    if (c->device >= 0) cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &s : c->sys) free_system(s);
+    cudaFree(c->d_sys);
+    cudaFree(c->d_work);
+    if (c->ev_it0) cudaEventDestroy(c->ev_it0);
+    if (c->ev_k0) cudaEventDestroy(c->ev_k0);
+    if (c->ev_k1) cudaEventDestroy(c->ev_k1);
+    if (c->ev_it1) cudaEventDestroy(c->ev_it1);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// Shared memory a block of the current shape needs for system s.
+size_t smem_for(const LaunchShape &sh, const SysParams &p)
+{
+    if (!sh.bits_in_smem) return 0;
+    return (size_t)sh.walkers_per_block * (size_t)p.words * sizeof(uint32_t);
+}
+
+// Split every system's walkers into blocks of the launch shape; order the
+// blocks by decreasing cost (attempts per walker grow with N) so the longest
+// blocks start first when systems of uneven size share one launch.
+int build_work(Context *c, const LaunchShape &sh)
+{
+    std::vector<BlockWork> work;
+    for (int s = 0; s < (int)c->sys.size(); ++s) {
+        const SysParams &p = c->sys[s].p;
+        for (int w0 = 0; w0 < p.n_walkers; w0 += sh.walkers_per_block) {
+            BlockWork bw{};
+            bw.sys = s;
+            bw.walker0 = w0;
+            bw.count = std::min(sh.walkers_per_block, p.n_walkers - w0);
+            work.push_back(bw);
+        }
+    }
+    std::stable_sort(work.begin(), work.end(), [&](const BlockWork &a, const BlockWork &b) {
+        const double ca = (double)c->sys[a.sys].p.N * c->sys[a.sys].p.d;
+        const double cb = (double)c->sys[b.sys].p.N * c->sys[b.sys].p.d;
+        return ca > cb;
+    });
+    if (c->d_work) {
+        cudaFree(c->d_work);
+        c->d_work = nullptr;
+    }
+    CUDA_TRY(c, cudaMalloc(&c->d_work, std::max<size_t>(1, work.size()) * sizeof(BlockWork)));
+    CUDA_TRY(c, cudaMemcpy(c->d_work, work.data(), work.size() * sizeof(BlockWork),
+                           cudaMemcpyHostToDevice));
+    c->n_blocks = (int)work.size();
+    return MUCAL_OK;
+}
+
+int apply_launch_config(Context *c, const mucal_launch_config &cfg)
+{
+    LaunchShape sh{};
+    sh.kernel = cfg.kernel;
+    sh.lanes = cfg.lanes_per_walker;
+    sh.walkers_per_block = cfg.walkers_per_block;
+    sh.bits_in_smem = cfg.bits_in_smem ? 1 : 0;
+    if (sh.kernel != MUCAL_KERNEL_THREAD)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "kernel %d is not available", sh.kernel);
+    if (sh.lanes != 1) return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
+    if (sh.walkers_per_block < 1 || sh.walkers_per_block * sh.lanes > 1024)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "walkers_per_block * lanes must be in [1, 1024]");
+    size_t smem = 0;
+    for (auto &s : c->sys) smem = std::max(smem, smem_for(sh, s.p));
+    if (smem > (size_t)c->max_smem)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "launch needs %zu bytes of shared memory, limit %d",
+                    smem, c->max_smem);
+    sh.smem_bytes = smem;
+    int rc = build_work(c, sh);
+    if (rc != MUCAL_OK) return rc;
+    c->shape = sh;
+    return MUCAL_OK;
+}
+
+Context *as_ctx(void *p) { return static_cast<Context *>(p); }
+
+int check_sys(Context *c, int32_t s)
+{
+    if (!c) return MUCAL_ERR_INVALID_ARG;
+    if (s < 0 || s >= (int32_t)c->sys.size())
+        return fail(c, MUCAL_ERR_INVALID_ARG, "system index %d out of range", s);
+    return MUCAL_OK;
+}
+
+int fetch_histogram(Context *c, System &s)
+{
+    if (!c->ran) return fail(c, MUCAL_ERR_NOT_READY, "no iteration has been run");
+    if (!s.hist_on_host) {
+        CUDA_TRY(c, cudaMemcpyAsync(s.H.data(), s.p.H, s.H.size() * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        s.hist_on_host = true;
+    }
+    return MUCAL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mucal_version(void) { return "mucal 0.1 (sm_103a)"; }
+
+const char *mucal_last_error(void *ctx)
+{
+    Context *c = as_ctx(ctx);
+    return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, void *cuda_stream,
+                       uint32_t flags)
+{
+    if (!out) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sys || n_sys <= 0) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "need at least one system");
+    for (int i = 0; i < n_sys; ++i) {
+        int rc = check_desc(sys[i], i);
+        if (rc != MUCAL_OK) return rc;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        return fail(nullptr, MUCAL_ERR_NO_DEVICE, "no CUDA device available");
+    }
+    Context *c = new (std::nothrow) Context();
+    if (!c) return fail(nullptr, MUCAL_ERR_OOM, "host allocation failed");
+    c->flags = flags;
+    int rc = MUCAL_OK;
+    auto bail = [&](int code) {
+        if (c->err.size()) g_init_error = c->err;
+        destroy_context(c);
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        c->device = -1;
+        return bail(fail(nullptr, MUCAL_ERR_NO_DEVICE, "cudaGetDevice failed"));
+    }
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(nullptr, MUCAL_ERR_CUDA, "stream creation failed"));
+        c->own_stream = true;
+    }
+    if (mucal::walker_update_max_smem(&c->max_smem) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_CUDA, "cannot query shared memory limit"));
+    if (cudaEventCreate(&c->ev_it0) != cudaSuccess || cudaEventCreate(&c->ev_k0) != cudaSuccess ||
+        cudaEventCreate(&c->ev_k1) != cudaSuccess || cudaEventCreate(&c->ev_it1) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_CUDA, "event creation failed"));
+
+    c->sys.resize(n_sys);
+    for (int i = 0; i < n_sys; ++i) {
+        System &s = c->sys[i];
+        s.desc = sys[i];
+        SysParams &p = s.p;
+        p.d = sys[i].d;
+        p.L = sys[i].L;
+        p.N = sys[i].N;
+        p.V = p.d == 2 ? p.L * p.L : p.L * p.L * p.L;
+        p.L2 = p.L * p.L;
+        if (sys[i].e_lo == 0 && sys[i].e_hi == 0) {
+            p.e_lo = -p.d * p.N;
+            s.desc.e_lo = p.e_lo;
+            s.desc.e_hi = 0;
+        } else {
+            p.e_lo = sys[i].e_lo;
+        }
+        p.n_bins = s.desc.e_hi - p.e_lo + 1;
+        p.width = 4 * p.d + 1;
+        p.words = (p.V + 31) / 32;
+        p.idx16 = p.V <= 65536 ? 1 : 0;
+        p.n_walkers = sys[i].n_walkers;
+        p.magL = (uint32_t)(((1ull << 32) + (uint64_t)p.L - 1) / (uint64_t)p.L);
+        p.seed_base = sys[i].seed_base;
+        const size_t nw = (size_t)p.n_walkers;
+        const size_t ib = p.idx16 ? 2 : 4;
+        void *ptr = nullptr;
+#define ALLOC(field, bytes)                                                         \
+    do {                                                                            \
+        cudaError_t e_ = cudaMalloc(&ptr, (bytes));                                 \
+        if (e_ != cudaSuccess) {                                                    \
+            cudaGetLastError();                                                     \
+            return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of %zu bytes for " \
+                             #field " failed", (size_t)(bytes)));                   \
+        }                                                                           \
+        p.field = decltype(p.field)(ptr);                                           \
+    } while (0)
+        ALLOC(bits, nw * p.words * sizeof(uint32_t));
+        ALLOC(S, nw * (size_t)p.V * ib);
+        ALLOC(E, nw * sizeof(int32_t));
+        ALLOC(hist, nw * (size_t)p.n_bins * sizeof(unsigned long long));
+        ALLOC(thr, (size_t)p.n_bins * p.width * sizeof(uint32_t));
+        ALLOC(accepts, nw * sizeof(unsigned long long));
+        ALLOC(H, (size_t)p.n_bins * sizeof(unsigned long long));
+#undef ALLOC
+        s.thr_count = (size_t)p.n_bins * p.width;
+        if (cudaMallocHost(&s.thr_pinned, s.thr_count * sizeof(uint32_t)) != cudaSuccess) {
+            s.thr_pinned = nullptr;
+            return bail(fail(nullptr, MUCAL_ERR_OOM, "pinned host allocation failed"));
+        }
+        s.lnW.assign(p.n_bins, 0.0);
+        s.visited.assign(p.n_bins, 0);
+        s.pacc.assign(p.n_bins, 0.0);
+        s.H.assign(p.n_bins, 0);
+        if (cudaMemsetAsync(p.bits, 0, nw * p.words * sizeof(uint32_t), c->stream) != cudaSuccess ||
+            cudaMemsetAsync(p.hist, 0, nw * (size_t)p.n_bins * 8, c->stream) != cudaSuccess ||
+            cudaMemsetAsync(p.H, 0, (size_t)p.n_bins * 8, c->stream) != cudaSuccess ||
+            cudaMemsetAsync(p.accepts, 0, nw * 8, c->stream) != cudaSuccess)
+            return bail(fail(nullptr, MUCAL_ERR_CUDA, "memset failed"));
+    }
+    if (cudaMalloc(&c->d_sys, n_sys * sizeof(SysParams)) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of system table failed"));
+    std::vector<SysParams> hp(n_sys);
+    for (int i = 0; i < n_sys; ++i) hp[i] = c->sys[i].p;
+    if (cudaMemcpy(c->d_sys, hp.data(), n_sys * sizeof(SysParams), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_CUDA, "copy of system table failed"));
+    if (mucal::launch_fill_identity(hp.data(), c->d_sys, n_sys, c->stream) != cudaSuccess ||
+        mucal::launch_init_walkers(hp.data(), c->d_sys, n_sys, c->stream) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_CUDA, "initial placement launch failed"));
+    for (int i = 0; i < n_sys; ++i) {
+        rc = upload_thresholds(c, c->sys[i]);
+        if (rc != MUCAL_OK) return bail(rc);
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_CUDA, "initial placement failed: %s",
+                         cudaGetErrorString(cudaGetLastError())));
+    // user-given windows must contain every initial energy
+    for (int i = 0; i < n_sys; ++i) {
+        const System &s = c->sys[i];
+        if (sys[i].e_lo == 0 && sys[i].e_hi == 0) continue;
+        std::vector<int32_t> e(s.p.n_walkers);
+        if (cudaMemcpy(e.data(), s.p.E, e.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(nullptr, MUCAL_ERR_CUDA, "energy read-back failed"));
+        for (int32_t v : e)
+            if (v < s.desc.e_lo || v > s.desc.e_hi)
+                return bail(fail(nullptr, MUCAL_ERR_INVALID_ARG,
+                                 "system %d: initial energy %d outside window [%d, %d]", i, v,
+                                 s.desc.e_lo, s.desc.e_hi));
+    }
+    mucal_launch_config def{MUCAL_KERNEL_THREAD, 1, 32, 1};
+    for (auto &s : c->sys)
+        if (smem_for(LaunchShape{0, 1, 32, 1, 0}, s.p) > (size_t)c->max_smem) def.bits_in_smem = 0;
+    rc = apply_launch_config(c, def);
+    if (rc != MUCAL_OK) return bail(rc);
+    *out = c;
+    return MUCAL_OK;
+}
+
+void mucal_destroy(void *ctx) { destroy_context(as_ctx(ctx)); }
+
+int mucal_set_weights(void *ctx, int32_t sys, const double *lnW, int32_t n_bins)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    System &s = c->sys[sys];
+    if (!lnW || n_bins != s.p.n_bins)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "lnW must hold n_bins = %d values", s.p.n_bins);
+    for (int b = 0; b < n_bins; ++b)
+        if (!std::isfinite(lnW[b])) return fail(c, MUCAL_ERR_INVALID_ARG, "lnW[%d] is not finite", b);
+    s.lnW.assign(lnW, lnW + n_bins);
+    std::fill(s.visited.begin(), s.visited.end(), 0);
+    std::fill(s.pacc.begin(), s.pacc.end(), 0.0);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    return upload_thresholds(c, s);
+}
+
+int mucal_get_weights(void *ctx, int32_t sys, double *lnW_out, int32_t n_bins)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    const System &s = c->sys[sys];
+    if (!lnW_out || n_bins != s.p.n_bins) return fail(c, MUCAL_ERR_INVALID_ARG, "bad lnW_out size");
+    std::copy(s.lnW.begin(), s.lnW.end(), lnW_out);
+    return MUCAL_OK;
+}
+
+int mucal_get_thresholds(void *ctx, int32_t sys, uint32_t *T, int64_t n)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    const System &s = c->sys[sys];
+    if (!T || n != (int64_t)s.thr_count) return fail(c, MUCAL_ERR_INVALID_ARG, "bad threshold buffer size");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaMemcpyAsync(T, s.p.thr, s.thr_count * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MUCAL_OK;
+}
+
+int mucal_set_launch_config(void *ctx, const mucal_launch_config *cfg)
+{
+    Context *c = as_ctx(ctx);
+    if (!c || !cfg) return MUCAL_ERR_INVALID_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return apply_launch_config(c, *cfg);
+}
+
+int mucal_get_launch_config(void *ctx, mucal_launch_config *cfg)
+{
+    Context *c = as_ctx(ctx);
+    if (!c || !cfg) return MUCAL_ERR_INVALID_ARG;
+    cfg->kernel = c->shape.kernel;
+    cfg->lanes_per_walker = c->shape.lanes;
+    cfg->walkers_per_block = c->shape.walkers_per_block;
+    cfg->bits_in_smem = c->shape.bits_in_smem;
+    return MUCAL_OK;
+}
+
+int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
+{
+    Context *c = as_ctx(ctx);
+    if (!c) return MUCAL_ERR_INVALID_ARG;
+    if (sweeps < 1) return fail(c, MUCAL_ERR_INVALID_ARG, "sweeps must be >= 1");
+    for (auto &s : c->sys)
+        if ((uint64_t)sweeps * (uint64_t)s.p.N >= (1ull << 40))
+            return fail(c, MUCAL_ERR_INVALID_ARG, "sweeps * N must be below 2^40");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaEventRecord(c->ev_it0, c->stream));
+    for (auto &s : c->sys) {
+        const size_t nw = (size_t)s.p.n_walkers;
+        CUDA_TRY(c, cudaMemsetAsync(s.p.hist, 0, nw * (size_t)s.p.n_bins * 8, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(s.p.H, 0, (size_t)s.p.n_bins * 8, c->stream));
+        s.hist_on_host = false;
+        s.last_attempts = (uint64_t)sweeps * (uint64_t)s.p.N * nw;
+    }
+    CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
+    CUDA_TRY(c, mucal::launch_walker_update(c->d_sys, c->d_work, c->n_blocks, c->shape,
+                                            (uint64_t)sweeps, iteration, c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->ev_k1, c->stream));
+    std::vector<SysParams> hp(c->sys.size());
+    for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
+    CUDA_TRY(c, mucal::launch_hist_reduce(hp.data(), c->d_sys, (int)hp.size(), c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->ev_it1, c->stream));
+    c->ran = true;
+    c->sweeps_last = (uint64_t)sweeps;
+    c->launches += 1;
+    return MUCAL_OK;
+}
+
+int mucal_get_histogram(void *ctx, int32_t sys, int64_t *H, int32_t n_bins, int64_t *per_walker)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    System &s = c->sys[sys];
+    if (!H || n_bins != s.p.n_bins) return fail(c, MUCAL_ERR_INVALID_ARG, "H must hold n_bins = %d", s.p.n_bins);
+    if (per_walker && !(c->flags & MUCAL_FLAG_PER_WALKER_HIST))
+        return fail(c, MUCAL_ERR_INVALID_ARG, "per-walker histograms need MUCAL_FLAG_PER_WALKER_HIST");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    rc = fetch_histogram(c, s);
+    if (rc != MUCAL_OK) return rc;
+    std::copy(s.H.begin(), s.H.end(), H);
+    if (per_walker) {
+        CUDA_TRY(c, cudaMemcpyAsync(per_walker, s.p.hist,
+                                    (size_t)s.p.n_walkers * (size_t)s.p.n_bins * 8,
+                                    cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    return MUCAL_OK;
+}
+
+int mucal_update_weights(void *ctx, int32_t sys, int32_t scheme, double *lnW_out, double *flatness_out)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    if (scheme != MUCAL_SCHEME_SIMPLE && scheme != MUCAL_SCHEME_RECURSIVE)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "unknown scheme %d", scheme);
+    System &s = c->sys[sys];
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    rc = fetch_histogram(c, s);
+    if (rc != MUCAL_OK) return rc;
+    if (scheme == MUCAL_SCHEME_SIMPLE)
+        update_simple(s);
+    else
+        update_recursive(s);
+    const double f = flatness(s);
+    rc = upload_thresholds(c, s);
+    if (rc != MUCAL_OK) return rc;
+    if (lnW_out) std::copy(s.lnW.begin(), s.lnW.end(), lnW_out);
+    if (flatness_out) *flatness_out = f;
+    return MUCAL_OK;
+}
+
+int mucal_set_target_window(void *ctx, int32_t sys, int32_t t_lo, int32_t t_hi)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    System &s = c->sys[sys];
+    if (t_lo == 0 && t_hi == 0) {
+        s.target_default = true;
+        return MUCAL_OK;
+    }
+    if (t_lo < s.desc.e_lo || t_hi > s.desc.e_hi || t_lo > t_hi)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "target window must lie inside [%d, %d]", s.desc.e_lo,
+                    s.desc.e_hi);
+    s.target_default = false;
+    s.t_lo = t_lo - s.desc.e_lo;
+    s.t_hi = t_hi - s.desc.e_lo;
+    return MUCAL_OK;
+}
+
+int mucal_get_walker_state(void *ctx, int32_t sys, int32_t walker, uint8_t *occ, int32_t *S, int32_t *E)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    const System &s = c->sys[sys];
+    const SysParams &p = s.p;
+    if (walker < 0 || walker >= p.n_walkers) return fail(c, MUCAL_ERR_INVALID_ARG, "walker out of range");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    std::vector<uint32_t> bits(p.words);
+    std::vector<uint8_t> sraw((size_t)p.V * (p.idx16 ? 2 : 4));
+    int32_t e = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(bits.data(), p.bits + (size_t)walker * p.words, p.words * 4,
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(sraw.data(), (const char *)p.S + (size_t)walker * sraw.size(),
+                                sraw.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&e, p.E + walker, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (occ)
+        for (int i = 0; i < p.V; ++i) occ[i] = (uint8_t)((bits[i >> 5] >> (i & 31)) & 1u);
+    if (S) {
+        for (int i = 0; i < p.V; ++i) {
+            if (p.idx16)
+                S[i] = ((const uint16_t *)sraw.data())[i];
+            else
+                S[i] = (int32_t)((const uint32_t *)sraw.data())[i];
+        }
+    }
+    if (E) *E = e;
+    return MUCAL_OK;
+}
+
+int mucal_get_system_info(void *ctx, int32_t sys, mucal_system_info *info)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    if (!info) return fail(c, MUCAL_ERR_INVALID_ARG, "info is NULL");
+    const System &s = c->sys[sys];
+    info->d = s.p.d;
+    info->L = s.p.L;
+    info->N = s.p.N;
+    info->n_walkers = s.p.n_walkers;
+    info->e_lo = s.desc.e_lo;
+    info->e_hi = s.desc.e_hi;
+    info->V = s.p.V;
+    info->n_bins = s.p.n_bins;
+    info->width = s.p.width;
+    info->index_bytes = s.p.idx16 ? 2 : 4;
+    info->seed_base = s.p.seed_base;
+    return MUCAL_OK;
+}
+
+int mucal_get_stats(void *ctx, int32_t sys, mucal_stats *st)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    if (!st) return fail(c, MUCAL_ERR_INVALID_ARG, "stats is NULL");
+    std::memset(st, 0, sizeof *st);
+    st->walker_launches = c->launches;
+    if (!c->ran) return MUCAL_OK;
+    const System &s = c->sys[sys];
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    std::vector<unsigned long long> acc(s.p.n_walkers);
+    CUDA_TRY(c, cudaMemcpyAsync(acc.data(), s.p.accepts, acc.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (auto v : acc) st->accepts += v;
+    st->attempts = s.last_attempts;
+    float ms = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+    st->kernel_ms = ms;
+    CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_it0, c->ev_it1));
+    st->iteration_ms = ms;
+    return MUCAL_OK;
+}
+
+int mucal_histogram_device_ptr(void *ctx, int32_t sys, void **dptr)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    if (!dptr) return fail(c, MUCAL_ERR_INVALID_ARG, "dptr is NULL");
+    *dptr = c->sys[sys].p.H;
+    return MUCAL_OK;
+}
+
+}  // extern "C"

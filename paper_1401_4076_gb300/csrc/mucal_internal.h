@@ -1,0 +1,60 @@
+// Internal definitions shared by the host driver and the CUDA kernels of
+// libmucal.  Nothing here is part of the public C ABI (include/mucal.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mucal {
+
+// Everything a kernel needs to know about one system (one lattice gas with
+// its walkers), resident in device memory as an array indexed by system.
+struct SysParams {
+    int32_t d, L, N, V;        // dimension, linear size, particles, L^d
+    int32_t L2;                // L*L
+    int32_t e_lo, n_bins;      // energy window [e_lo, e_lo + n_bins - 1]
+    int32_t width;             // 4d + 1 thresholds per bin
+    int32_t words;             // 32-bit words of one occupation bitset, ceil(V/32)
+    int32_t idx16;             // 1: S holds uint16 site indices, 0: uint32
+    int32_t n_walkers;
+    uint32_t magL;             // ceil(2^32 / L): floor(s / L) = umulhi(s, magL) for s*L < 2^32
+    uint64_t seed_base;        // walker w has Philox key seed_base + w
+    uint32_t *bits;            // [n_walkers][words] occupation n_i, bit s%32 of word s/32
+    void *S;                   // [n_walkers][V] particle sites then empty sites
+    int32_t *E;                // [n_walkers] current energy
+    unsigned long long *hist;  // [n_walkers][n_bins] per-walker histogram H_j(E)
+    const uint32_t *thr;       // [n_bins][width] acceptance thresholds
+    unsigned long long *accepts; // [n_walkers] accepted moves in the last iteration
+    unsigned long long *H;     // [n_bins] summed histogram H(E) (Eq. 2)
+};
+
+// One block of the walker-update launch works on walkers
+// [walker0, walker0 + count) of system sys.
+struct BlockWork {
+    int32_t sys;
+    int32_t walker0;
+    int32_t count;
+    int32_t pad;
+};
+
+struct LaunchShape {
+    int kernel;             // MUCAL_KERNEL_THREAD / MUCAL_KERNEL_GROUP
+    int lanes;              // lanes per walker
+    int walkers_per_block;
+    int bits_in_smem;
+    size_t smem_bytes;      // dynamic shared memory per block
+};
+
+// Kernel launchers (walker_kernels.cu).  All are asynchronous on `stream`.
+cudaError_t launch_fill_identity(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
+                                 cudaStream_t stream);
+cudaError_t launch_init_walkers(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
+                                cudaStream_t stream);
+cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
+                                 int n_blocks, const LaunchShape &shape, uint64_t sweeps,
+                                 uint32_t iteration, cudaStream_t stream);
+cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
+                               cudaStream_t stream);
+cudaError_t walker_update_max_smem(int *bytes);
+
+}  // namespace mucal

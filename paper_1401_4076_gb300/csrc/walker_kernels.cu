@@ -1,0 +1,351 @@
+// CUDA kernels of libmucal: initial placement, the walker update of the
+// parallel multicanonical method (Sec. 2) for the lattice gas of Eq. 5, and
+// the device-side histogram sum of Eq. 2.
+//
+// Target: sm_103a (GB300).  The walker update is integer work with a serial
+// dependency per walker (each attempt reads the state the previous accepted
+// attempt wrote), so it is bound by latency and issue slots, not by tensor
+// cores or HBM.  Two kernels are provided:
+//   walker_update_thread: one thread advances one walker;
+//   walker_update_group:  a group of G lanes advances one walker.  The lanes
+//     evaluate G consecutive attempts against the same state, then commit them
+//     in order; after each accepted move the remaining lanes re-evaluate
+//     against the updated state, so the chain is exactly the one-thread chain.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mucal_internal.h"
+
+namespace mucal {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// multiply-high/low on words 0 and 2, high halves xor-ed into words 1 and 3
+// with the round key, key bumped by the Weyl increments after each round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Periodic neighbours of site s on the L^D lattice, s = x + L y (+ L^2 z).
+// Only x (and y in 3D) need a division; the outermost axis wraps by comparing
+// s itself.  floor(s / L) = umulhi(s, ceil(2^32 / L)) holds since s*L < 2^32.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void neighbours(const SysParams &p, uint32_t s, uint32_t (&nb)[2 * D])
+{
+    const uint32_t L = (uint32_t)p.L;
+    const uint32_t V = (uint32_t)p.V;
+    const uint32_t q = __umulhi(s, p.magL);
+    const uint32_t x = s - q * L;
+    nb[0] = (x == 0) ? s + L - 1 : s - 1;
+    nb[1] = (x == L - 1) ? s - (L - 1) : s + 1;
+    if constexpr (D == 2) {
+        nb[2] = (s < L) ? s + (V - L) : s - L;
+        nb[3] = (s >= V - L) ? s - (V - L) : s + L;
+    } else {
+        const uint32_t L2 = (uint32_t)p.L2;
+        const uint32_t q2 = __umulhi(q, p.magL);
+        const uint32_t y = q - q2 * L;
+        nb[2] = (y == 0) ? s + (L2 - L) : s - L;
+        nb[3] = (y == L - 1) ? s - (L2 - L) : s + L;
+        nb[4] = (s < L2) ? s + (V - L2) : s - L2;
+        nb[5] = (s >= V - L2) ? s - (V - L2) : s + L2;
+    }
+}
+
+__device__ __forceinline__ uint32_t occupied(const uint32_t *bits, uint32_t s)
+{
+    return (bits[s >> 5] >> (s & 31u)) & 1u;
+}
+
+// Energy change of moving the particle at a to the empty site b: occupied
+// neighbours of a are lost bonds, occupied neighbours of b other than a are
+// gained bonds; E = -#bonds, so dE = n_a - n_b.
+template <int D>
+__device__ __forceinline__ int jump_delta_e(const SysParams &p, const uint32_t *bits, uint32_t a,
+                                            uint32_t b)
+{
+    uint32_t na[2 * D], nbb[2 * D];
+    neighbours<D>(p, a, na);
+    neighbours<D>(p, b, nbb);
+    int n_a = 0, n_b = 0;
+#pragma unroll
+    for (int i = 0; i < 2 * D; ++i) {
+        n_a += (int)occupied(bits, na[i]);
+        n_b += (int)(occupied(bits, nbb[i]) & (nbb[i] != a ? 1u : 0u));
+    }
+    return n_a - n_b;
+}
+
+template <typename IdxT>
+__device__ __forceinline__ IdxT *walker_S(const SysParams &p, int w)
+{
+    return reinterpret_cast<IdxT *>(p.S) + (size_t)w * (size_t)p.V;
+}
+
+// ---------------------------------------------------------------------------
+// One thread, one walker: A attempts in order.  The histogram is kept as a
+// run length (current bin, count) and added to the walker's histogram only
+// when the energy changes, which records exactly one entry per attempt.
+// ---------------------------------------------------------------------------
+template <int D, typename IdxT>
+__device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, uint64_t A, uint32_t iter)
+{
+    IdxT *S = walker_S<IdxT>(p, w);
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t holes = (uint32_t)(p.V - p.N);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t *thr = p.thr;
+    const int width = p.width;
+    unsigned long long *hist = p.hist + (size_t)w * (size_t)p.n_bins;
+    int bin = p.E[w] - p.e_lo;
+    int row = bin * width + 2 * D;
+    uint32_t run = 0;
+    unsigned long long acc = 0;
+    for (uint64_t t = 0; t < A; ++t) {
+        const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
+        const uint32_t k = __umulhi(r.x, N);
+        const uint32_t m = __umulhi(r.y, holes);
+        const uint32_t a = S[k];
+        const uint32_t b = S[N + m];
+        const int de = jump_delta_e<D>(p, bits, a, b);
+        const uint32_t T = __ldg(thr + row + de);
+        if (T == 0xFFFFFFFFu || r.z < T) {
+            bits[a >> 5] &= ~(1u << (a & 31u));
+            bits[b >> 5] |= (1u << (b & 31u));
+            S[k] = (IdxT)b;
+            S[N + m] = (IdxT)a;
+            ++acc;
+            if (de != 0) {
+                if (run) atomicAdd(hist + bin, (unsigned long long)run);
+                bin += de;
+                row += de * width;
+                run = 0;
+            }
+        }
+        ++run;
+        if (run == 0x80000000u) {
+            atomicAdd(hist + bin, (unsigned long long)run);
+            run = 0;
+        }
+    }
+    if (run) atomicAdd(hist + bin, (unsigned long long)run);
+    p.E[w] = bin + p.e_lo;
+    p.accepts[w] = acc;
+}
+
+template <int D>
+__device__ void chain_thread_dispatch_idx(const SysParams &p, int w, uint32_t *bits, uint64_t A,
+                                          uint32_t iter)
+{
+    if (p.idx16)
+        chain_thread<D, uint16_t>(p, w, bits, A, iter);
+    else
+        chain_thread<D, uint32_t>(p, w, bits, A, iter);
+}
+
+// Copy the bitsets of walkers [w0, w0+count) between global and shared memory
+// (contiguous in both), all threads of the block cooperating.
+__device__ __forceinline__ void block_copy_words(uint32_t *dst, const uint32_t *src, size_t n)
+{
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+__global__ void __launch_bounds__(1024)
+walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
+                     uint64_t sweeps, uint32_t iter, int bits_in_smem)
+{
+    extern __shared__ uint32_t smem_bits[];
+    const BlockWork wk = work[blockIdx.x];
+    const SysParams &p = sys[wk.sys];
+    const int lw = threadIdx.x;
+    const size_t block_words = (size_t)wk.count * (size_t)p.words;
+    uint32_t *gbits = p.bits + (size_t)wk.walker0 * (size_t)p.words;
+    if (bits_in_smem) {
+        block_copy_words(smem_bits, gbits, block_words);
+        __syncthreads();
+    }
+    if (lw < wk.count) {
+        const int w = wk.walker0 + lw;
+        uint32_t *bits = bits_in_smem ? smem_bits + (size_t)lw * p.words
+                                      : gbits + (size_t)lw * p.words;
+        const uint64_t A = sweeps * (uint64_t)p.N;
+        if (p.d == 2)
+            chain_thread_dispatch_idx<2>(p, w, bits, A, iter);
+        else
+            chain_thread_dispatch_idx<3>(p, w, bits, A, iter);
+    }
+    if (bits_in_smem) {
+        __syncthreads();
+        block_copy_words(gbits, smem_bits, block_words);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial placement.
+// ---------------------------------------------------------------------------
+template <typename IdxT>
+__global__ void fill_identity(SysParams p)
+{
+    const size_t total = (size_t)p.n_walkers * (size_t)p.V;
+    IdxT *S = reinterpret_cast<IdxT *>(p.S);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x)
+        S[i] = (IdxT)(i % (size_t)p.V);
+}
+
+// Partial Fisher-Yates from the init stream (counter (j/4 lo, j/4 hi, 0, 1),
+// word j%4), then the bitset and a full energy count over the particles,
+// looking in the +1 direction of every axis so each bond counts once.
+template <int D, typename IdxT>
+__device__ void init_one(const SysParams &p, int w)
+{
+    IdxT *S = walker_S<IdxT>(p, w);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t V = (uint32_t)p.V;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    for (uint32_t j = 0; j < (uint32_t)p.N; ++j) {
+        if ((j & 3u) == 0) r = philox10(make_uint4(j >> 2, 0u, 0u, 1u), k0, k1);
+        const uint32_t word = (j & 3u) == 0 ? r.x : (j & 3u) == 1 ? r.y : (j & 3u) == 2 ? r.z : r.w;
+        const uint32_t idx = j + __umulhi(word, V - j);
+        const IdxT tmp = S[j];
+        S[j] = S[idx];
+        S[idx] = tmp;
+    }
+    uint32_t *bits = p.bits + (size_t)w * (size_t)p.words;
+    for (uint32_t j = 0; j < (uint32_t)p.N; ++j) {
+        const uint32_t s = S[j];
+        bits[s >> 5] |= 1u << (s & 31u);
+    }
+    int pairs = 0;
+    for (uint32_t j = 0; j < (uint32_t)p.N; ++j) {
+        uint32_t nb[2 * D];
+        neighbours<D>(p, (uint32_t)S[j], nb);
+#pragma unroll
+        for (int k = 0; k < D; ++k) pairs += (int)occupied(bits, nb[2 * k + 1]);
+    }
+    p.E[w] = -pairs;
+}
+
+__global__ void init_walkers_kernel(const SysParams *__restrict__ sys, int s)
+{
+    const SysParams &p = sys[s];
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= p.n_walkers) return;
+    if (p.d == 2) {
+        if (p.idx16) init_one<2, uint16_t>(p, w); else init_one<2, uint32_t>(p, w);
+    } else {
+        if (p.idx16) init_one<3, uint16_t>(p, w); else init_one<3, uint32_t>(p, w);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// H(E) = sum_j H_j(E) (Eq. 2).  Block (x: 256 bins, y: a chunk of walkers);
+// each thread sums its bin over the chunk (coalesced across the bins) and
+// adds the partial sum to H with one 64-bit atomic.
+// ---------------------------------------------------------------------------
+constexpr int kReduceWalkers = 64;
+
+__global__ void hist_reduce_kernel(SysParams p)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.n_bins) return;
+    const int w0 = blockIdx.y * kReduceWalkers;
+    const int w1 = min(w0 + kReduceWalkers, p.n_walkers);
+    unsigned long long sum = 0;
+    const unsigned long long *h = p.hist + (size_t)w0 * (size_t)p.n_bins + b;
+    for (int w = w0; w < w1; ++w, h += p.n_bins) sum += *h;
+    if (sum) atomicAdd(p.H + b, sum);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+cudaError_t launch_fill_identity(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
+                                 cudaStream_t stream)
+{
+    (void)dev_sys;
+    for (int s = 0; s < n_sys; ++s) {
+        const SysParams &p = host_sys[s];
+        const size_t total = (size_t)p.n_walkers * (size_t)p.V;
+        const int threads = 256;
+        size_t blocks = (total + threads - 1) / threads;
+        if (blocks > 65536) blocks = 65536;
+        if (p.idx16)
+            fill_identity<uint16_t><<<(unsigned)blocks, threads, 0, stream>>>(p);
+        else
+            fill_identity<uint32_t><<<(unsigned)blocks, threads, 0, stream>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_init_walkers(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
+                                cudaStream_t stream)
+{
+    for (int s = 0; s < n_sys; ++s) {
+        const int threads = 128;
+        const int blocks = (host_sys[s].n_walkers + threads - 1) / threads;
+        init_walkers_kernel<<<blocks, threads, 0, stream>>>(dev_sys, s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t walker_update_max_smem(int *bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(walker_update_thread, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                *bytes);
+}
+
+cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
+                                 int n_blocks, const LaunchShape &shape, uint64_t sweeps,
+                                 uint32_t iteration, cudaStream_t stream)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    const int threads = shape.walkers_per_block * shape.lanes;
+    walker_update_thread<<<n_blocks, threads, shape.smem_bytes, stream>>>(
+        dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
+                               cudaStream_t stream)
+{
+    (void)dev_sys;
+    for (int s = 0; s < n_sys; ++s) {
+        const SysParams &p = host_sys[s];
+        dim3 grid((p.n_bins + 255) / 256, (p.n_walkers + kReduceWalkers - 1) / kReduceWalkers);
+        hist_reduce_kernel<<<grid, 256, 0, stream>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace mucal

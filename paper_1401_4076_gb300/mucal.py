@@ -1,0 +1,315 @@
+"""Python binding of libmucal (ctypes, argument marshalling only).
+
+The functions carry the names of the C ABI in ``include/mucal.h``; every step
+of the simulation runs inside the library (CUDA kernels and its host-side
+double-precision weight update).  There is no CPU fallback: loading fails
+loudly if the compiled library is missing, and ``mucal_init_systems`` raises
+if no CUDA device is usable.
+
+``Mucal`` is a small convenience wrapper holding one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libmucal.so")
+
+MUCAL_OK = 0
+MUCAL_ERR_INVALID_ARG = -1
+MUCAL_ERR_CUDA = -2
+MUCAL_ERR_OOM = -3
+MUCAL_ERR_NO_DEVICE = -4
+MUCAL_ERR_NOT_READY = -5
+MUCAL_ERR_STATE = -6
+MUCAL_FLAG_PER_WALKER_HIST = 0x1
+MUCAL_SCHEME_SIMPLE = 0
+MUCAL_SCHEME_RECURSIVE = 1
+MUCAL_KERNEL_THREAD = 0
+MUCAL_KERNEL_GROUP = 1
+
+EXPORTED = [
+    "mucal_init_systems", "mucal_destroy", "mucal_last_error", "mucal_set_weights",
+    "mucal_get_weights", "mucal_get_thresholds", "mucal_set_launch_config",
+    "mucal_get_launch_config", "mucal_run_iteration", "mucal_get_histogram",
+    "mucal_update_weights", "mucal_set_target_window", "mucal_get_walker_state",
+    "mucal_get_system_info", "mucal_get_stats", "mucal_histogram_device_ptr", "mucal_version",
+]
+
+
+class mucal_system_desc(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("L", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("n_walkers", ctypes.c_int32), ("e_lo", ctypes.c_int32), ("e_hi", ctypes.c_int32),
+                ("seed_base", ctypes.c_uint64)]
+
+
+class mucal_launch_config(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
+                ("walkers_per_block", ctypes.c_int32), ("bits_in_smem", ctypes.c_int32)]
+
+
+class mucal_system_info(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("L", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("n_walkers", ctypes.c_int32), ("e_lo", ctypes.c_int32), ("e_hi", ctypes.c_int32),
+                ("V", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("index_bytes", ctypes.c_int32), ("seed_base", ctypes.c_uint64)]
+
+
+class mucal_stats(ctypes.Structure):
+    _fields_ = [("attempts", ctypes.c_uint64), ("accepts", ctypes.c_uint64),
+                ("kernel_ms", ctypes.c_double), ("iteration_ms", ctypes.c_double),
+                ("walker_launches", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmucal.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmucal.so not found at {path}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "mucal_init_systems": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(mucal_system_desc),
+                                              I32, P, U32]),
+        "mucal_destroy": (None, [P]),
+        "mucal_last_error": (ctypes.c_char_p, [P]),
+        "mucal_set_weights": (ctypes.c_int, [P, I32, P, I32]),
+        "mucal_get_weights": (ctypes.c_int, [P, I32, P, I32]),
+        "mucal_get_thresholds": (ctypes.c_int, [P, I32, P, I64]),
+        "mucal_set_launch_config": (ctypes.c_int, [P, ctypes.POINTER(mucal_launch_config)]),
+        "mucal_get_launch_config": (ctypes.c_int, [P, ctypes.POINTER(mucal_launch_config)]),
+        "mucal_run_iteration": (ctypes.c_int, [P, I64, U32]),
+        "mucal_get_histogram": (ctypes.c_int, [P, I32, P, I32, P]),
+        "mucal_update_weights": (ctypes.c_int, [P, I32, I32, P, P]),
+        "mucal_set_target_window": (ctypes.c_int, [P, I32, I32, I32]),
+        "mucal_get_walker_state": (ctypes.c_int, [P, I32, I32, P, P, P]),
+        "mucal_get_system_info": (ctypes.c_int, [P, I32, ctypes.POINTER(mucal_system_info)]),
+        "mucal_get_stats": (ctypes.c_int, [P, I32, ctypes.POINTER(mucal_stats)]),
+        "mucal_histogram_device_ptr": (ctypes.c_int, [P, I32, ctypes.POINTER(P)]),
+        "mucal_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MucalError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mucal error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, ctx=None):
+    if rc != MUCAL_OK:
+        msg = load_library().mucal_last_error(ctx)
+        raise MucalError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# --------------------------------------------------------------------------
+# C ABI, one function per export (same names, numpy arrays for buffers).
+# --------------------------------------------------------------------------
+
+def mucal_init_systems(systems, cuda_stream=None, flags=0):
+    """systems: list of dicts/tuples (d, L, N, n_walkers, e_lo, e_hi, seed_base)."""
+    lib = load_library()
+    arr = (mucal_system_desc * len(systems))()
+    for i, s in enumerate(systems):
+        if isinstance(s, dict):
+            s = (s["d"], s["L"], s["N"], s["n_walkers"], s.get("e_lo", 0), s.get("e_hi", 0),
+                 s.get("seed_base", 0))
+        arr[i] = mucal_system_desc(*s)
+    ctx = ctypes.c_void_p()
+    rc = lib.mucal_init_systems(ctypes.byref(ctx), arr, len(systems), cuda_stream, flags)
+    _check(rc, None)
+    return ctx
+
+
+def mucal_destroy(ctx):
+    load_library().mucal_destroy(ctx)
+
+
+def mucal_last_error(ctx):
+    m = load_library().mucal_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def mucal_set_weights(ctx, sys, lnW):
+    w = np.ascontiguousarray(lnW, dtype=np.float64)
+    _check(load_library().mucal_set_weights(ctx, sys, _ptr(w), w.size), ctx)
+
+
+def mucal_get_weights(ctx, sys, n_bins):
+    out = np.zeros(n_bins, dtype=np.float64)
+    _check(load_library().mucal_get_weights(ctx, sys, _ptr(out), n_bins), ctx)
+    return out
+
+
+def mucal_get_thresholds(ctx, sys, n_bins, width):
+    T = np.zeros((n_bins, width), dtype=np.uint32)
+    _check(load_library().mucal_get_thresholds(ctx, sys, _ptr(T), T.size), ctx)
+    return T
+
+
+def mucal_set_launch_config(ctx, kernel=MUCAL_KERNEL_THREAD, lanes_per_walker=1,
+                            walkers_per_block=32, bits_in_smem=1):
+    cfg = mucal_launch_config(kernel, lanes_per_walker, walkers_per_block, bits_in_smem)
+    _check(load_library().mucal_set_launch_config(ctx, ctypes.byref(cfg)), ctx)
+
+
+def mucal_get_launch_config(ctx):
+    cfg = mucal_launch_config()
+    _check(load_library().mucal_get_launch_config(ctx, ctypes.byref(cfg)), ctx)
+    return {"kernel": cfg.kernel, "lanes_per_walker": cfg.lanes_per_walker,
+            "walkers_per_block": cfg.walkers_per_block, "bits_in_smem": cfg.bits_in_smem}
+
+
+def mucal_run_iteration(ctx, sweeps, iteration):
+    _check(load_library().mucal_run_iteration(ctx, int(sweeps), int(iteration) & 0xFFFFFFFF), ctx)
+
+
+def mucal_get_histogram(ctx, sys, n_bins, per_walker_shape=None):
+    H = np.zeros(n_bins, dtype=np.int64)
+    pw = None if per_walker_shape is None else np.zeros(per_walker_shape, dtype=np.int64)
+    _check(load_library().mucal_get_histogram(ctx, sys, _ptr(H), n_bins, _ptr(pw)), ctx)
+    return H if pw is None else (H, pw)
+
+
+def mucal_update_weights(ctx, sys, scheme, n_bins):
+    lnW = np.zeros(n_bins, dtype=np.float64)
+    f = ctypes.c_double()
+    _check(load_library().mucal_update_weights(ctx, sys, scheme, _ptr(lnW), ctypes.addressof(f)),
+           ctx)
+    return lnW, f.value
+
+
+def mucal_set_target_window(ctx, sys, t_lo, t_hi):
+    _check(load_library().mucal_set_target_window(ctx, sys, t_lo, t_hi), ctx)
+
+
+def mucal_get_walker_state(ctx, sys, walker, V):
+    occ = np.zeros(V, dtype=np.uint8)
+    S = np.zeros(V, dtype=np.int32)
+    E = ctypes.c_int32()
+    _check(load_library().mucal_get_walker_state(ctx, sys, walker, _ptr(occ), _ptr(S),
+                                                  ctypes.addressof(E)), ctx)
+    return occ, S, E.value
+
+
+def mucal_get_system_info(ctx, sys):
+    info = mucal_system_info()
+    _check(load_library().mucal_get_system_info(ctx, sys, ctypes.byref(info)), ctx)
+    return {f: getattr(info, f) for f, _ in mucal_system_info._fields_}
+
+
+def mucal_get_stats(ctx, sys):
+    st = mucal_stats()
+    _check(load_library().mucal_get_stats(ctx, sys, ctypes.byref(st)), ctx)
+    return {f: getattr(st, f) for f, _ in mucal_stats._fields_}
+
+
+def mucal_histogram_device_ptr(ctx, sys):
+    p = ctypes.c_void_p()
+    _check(load_library().mucal_histogram_device_ptr(ctx, sys, ctypes.byref(p)), ctx)
+    return p.value
+
+
+def mucal_version():
+    return load_library().mucal_version().decode()
+
+
+# --------------------------------------------------------------------------
+# Convenience wrapper.
+# --------------------------------------------------------------------------
+
+@dataclass
+class SystemDesc:
+    d: int
+    L: int
+    N: int
+    n_walkers: int
+    e_lo: int = 0
+    e_hi: int = 0
+    seed_base: int = 0
+
+    def as_tuple(self):
+        return (self.d, self.L, self.N, self.n_walkers, self.e_lo, self.e_hi, self.seed_base)
+
+
+class Mucal:
+    """One library context over several systems, with numpy-returning helpers."""
+
+    def __init__(self, systems, cuda_stream=None, per_walker_hist=False):
+        descs = [s.as_tuple() if isinstance(s, SystemDesc) else s for s in systems]
+        flags = MUCAL_FLAG_PER_WALKER_HIST if per_walker_hist else 0
+        self.ctx = mucal_init_systems(descs, cuda_stream, flags)
+        self.info = [mucal_get_system_info(self.ctx, i) for i in range(len(descs))]
+
+    def close(self):
+        if self.ctx is not None:
+            mucal_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_weights(self, sys, lnW):
+        mucal_set_weights(self.ctx, sys, lnW)
+
+    def weights(self, sys):
+        return mucal_get_weights(self.ctx, sys, self.info[sys]["n_bins"])
+
+    def thresholds(self, sys):
+        i = self.info[sys]
+        return mucal_get_thresholds(self.ctx, sys, i["n_bins"], i["width"])
+
+    def set_launch(self, **kw):
+        mucal_set_launch_config(self.ctx, **kw)
+
+    def launch(self):
+        return mucal_get_launch_config(self.ctx)
+
+    def run_iteration(self, sweeps, iteration):
+        mucal_run_iteration(self.ctx, sweeps, iteration)
+
+    def histogram(self, sys, per_walker=False):
+        i = self.info[sys]
+        shape = (i["n_walkers"], i["n_bins"]) if per_walker else None
+        return mucal_get_histogram(self.ctx, sys, i["n_bins"], shape)
+
+    def update_weights(self, sys, scheme=MUCAL_SCHEME_RECURSIVE):
+        return mucal_update_weights(self.ctx, sys, scheme, self.info[sys]["n_bins"])
+
+    def set_target_window(self, sys, t_lo, t_hi):
+        mucal_set_target_window(self.ctx, sys, t_lo, t_hi)
+
+    def walker_state(self, sys, walker):
+        return mucal_get_walker_state(self.ctx, sys, walker, self.info[sys]["V"])
+
+    def stats(self, sys=0):
+        return mucal_get_stats(self.ctx, sys)

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+Integer work (placement, thresholds, walker chains, histograms) must be
+bit-exact; the float64 weight iteration must agree to 1e-12 relative.  Small
+systems are compared in full (every walker, every iteration); the large
+workloads in the launch configuration the benchmark times are compared on
+sampled walkers, whose final states and histograms the oracle computes one by
+one, and through invariants that hold at any size.
+"""
+import numpy as np
+import pytest
+
+from oracle import chain
+from oracle.recursion import recursive_update, simple_update
+from paper_1401_4076_gb300 import mucal as m
+from paper_1401_4076_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1401_4076_gb300 import _build_ext
+    _build_ext.build_library()
+    m.load_library()
+
+
+def _window(d, N, e_lo, e_hi):
+    return (-d * N, 0) if (e_lo == 0 and e_hi == 0) else (e_lo, e_hi)
+
+
+def _oracle_states(d, L, N, walkers, seed_base, pick=None):
+    S, occ, E = chain.init_walkers(d, L, N, walkers, seed_base)
+    if pick is not None:
+        S, occ, E = S[pick].copy(), occ[pick].copy(), E[pick].copy()
+    return S, occ, E
+
+
+def _assert_walker_equal(mc, sys, w, S, occ, E):
+    g_occ, g_S, g_E = mc.walker_state(sys, w)
+    np.testing.assert_array_equal(g_occ, occ)
+    np.testing.assert_array_equal(g_S, S)
+    assert g_E == E
+
+
+def _rel_close(a, b, rtol=1e-12):
+    scale = max(1.0, float(np.abs(b).max()))
+    np.testing.assert_allclose(a, b, rtol=rtol, atol=rtol * scale)
+
+
+# --------------------------------------------------------------- placement --
+
+@pytest.mark.parametrize("desc", [
+    (2, 16, 32, 64, 0, 0, 0),       # small 2D, uint16 lists
+    (3, 8, 50, 37, 0, 0, 1000),     # ragged walker count
+    (2, 257, 300, 3, 0, 0, 5),      # V = 66049 > 65536: uint32 lists
+    (3, 5, 124, 4, 0, 0, 9),        # N = V - 1
+    (2, 3, 1, 5, 0, 0, 77),         # L = 3, N = 1
+])
+def test_initial_placement_bit_exact(desc):
+    d, L, N, W, lo, hi, seed = desc
+    with m.Mucal([desc]) as mc:
+        S, occ, E = _oracle_states(d, L, N, W, seed)
+        for w in range(W):
+            _assert_walker_equal(mc, 0, w, S[w], occ[w], E[w])
+
+
+# -------------------------------------------------------------- thresholds --
+
+@pytest.mark.parametrize("d,N", [(2, 32), (3, 100)])
+def test_threshold_table_bit_exact(d, N):
+    L = 16 if d == 2 else 10
+    with m.Mucal([(d, L, N, 2, 0, 0, 0)]) as mc:
+        nb = d * N + 1
+        for seed in range(3):
+            lnW = workloads.random_log_weights(nb, seed, scale=0.4)
+            mc.set_weights(0, lnW)
+            np.testing.assert_array_equal(mc.thresholds(0), chain.thresholds(d, -d * N, 0, lnW))
+
+
+# ------------------------------------------------- full small-case parity --
+
+@pytest.mark.parametrize("launch", [
+    dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=32, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=7, bits_in_smem=0),
+])
+def test_small_2d_ten_iterations_bit_exact(launch):
+    """2D L=16, N=32, 64 walkers, seeds 0..63, lnW=0 start, 10 iterations of
+    2000 sweeps with the recursive update: every per-walker histogram of every
+    iteration bit-exact, weights within 1e-12, thresholds bit-exact."""
+    wl = workloads.SMALL_2D
+    d, L, N, W, lo, hi, seed = wl.systems[0]
+    e_lo, e_hi = _window(d, N, lo, hi)
+    nb = e_hi - e_lo + 1
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    lnW = np.zeros(nb)
+    s_cum = np.zeros(nb, bool)
+    phat = np.zeros(nb)
+    with m.Mucal(wl.systems, per_walker_hist=True) as mc:
+        mc.set_launch(**launch)
+        for it in range(wl.iterations):
+            T = chain.thresholds(d, e_lo, e_hi, lnW)
+            np.testing.assert_array_equal(mc.thresholds(0), T)
+            mc.run_iteration(wl.sweeps, it)
+            hist, _ = chain.run_walkers(d, L, N, seed, it, wl.sweeps * N, e_lo, e_hi, T, S, occ, E)
+            H, per = mc.histogram(0, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+            np.testing.assert_array_equal(H, hist.sum(axis=0))
+            g_lnW, flat = mc.update_weights(0, m.MUCAL_SCHEME_RECURSIVE)
+            lnW, s_cum, phat = recursive_update(lnW, hist.sum(axis=0), s_cum, phat)
+            _rel_close(g_lnW, lnW)
+        for w in (0, 31, 63):
+            _assert_walker_equal(mc, 0, w, S[w], occ[w], E[w])
+        st = mc.stats(0)
+        assert st["attempts"] == W * wl.sweeps * N
+
+
+def test_simple_scheme_matches_oracle():
+    d, L, N, W = 2, 12, 20, 16
+    with m.Mucal([(d, L, N, W, 0, 0, 3)]) as mc:
+        nb = d * N + 1
+        lnW = np.zeros(nb)
+        for it in range(4):
+            mc.run_iteration(50, it)
+            H = mc.histogram(0)
+            g, _ = mc.update_weights(0, m.MUCAL_SCHEME_SIMPLE)
+            lnW = simple_update(lnW, H)
+            _rel_close(g, lnW)
+
+
+# ---------------------------------------------------------- edge cases ------
+
+@pytest.mark.parametrize("desc,sweeps", [
+    ((3, 6, 40, 37, 0, 0, 11), 30),          # 3D, ragged walker count
+    ((2, 3, 1, 5, 0, 0, 77), 200),           # single particle on 3x3
+    ((3, 5, 124, 4, 0, 0, 9), 20),           # N = V - 1: one hole
+    ((2, 257, 300, 2, 0, 0, 5), 3),          # uint32 site lists
+    ((3, 4, 20, 8, -30, -2, 0), 40),         # user window (checked to hold the start)
+])
+def test_edge_cases_bit_exact(desc, sweeps):
+    d, L, N, W, lo, hi, seed = desc
+    e_lo, e_hi = _window(d, N, lo, hi)
+    nb = e_hi - e_lo + 1
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    if lo or hi:
+        if not ((E >= e_lo) & (E <= e_hi)).all():
+            with pytest.raises(m.MucalError):
+                m.Mucal([desc])
+            return
+    lnW = workloads.random_log_weights(nb, 1, scale=0.5)
+    with m.Mucal([desc], per_walker_hist=True) as mc:
+        mc.set_weights(0, lnW)
+        T = chain.thresholds(d, e_lo, e_hi, lnW)
+        for it in range(2):
+            mc.run_iteration(sweeps, it)
+            hist, _ = chain.run_walkers(d, L, N, seed, it, sweeps * N, e_lo, e_hi, T, S, occ, E)
+            _, per = mc.histogram(0, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+        for w in range(W):
+            _assert_walker_equal(mc, 0, w, S[w], occ[w], E[w])
+
+
+def test_window_boundary_is_never_crossed():
+    """A narrow window around the start: moves leaving it are rejected (T = 0)."""
+    d, L, N, W, seed = 2, 10, 30, 16, 4
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    e_lo, e_hi = int(E.min()) - 2, int(E.max()) + 2
+    e_hi = min(e_hi, 0)
+    desc = (d, L, N, W, e_lo, e_hi, seed)
+    T = chain.thresholds(d, e_lo, e_hi, np.zeros(e_hi - e_lo + 1))
+    with m.Mucal([desc], per_walker_hist=True) as mc:
+        mc.run_iteration(100, 0)
+        _, per = mc.histogram(0, per_walker=True)
+    hist, _ = chain.run_walkers(d, L, N, seed, 0, 100 * N, e_lo, e_hi, T, S, occ, E)
+    np.testing.assert_array_equal(per, hist)
+    assert per[:, 0].sum() > 0 or per[:, -1].sum() > 0
+
+
+# ------------------------------------------------ several systems, one launch
+
+def test_multi_system_launch_bit_exact():
+    systems = [(2, 16, 32, 40, 0, 0, 0), (3, 8, 60, 25, 0, 0, 500), (2, 24, 50, 33, 0, 0, 900)]
+    with m.Mucal(systems, per_walker_hist=True) as mc:
+        mc.set_launch(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=16,
+                      bits_in_smem=1)
+        lnWs = []
+        for i, (d, L, N, W, lo, hi, seed) in enumerate(systems):
+            lnW = workloads.random_log_weights(d * N + 1, 10 + i, scale=0.3)
+            mc.set_weights(i, lnW)
+            lnWs.append(lnW)
+        mc.run_iteration(25, 3)
+        for i, (d, L, N, W, lo, hi, seed) in enumerate(systems):
+            S, occ, E = _oracle_states(d, L, N, W, seed)
+            T = chain.thresholds(d, -d * N, 0, lnWs[i])
+            hist, _ = chain.run_walkers(d, L, N, seed, 3, 25 * N, -d * N, 0, T, S, occ, E)
+            H, per = mc.histogram(i, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+            np.testing.assert_array_equal(H, hist.sum(axis=0))
+
+
+# -------------------------------------------- full-size, sampled walkers ----
+
+def _sampled_full_size(wl, sweeps, pick, launch=None, lnW_seed=None):
+    d, L, N, W, lo, hi, seed = wl.systems[0]
+    e_lo, e_hi = _window(d, N, lo, hi)
+    nb = e_hi - e_lo + 1
+    lnW = np.zeros(nb) if lnW_seed is None else workloads.random_log_weights(nb, lnW_seed, 0.05)
+    with m.Mucal(wl.systems, per_walker_hist=True) as mc:
+        if launch:
+            mc.set_launch(**launch)
+        mc.set_weights(0, lnW)
+        mc.run_iteration(sweeps, 0)
+        H, per = mc.histogram(0, per_walker=True)
+        assert H.sum() == W * sweeps * N
+        np.testing.assert_array_equal(H, per.sum(axis=0))
+        S, occ, E = _oracle_states(d, L, N, W, seed, pick)
+        T = chain.thresholds(d, e_lo, e_hi, lnW)
+        hist, _ = chain.run_walkers(d, L, N, seed, 0, sweeps * N, e_lo, e_hi, T, S, occ, E,
+                                    walkers=pick)
+        np.testing.assert_array_equal(per[pick], hist)
+        for i, w in enumerate(pick):
+            _assert_walker_equal(mc, 0, w, S[i], occ[i], E[i])
+
+
+def test_medium_2d_first_iteration_sampled():
+    """2D L=64, N=410, 4096 walkers, first iteration (lnW = 0) at full size."""
+    _sampled_full_size(workloads.MEDIUM_2D, workloads.MEDIUM_2D.sweeps, [0, 1, 777, 2048, 4095])
+
+
+def test_large_3d_first_iteration_sampled():
+    """3D L=32, N=3277, 8192 walkers, one iteration with non-trivial weights."""
+    _sampled_full_size(workloads.LARGE_3D, 20, [0, 4097, 8191], lnW_seed=3)
