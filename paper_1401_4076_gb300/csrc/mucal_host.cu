@@ -295,9 +295,17 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     sh.lanes = cfg.lanes_per_walker;
     sh.walkers_per_block = cfg.walkers_per_block;
     sh.bits_in_smem = cfg.bits_in_smem ? 1 : 0;
-    if (sh.kernel != MUCAL_KERNEL_THREAD)
-        return fail(c, MUCAL_ERR_INVALID_ARG, "kernel %d is not available", sh.kernel);
-    if (sh.lanes != 1) return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
+    if (sh.kernel == MUCAL_KERNEL_THREAD) {
+        if (sh.lanes != 1)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
+    } else if (sh.kernel == MUCAL_KERNEL_GROUP) {
+        if (sh.lanes != 2 && sh.lanes != 4 && sh.lanes != 8 && sh.lanes != 16 && sh.lanes != 32)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel needs lanes_per_walker in {2,4,8,16,32}");
+        if ((sh.walkers_per_block * sh.lanes) % 32 != 0)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel needs whole warps per block");
+    } else {
+        return fail(c, MUCAL_ERR_INVALID_ARG, "unknown kernel %d", sh.kernel);
+    }
     if (sh.walkers_per_block < 1 || sh.walkers_per_block * sh.lanes > 1024)
         return fail(c, MUCAL_ERR_INVALID_ARG, "walkers_per_block * lanes must be in [1, 1024]");
     size_t smem = 0;

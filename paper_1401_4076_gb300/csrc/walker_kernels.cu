@@ -197,6 +197,141 @@ walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restr
 }
 
 // ---------------------------------------------------------------------------
+// G lanes per walker (G divides 32).  Lane j of a group owns attempt t0 + j of
+// the current batch: it draws its random numbers and reads its particle and
+// empty site once, then every round evaluates dE and the acceptance against
+// the walker's current state.  The first accepting lane f commits; lanes
+// before it were rejected by that same state, lanes after it re-evaluate in
+// the next round (their list entries are patched in registers when the commit
+// touched the same list slot).  The warp's groups step through the rounds in
+// lock-step so that no group's path diverges from the others'.
+// ---------------------------------------------------------------------------
+template <int D, typename IdxT, int G>
+__device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits, uint64_t A,
+                            uint32_t iter)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (G - 1);
+    const int gbase = lane - j;
+    IdxT *S = active ? walker_S<IdxT>(p, w) : nullptr;
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t holes = (uint32_t)(p.V - p.N);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t *thr = p.thr;
+    const int width = p.width;
+    unsigned long long *hist = active ? p.hist + (size_t)w * (size_t)p.n_bins : nullptr;
+    int bin = active ? p.E[w] - p.e_lo : 0;
+    uint32_t run = 0;
+    unsigned long long acc = 0;
+    for (uint64_t t0 = 0; t0 < A; t0 += G) {
+        const uint64_t t = t0 + (uint64_t)j;
+        const int n_valid = (int)((A - t0) < (uint64_t)G ? (A - t0) : (uint64_t)G);
+        const bool valid = active && (j < n_valid);
+        uint32_t k = 0, m = 0, a = 0, b = 0, r2 = 0;
+        if (valid) {
+            const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
+            k = __umulhi(r.x, N);
+            m = __umulhi(r.y, holes);
+            r2 = r.z;
+            a = S[k];
+            b = S[N + m];
+        }
+        int pos = 0;
+        bool done = !active;
+        while (__any_sync(FULL, !done)) {
+            bool accept = false;
+            int de = 0;
+            if (!done && valid && j >= pos) {
+                de = jump_delta_e<D>(p, bits, a, b);
+                const uint32_t T = __ldg(thr + bin * width + 2 * D + de);
+                accept = (T == 0xFFFFFFFFu) || (r2 < T);
+            }
+            const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
+            const int f = bal ? __ffs(bal) - 1 : G;
+            const int src = gbase + (f < G ? f : 0);
+            const int de_f = __shfl_sync(FULL, de, src);
+            const uint32_t a_f = __shfl_sync(FULL, a, src);
+            const uint32_t b_f = __shfl_sync(FULL, b, src);
+            const uint32_t k_f = __shfl_sync(FULL, k, src);
+            const uint32_t m_f = __shfl_sync(FULL, m, src);
+            if (!done) {
+                if (f < G) {
+                    run += (uint32_t)(f - pos);      // rejected at the current energy
+                    if (j == f) {
+                        bits[a_f >> 5] &= ~(1u << (a_f & 31u));
+                        bits[b_f >> 5] |= 1u << (b_f & 31u);
+                        S[k_f] = (IdxT)b_f;
+                        S[N + m_f] = (IdxT)a_f;
+                    }
+                    ++acc;
+                    if (de_f != 0) {
+                        if (j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
+                        bin += de_f;
+                        run = 0;
+                    }
+                    run += 1;
+                    if (j > f) {
+                        if (k == k_f) a = b_f;
+                        if (m == m_f) b = a_f;
+                    }
+                    pos = f + 1;
+                    if (pos >= n_valid) done = true;
+                } else {
+                    run += (uint32_t)(n_valid - pos);
+                    done = true;
+                }
+            }
+            __syncwarp(FULL);
+        }
+        if (run >= 0x40000000u) {
+            if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)run);
+            run = 0;
+        }
+    }
+    if (active && j == 0) {
+        if (run) atomicAdd(hist + bin, (unsigned long long)run);
+        p.E[w] = bin + p.e_lo;
+        p.accepts[w] = acc;
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(1024)
+walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
+                    uint64_t sweeps, uint32_t iter, int bits_in_smem)
+{
+    extern __shared__ uint32_t smem_bits[];
+    const BlockWork wk = work[blockIdx.x];
+    const SysParams &p = sys[wk.sys];
+    const int lw = threadIdx.x / G;
+    const size_t block_words = (size_t)wk.count * (size_t)p.words;
+    uint32_t *gbits = p.bits + (size_t)wk.walker0 * (size_t)p.words;
+    if (bits_in_smem) {
+        block_copy_words(smem_bits, gbits, block_words);
+        __syncthreads();
+    }
+    const bool active = lw < wk.count;
+    const int w = wk.walker0 + (active ? lw : 0);
+    uint32_t *bits = bits_in_smem ? smem_bits + (size_t)(active ? lw : 0) * p.words
+                                  : gbits + (size_t)(active ? lw : 0) * p.words;
+    const uint64_t A = sweeps * (uint64_t)p.N;
+    if (p.d == 2) {
+        if (p.idx16) chain_group<2, uint16_t, G>(p, w, active, bits, A, iter);
+        else chain_group<2, uint32_t, G>(p, w, active, bits, A, iter);
+    } else {
+        if (p.idx16) chain_group<3, uint16_t, G>(p, w, active, bits, A, iter);
+        else chain_group<3, uint32_t, G>(p, w, active, bits, A, iter);
+    }
+    if (bits_in_smem) {
+        __syncthreads();
+        block_copy_words(gbits, smem_bits, block_words);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Initial placement.
 // ---------------------------------------------------------------------------
 template <typename IdxT>
@@ -319,8 +454,14 @@ cudaError_t walker_update_max_smem(int *bytes)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(walker_update_thread, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                *bytes);
+    const void *fns[] = {(const void *)walker_update_thread, (const void *)walker_update_group<2>,
+                         (const void *)walker_update_group<4>, (const void *)walker_update_group<8>,
+                         (const void *)walker_update_group<16>, (const void *)walker_update_group<32>};
+    for (const void *fn : fns) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, *bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
@@ -329,8 +470,35 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
 {
     if (n_blocks <= 0) return cudaSuccess;
     const int threads = shape.walkers_per_block * shape.lanes;
-    walker_update_thread<<<n_blocks, threads, shape.smem_bytes, stream>>>(
-        dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+    if (shape.kernel == 0) {
+        walker_update_thread<<<n_blocks, threads, shape.smem_bytes, stream>>>(
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+        return cudaGetLastError();
+    }
+    switch (shape.lanes) {
+    case 2:
+        walker_update_group<2><<<n_blocks, threads, shape.smem_bytes, stream>>>(
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+        break;
+    case 4:
+        walker_update_group<4><<<n_blocks, threads, shape.smem_bytes, stream>>>(
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+        break;
+    case 8:
+        walker_update_group<8><<<n_blocks, threads, shape.smem_bytes, stream>>>(
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+        break;
+    case 16:
+        walker_update_group<16><<<n_blocks, threads, shape.smem_bytes, stream>>>(
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+        break;
+    case 32:
+        walker_update_group<32><<<n_blocks, threads, shape.smem_bytes, stream>>>(
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
