@@ -148,10 +148,15 @@ def cpu_oracle_rate(wl, budget_s: float, seed_offset: int = 0):
     nw = min(W, max(chain.num_threads() * 4, 16))
     S, occ, E = chain.init_walkers(d, L, N, nw, seed)
     T = chain.thresholds(d, e_lo, e_hi, np.zeros(e_hi - e_lo + 1))
-    t0 = time.perf_counter()
-    chain.run_walkers(d, L, N, seed, 0, N, e_lo, e_hi, T, S, occ, E)
-    dt = max(time.perf_counter() - t0, 1e-4)
-    sweeps = max(1, int(budget_s / dt))
+    cal = 1
+    while True:
+        t0 = time.perf_counter()
+        chain.run_walkers(d, L, N, seed, 0, cal * N, e_lo, e_hi, T, S, occ, E)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 or cal > (1 << 30):
+            break
+        cal *= 4
+    sweeps = max(1, int(budget_s * cal / dt))
     t0 = time.perf_counter()
     chain.run_walkers(d, L, N, seed, 1, sweeps * N, e_lo, e_hi, T, S, occ, E)
     dt = time.perf_counter() - t0
@@ -214,6 +219,9 @@ def main(argv=None):
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--wpb", type=int, default=0)
     ap.add_argument("--smem", type=int, default=-1)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the launch-shape autotuner (run after the warm-up steps)")
+    ap.add_argument("--tune-sweeps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -265,6 +273,20 @@ def main(argv=None):
     for it in range(args.warmup):
         step(it)
     torch.cuda.synchronize(device)
+    explicit = args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0
+    if not args.no_autotune and not explicit:
+        from paper_1401_4076_gb300.autotune import autotune
+        lnWs = [mc.weights(s) for s in range(len(systems))]
+        best, table = autotune(systems, lnW=lnWs, sweeps=args.tune_sweeps,
+                               cuda_stream=stream.cuda_stream)
+        mc.set_launch(**best)
+        args.launch_desc = mc.launch()
+        for cfg, ms in table[:5]:
+            print(json.dumps({"autotune": cfg, "kernel_ms": ms}), file=sys.stderr)
+    acc0 = mc.stats(0)
+    print(json.dumps({"warmup_acceptance": acc0["accepts"] / max(1, acc0["attempts"])}),
+          file=sys.stderr)
+    torch.cuda.synchronize(device)
     _barrier(world)
     torch.cuda.synchronize(device)
 
@@ -274,13 +296,16 @@ def main(argv=None):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kernel_ms = []
+    accs = []
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
         starts[i].record(stream)
         step(args.warmup + i)
         ends[i].record(stream)
-        kernel_ms.append(mc.stats(0)["kernel_ms"])
+        st = mc.stats(0)
+        kernel_ms.append(st["kernel_ms"])
+        accs.append(st["accepts"] / max(1, st["attempts"]))
     torch.cuda.synchronize(device)
     wall = time.perf_counter() - wall0
     _barrier(world)
@@ -310,7 +335,8 @@ def main(argv=None):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": _config(wl, args), "roofline": roofline,
-            "clocks": clk, "gpu_launches": None}
+            "clocks": clk, "gpu_launches": None,
+            "acceptance": statistics.mean(accs)}
     # launches inside the timed region: per step one walker update, one memset pair
     # per system is a driver memset, one histogram-reduce launch per system
     line["gpu_launches"] = args.steps * (1 + len(systems))

@@ -1,0 +1,68 @@
+"""Launch-shape autotuner for the walker update.
+
+For a set of systems it times every candidate launch shape: kernel (one
+thread per walker, or G lanes per walker), walkers per block, and whether the
+occupation bitsets are staged in shared memory.  All candidates compute the
+identical chain (the group kernel commits attempts in order), so only speed
+differs.  Timing runs on a scratch context whose walkers use other seeds, so
+the caller's chains are not advanced.  The acceptance rate changes which
+shape wins, so the caller passes the weights it will run with.
+"""
+from __future__ import annotations
+
+import json
+import statistics
+
+from . import mucal as m
+
+
+def candidates(max_threads: int = 1024):
+    out = []
+    for wpb in (4, 8, 16, 32):
+        for smem in (1, 0):
+            out.append(dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1,
+                            walkers_per_block=wpb, bits_in_smem=smem))
+    for g in (2, 4, 8, 16, 32):
+        for threads in (64, 128, 256):
+            wpb = threads // g
+            if wpb < 1 or threads > max_threads:
+                continue
+            for smem in (1, 0):
+                out.append(dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=g,
+                                walkers_per_block=wpb, bits_in_smem=smem))
+    return out
+
+
+def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 2, cuda_stream=None,
+             seed_shift: int = 1 << 40, cands=None, log=None):
+    """Return (best launch dict, table of (launch, kernel ms)) for ``systems``.
+
+    ``lnW``: optional list of per-system log-weights to time with.
+    """
+    scratch = [(d, L, N, W, lo, hi, seed + seed_shift) for (d, L, N, W, lo, hi, seed) in systems]
+    table = []
+    with m.Mucal(scratch, cuda_stream=cuda_stream) as mc:
+        if lnW is not None:
+            for i, w in enumerate(lnW):
+                if w is not None:
+                    mc.set_weights(i, w)
+        it = 0
+        for cfg in (cands or candidates()):
+            try:
+                mc.set_launch(**cfg)
+            except m.MucalError:
+                continue
+            mc.run_iteration(sweeps, it)      # warm-up of this shape
+            it += 1
+            mc.stats(0)
+            times = []
+            for _ in range(repeats):
+                mc.run_iteration(sweeps, it)
+                it += 1
+                times.append(mc.stats(0)["kernel_ms"])
+            ms = statistics.median(times)
+            table.append((cfg, ms))
+            if log:
+                log(json.dumps({"launch": cfg, "kernel_ms": ms}))
+    table.sort(key=lambda x: x[1])
+    return table[0][0], table

@@ -117,12 +117,23 @@ __device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, uint64_t
     int row = bin * width + 2 * D;
     uint32_t run = 0;
     unsigned long long acc = 0;
+    if (A == 0) return;
+    // attempt t's random numbers and list reads are issued one attempt early;
+    // a commit that moves the same list slot patches the early read
+    uint4 r = philox10(make_uint4(0u, 0u, iter, 0u), k0, k1);
+    uint32_t k = __umulhi(r.x, N), m = __umulhi(r.y, holes);
+    uint32_t a = S[k], b = S[N + m];
     for (uint64_t t = 0; t < A; ++t) {
-        const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
-        const uint32_t k = __umulhi(r.x, N);
-        const uint32_t m = __umulhi(r.y, holes);
-        const uint32_t a = S[k];
-        const uint32_t b = S[N + m];
+        const uint64_t tn = t + 1;
+        uint32_t kn = 0, mn = 0, an = 0, bn = 0;
+        uint4 rn = make_uint4(0, 0, 0, 0);
+        if (tn < A) {
+            rn = philox10(make_uint4((uint32_t)tn, (uint32_t)(tn >> 32), iter, 0u), k0, k1);
+            kn = __umulhi(rn.x, N);
+            mn = __umulhi(rn.y, holes);
+            an = S[kn];
+            bn = S[N + mn];
+        }
         const int de = jump_delta_e<D>(p, bits, a, b);
         const uint32_t T = __ldg(thr + row + de);
         if (T == 0xFFFFFFFFu || r.z < T) {
@@ -130,6 +141,8 @@ __device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, uint64_t
             bits[b >> 5] |= (1u << (b & 31u));
             S[k] = (IdxT)b;
             S[N + m] = (IdxT)a;
+            if (kn == k) an = b;
+            if (mn == m) bn = a;
             ++acc;
             if (de != 0) {
                 if (run) atomicAdd(hist + bin, (unsigned long long)run);
@@ -143,6 +156,11 @@ __device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, uint64_t
             atomicAdd(hist + bin, (unsigned long long)run);
             run = 0;
         }
+        r = rn;
+        k = kn;
+        m = mn;
+        a = an;
+        b = bn;
     }
     if (run) atomicAdd(hist + bin, (unsigned long long)run);
     p.E[w] = bin + p.e_lo;
@@ -206,6 +224,16 @@ walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restr
 // touched the same list slot).  The warp's groups step through the rounds in
 // lock-step so that no group's path diverges from the others'.
 // ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ int count_occupied(const uint32_t *bits, const uint32_t (&nb)[2 * D],
+                                              uint32_t skip)
+{
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 2 * D; ++i) n += (int)(occupied(bits, nb[i]) & (nb[i] != skip ? 1u : 0u));
+    return n;
+}
+
 template <int D, typename IdxT, int G>
 __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits, uint64_t A,
                             uint32_t iter)
@@ -220,7 +248,7 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
     const uint32_t holes = (uint32_t)(p.V - p.N);
     const uint64_t seed = p.seed_base + (uint64_t)w;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const uint32_t *thr = p.thr;
+    const uint32_t *thr = p.thr + 2 * D;
     const int width = p.width;
     unsigned long long *hist = active ? p.hist + (size_t)w * (size_t)p.n_bins : nullptr;
     int bin = active ? p.E[w] - p.e_lo : 0;
@@ -231,6 +259,7 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
         const int n_valid = (int)((A - t0) < (uint64_t)G ? (A - t0) : (uint64_t)G);
         const bool valid = active && (j < n_valid);
         uint32_t k = 0, m = 0, a = 0, b = 0, r2 = 0;
+        uint32_t na[2 * D], nb[2 * D];
         if (valid) {
             const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
             k = __umulhi(r.x, N);
@@ -238,6 +267,8 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
             r2 = r.z;
             a = S[k];
             b = S[N + m];
+            neighbours<D>(p, a, na);
+            neighbours<D>(p, b, nb);
         }
         int pos = 0;
         bool done = !active;
@@ -245,8 +276,8 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
             bool accept = false;
             int de = 0;
             if (!done && valid && j >= pos) {
-                de = jump_delta_e<D>(p, bits, a, b);
-                const uint32_t T = __ldg(thr + bin * width + 2 * D + de);
+                de = count_occupied<D>(bits, na, 0xFFFFFFFFu) - count_occupied<D>(bits, nb, a);
+                const uint32_t T = __ldg(thr + bin * width + de);
                 accept = (T == 0xFFFFFFFFu) || (r2 < T);
             }
             const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
@@ -274,8 +305,15 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
                     }
                     run += 1;
                     if (j > f) {
-                        if (k == k_f) a = b_f;
-                        if (m == m_f) b = a_f;
+                        // the commit moved list slots k_f and N + m_f
+                        if (k == k_f) {
+                            a = b_f;
+                            neighbours<D>(p, a, na);
+                        }
+                        if (m == m_f) {
+                            b = a_f;
+                            neighbours<D>(p, b, nb);
+                        }
                     }
                     pos = f + 1;
                     if (pos >= n_valid) done = true;

@@ -83,10 +83,24 @@ def test_threshold_table_bit_exact(d, N):
 
 # ------------------------------------------------- full small-case parity --
 
-@pytest.mark.parametrize("launch", [
+LAUNCHES = [
     dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=32, bits_in_smem=1),
     dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=7, bits_in_smem=0),
-])
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=2, walkers_per_block=16, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=4, walkers_per_block=24, bits_in_smem=0),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16, walkers_per_block=2, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=32, walkers_per_block=5, bits_in_smem=0),
+]
+GROUP8 = LAUNCHES[4]
+GROUP32 = LAUNCHES[6]
+
+
+def _lid(c):
+    return f"k{c['kernel']}-G{c['lanes_per_walker']}-w{c['walkers_per_block']}-s{c['bits_in_smem']}"
+
+
+@pytest.mark.parametrize("launch", LAUNCHES, ids=_lid)
 def test_small_2d_ten_iterations_bit_exact(launch):
     """2D L=16, N=32, 64 walkers, seeds 0..63, lnW=0 start, 10 iterations of
     2000 sweeps with the recursive update: every per-walker histogram of every
@@ -133,14 +147,16 @@ def test_simple_scheme_matches_oracle():
 
 # ---------------------------------------------------------- edge cases ------
 
+@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP32], ids=_lid)
 @pytest.mark.parametrize("desc,sweeps", [
     ((3, 6, 40, 37, 0, 0, 11), 30),          # 3D, ragged walker count
     ((2, 3, 1, 5, 0, 0, 77), 200),           # single particle on 3x3
     ((3, 5, 124, 4, 0, 0, 9), 20),           # N = V - 1: one hole
     ((2, 257, 300, 2, 0, 0, 5), 3),          # uint32 site lists
     ((3, 4, 20, 8, -30, -2, 0), 40),         # user window (checked to hold the start)
+    ((2, 8, 3, 9, 0, 0, 3), 7),              # attempts per walker (21) not a multiple of G
 ])
-def test_edge_cases_bit_exact(desc, sweeps):
+def test_edge_cases_bit_exact(desc, sweeps, launch):
     d, L, N, W, lo, hi, seed = desc
     e_lo, e_hi = _window(d, N, lo, hi)
     nb = e_hi - e_lo + 1
@@ -152,6 +168,10 @@ def test_edge_cases_bit_exact(desc, sweeps):
             return
     lnW = workloads.random_log_weights(nb, 1, scale=0.5)
     with m.Mucal([desc], per_walker_hist=True) as mc:
+        try:
+            mc.set_launch(**launch)
+        except m.MucalError:        # bitsets too large for shared memory at this block size
+            mc.set_launch(**dict(launch, bits_in_smem=0))
         mc.set_weights(0, lnW)
         T = chain.thresholds(d, e_lo, e_hi, lnW)
         for it in range(2):
@@ -181,11 +201,11 @@ def test_window_boundary_is_never_crossed():
 
 # ------------------------------------------------ several systems, one launch
 
-def test_multi_system_launch_bit_exact():
+@pytest.mark.parametrize("launch", [LAUNCHES[0], GROUP8], ids=_lid)
+def test_multi_system_launch_bit_exact(launch):
     systems = [(2, 16, 32, 40, 0, 0, 0), (3, 8, 60, 25, 0, 0, 500), (2, 24, 50, 33, 0, 0, 900)]
     with m.Mucal(systems, per_walker_hist=True) as mc:
-        mc.set_launch(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=16,
-                      bits_in_smem=1)
+        mc.set_launch(**launch)
         lnWs = []
         for i, (d, L, N, W, lo, hi, seed) in enumerate(systems):
             lnW = workloads.random_log_weights(d * N + 1, 10 + i, scale=0.3)
@@ -225,11 +245,14 @@ def _sampled_full_size(wl, sweeps, pick, launch=None, lnW_seed=None):
             _assert_walker_equal(mc, 0, w, S[i], occ[i], E[i])
 
 
-def test_medium_2d_first_iteration_sampled():
+@pytest.mark.parametrize("launch", [None, GROUP8], ids=["default", "G8"])
+def test_medium_2d_first_iteration_sampled(launch):
     """2D L=64, N=410, 4096 walkers, first iteration (lnW = 0) at full size."""
-    _sampled_full_size(workloads.MEDIUM_2D, workloads.MEDIUM_2D.sweeps, [0, 1, 777, 2048, 4095])
+    _sampled_full_size(workloads.MEDIUM_2D, workloads.MEDIUM_2D.sweeps, [0, 1, 777, 2048, 4095],
+                       launch=launch)
 
 
-def test_large_3d_first_iteration_sampled():
+@pytest.mark.parametrize("launch", [None, GROUP32], ids=["default", "G32"])
+def test_large_3d_first_iteration_sampled(launch):
     """3D L=32, N=3277, 8192 walkers, one iteration with non-trivial weights."""
-    _sampled_full_size(workloads.LARGE_3D, 20, [0, 4097, 8191], lnW_seed=3)
+    _sampled_full_size(workloads.LARGE_3D, 20, [0, 4097, 8191], launch=launch, lnW_seed=3)
