@@ -17,13 +17,16 @@ from . import mucal as m
 
 
 def candidates(max_threads: int = 1024):
+    """Launch shapes to try.  Block sizes include odd multiples of a warp so
+    that a one-wave launch can match walkers to SMs when shared memory limits
+    the blocks per SM."""
     out = []
     for wpb in (4, 8, 16, 32):
         for smem in (1, 0):
             out.append(dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1,
                             walkers_per_block=wpb, bits_in_smem=smem))
-    for g in (2, 4, 8, 16, 32):
-        for threads in (64, 128, 256):
+    for g in (4, 8, 16, 32):
+        for threads in (64, 96, 128, 160, 192, 224, 256, 384, 512):
             wpb = threads // g
             if wpb < 1 or threads > max_threads:
                 continue
@@ -33,14 +36,28 @@ def candidates(max_threads: int = 1024):
     return out
 
 
-def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 2, cuda_stream=None,
-             seed_shift: int = 1 << 40, cands=None, log=None):
+def _time(mc, cfg, sweeps, repeats, it):
+    mc.set_launch(**cfg)
+    mc.run_iteration(sweeps, it)      # warm-up of this shape
+    it += 1
+    times = []
+    for _ in range(repeats):
+        mc.run_iteration(sweeps, it)
+        it += 1
+        times.append(mc.stats(0)["kernel_ms"])
+    return statistics.median(times), it
+
+
+def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 3, cuda_stream=None,
+             seed_shift: int = 1 << 40, cands=None, finalists: int = 8, log=None):
     """Return (best launch dict, table of (launch, kernel ms)) for ``systems``.
 
-    ``lnW``: optional list of per-system log-weights to time with.
+    Two stages: every candidate once, then the fastest ``finalists`` again
+    with ``repeats`` timed runs each.  ``lnW``: optional per-system
+    log-weights to time with.
     """
     scratch = [(d, L, N, W, lo, hi, seed + seed_shift) for (d, L, N, W, lo, hi, seed) in systems]
-    table = []
+    first = []
     with m.Mucal(scratch, cuda_stream=cuda_stream) as mc:
         if lnW is not None:
             for i, w in enumerate(lnW):
@@ -49,20 +66,16 @@ def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 2, cuda_stream=
         it = 0
         for cfg in (cands or candidates()):
             try:
-                mc.set_launch(**cfg)
+                ms, it = _time(mc, cfg, sweeps, 1, it)
             except m.MucalError:
                 continue
-            mc.run_iteration(sweeps, it)      # warm-up of this shape
-            it += 1
-            mc.stats(0)
-            times = []
-            for _ in range(repeats):
-                mc.run_iteration(sweeps, it)
-                it += 1
-                times.append(mc.stats(0)["kernel_ms"])
-            ms = statistics.median(times)
+            first.append((cfg, ms))
+        first.sort(key=lambda x: x[1])
+        table = []
+        for cfg, _ in first[:finalists]:
+            ms, it = _time(mc, cfg, sweeps, repeats, it)
             table.append((cfg, ms))
             if log:
                 log(json.dumps({"launch": cfg, "kernel_ms": ms}))
     table.sort(key=lambda x: x[1])
-    return table[0][0], table
+    return table[0][0], table + first[finalists:]

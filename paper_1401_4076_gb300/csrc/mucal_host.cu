@@ -249,11 +249,13 @@ void destroy_context(Context *c)
     delete c;
 }
 
-// Shared memory a block of the current shape needs for system s.
+// Shared memory a block of the given shape needs for system p.
 size_t smem_for(const LaunchShape &sh, const SysParams &p)
 {
-    if (!sh.bits_in_smem) return 0;
-    return (size_t)sh.walkers_per_block * (size_t)p.words * sizeof(uint32_t);
+    size_t bytes = 0;
+    if (sh.thr_in_smem) bytes += mucal::thr_smem_words(p) * sizeof(uint32_t);
+    if (sh.bits_in_smem) bytes += (size_t)sh.walkers_per_block * (size_t)p.words * sizeof(uint32_t);
+    return bytes;
 }
 
 // Split every system's walkers into blocks of the launch shape; order the
@@ -262,15 +264,21 @@ size_t smem_for(const LaunchShape &sh, const SysParams &p)
 int build_work(Context *c, const LaunchShape &sh)
 {
     std::vector<BlockWork> work;
+    const bool per_walker = (c->flags & MUCAL_FLAG_PER_WALKER_HIST) != 0;
     for (int s = 0; s < (int)c->sys.size(); ++s) {
-        const SysParams &p = c->sys[s].p;
+        SysParams &p = c->sys[s].p;
+        int rows = 0;
         for (int w0 = 0; w0 < p.n_walkers; w0 += sh.walkers_per_block) {
             BlockWork bw{};
             bw.sys = s;
             bw.walker0 = w0;
             bw.count = std::min(sh.walkers_per_block, p.n_walkers - w0);
+            bw.hist_row = per_walker ? -1 : rows;
+            ++rows;
             work.push_back(bw);
         }
+        // blocks never outnumber walkers, so the per-walker allocation holds them
+        p.hist_rows = per_walker ? p.n_walkers : rows;
     }
     std::stable_sort(work.begin(), work.end(), [&](const BlockWork &a, const BlockWork &b) {
         const double ca = (double)c->sys[a.sys].p.N * c->sys[a.sys].p.d;
@@ -285,6 +293,9 @@ int build_work(Context *c, const LaunchShape &sh)
     CUDA_TRY(c, cudaMemcpy(c->d_work, work.data(), work.size() * sizeof(BlockWork),
                            cudaMemcpyHostToDevice));
     c->n_blocks = (int)work.size();
+    std::vector<SysParams> hp(c->sys.size());
+    for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
+    CUDA_TRY(c, cudaMemcpy(c->d_sys, hp.data(), hp.size() * sizeof(SysParams), cudaMemcpyHostToDevice));
     return MUCAL_OK;
 }
 
@@ -308,6 +319,11 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     }
     if (sh.walkers_per_block < 1 || sh.walkers_per_block * sh.lanes > 1024)
         return fail(c, MUCAL_ERR_INVALID_ARG, "walkers_per_block * lanes must be in [1, 1024]");
+    // the threshold table joins the bitsets in shared memory whenever every
+    // system's table fits next to its block of bitsets
+    sh.thr_in_smem = 1;
+    for (auto &s : c->sys)
+        if (smem_for(sh, s.p) > (size_t)c->max_smem) sh.thr_in_smem = 0;
     size_t smem = 0;
     for (auto &s : c->sys) smem = std::max(smem, smem_for(sh, s.p));
     if (smem > (size_t)c->max_smem)
@@ -417,6 +433,7 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
         p.words = (p.V + 31) / 32;
         p.idx16 = p.V <= 65536 ? 1 : 0;
         p.n_walkers = sys[i].n_walkers;
+        p.hist_rows = p.n_walkers;
         p.magL = (uint32_t)(((1ull << 32) + (uint64_t)p.L - 1) / (uint64_t)p.L);
         p.seed_base = sys[i].seed_base;
         const size_t nw = (size_t)p.n_walkers;
@@ -484,9 +501,10 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
                                  "system %d: initial energy %d outside window [%d, %d]", i, v,
                                  s.desc.e_lo, s.desc.e_hi));
     }
-    mucal_launch_config def{MUCAL_KERNEL_THREAD, 1, 32, 1};
+    mucal_launch_config def{MUCAL_KERNEL_GROUP, 8, 16, 1};
     for (auto &s : c->sys)
-        if (smem_for(LaunchShape{0, 1, 32, 1, 0}, s.p) > (size_t)c->max_smem) def.bits_in_smem = 0;
+        if (smem_for(LaunchShape{MUCAL_KERNEL_GROUP, 8, 16, 1, 0, 0}, s.p) > (size_t)c->max_smem)
+            def.bits_in_smem = 0;
     rc = apply_launch_config(c, def);
     if (rc != MUCAL_OK) return bail(rc);
     *out = c;
@@ -568,7 +586,8 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
     CUDA_TRY(c, cudaEventRecord(c->ev_it0, c->stream));
     for (auto &s : c->sys) {
         const size_t nw = (size_t)s.p.n_walkers;
-        CUDA_TRY(c, cudaMemsetAsync(s.p.hist, 0, nw * (size_t)s.p.n_bins * 8, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(s.p.hist, 0, (size_t)s.p.hist_rows * (size_t)s.p.n_bins * 8,
+                                    c->stream));
         CUDA_TRY(c, cudaMemsetAsync(s.p.H, 0, (size_t)s.p.n_bins * 8, c->stream));
         s.hist_on_host = false;
         s.last_attempts = (uint64_t)sweeps * (uint64_t)s.p.N * nw;

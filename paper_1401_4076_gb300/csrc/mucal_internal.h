@@ -22,7 +22,9 @@ struct SysParams {
     uint32_t *bits;            // [n_walkers][words] occupation n_i, bit s%32 of word s/32
     void *S;                   // [n_walkers][V] particle sites then empty sites
     int32_t *E;                // [n_walkers] current energy
-    unsigned long long *hist;  // [n_walkers][n_bins] per-walker histogram H_j(E)
+    unsigned long long *hist;  // [rows][n_bins] histogram rows: one per walker (H_j(E)) when
+                               // per-walker histograms are kept, else one per launch block
+    int32_t hist_rows;         // rows in use for the current launch shape
     const uint32_t *thr;       // [n_bins][width] acceptance thresholds
     unsigned long long *accepts; // [n_walkers] accepted moves in the last iteration
     unsigned long long *H;     // [n_bins] summed histogram H(E) (Eq. 2)
@@ -34,7 +36,7 @@ struct BlockWork {
     int32_t sys;
     int32_t walker0;
     int32_t count;
-    int32_t pad;
+    int32_t hist_row;   // this block's histogram row when rows are per block, else -1
 };
 
 struct LaunchShape {
@@ -42,6 +44,7 @@ struct LaunchShape {
     int lanes;              // lanes per walker
     int walkers_per_block;
     int bits_in_smem;
+    int thr_in_smem;        // stage the system's threshold table in shared memory
     size_t smem_bytes;      // dynamic shared memory per block
 };
 
@@ -53,6 +56,8 @@ cudaError_t launch_init_walkers(const SysParams *host_sys, const SysParams *dev_
 cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
                                  int n_blocks, const LaunchShape &shape, uint64_t sweeps,
                                  uint32_t iteration, cudaStream_t stream);
+// Shared-memory layout of a walker-update block: [threshold table][bitsets].
+size_t thr_smem_words(const SysParams &p);
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                cudaStream_t stream);
 cudaError_t walker_update_max_smem(int *bytes);

@@ -97,29 +97,42 @@ __device__ __forceinline__ IdxT *walker_S(const SysParams &p, int w)
     return reinterpret_cast<IdxT *>(p.S) + (size_t)w * (size_t)p.V;
 }
 
+// Shared-memory words used by the threshold table of system p (rounded up to
+// 16 bytes so that the bitsets behind it stay aligned).
+__host__ __device__ __forceinline__ size_t thr_words_aligned(const SysParams &p)
+{
+    return (((size_t)p.n_bins * (size_t)p.width) + 3u) & ~(size_t)3u;
+}
+
+// Histogram row a walker records into: its own row when per-walker histograms
+// are kept, otherwise its block's row.
+__device__ __forceinline__ unsigned long long *hist_row(const SysParams &p, int w, int block_row)
+{
+    const int row = block_row >= 0 ? block_row : w;
+    return p.hist + (size_t)row * (size_t)p.n_bins;
+}
+
 // ---------------------------------------------------------------------------
 // One thread, one walker: A attempts in order.  The histogram is kept as a
-// run length (current bin, count) and added to the walker's histogram only
-// when the energy changes, which records exactly one entry per attempt.
+// run length (current bin, count) and added to the histogram row only when
+// the energy changes, which records exactly one entry per attempt.  Attempt
+// t+1's random numbers and list reads are issued during attempt t; a commit
+// that moves the same list slot patches the early read.
 // ---------------------------------------------------------------------------
 template <int D, typename IdxT>
-__device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, uint64_t A, uint32_t iter)
+__device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, const uint32_t *thr,
+                             unsigned long long *hist, uint64_t A, uint32_t iter)
 {
     IdxT *S = walker_S<IdxT>(p, w);
     const uint32_t N = (uint32_t)p.N;
     const uint32_t holes = (uint32_t)(p.V - p.N);
     const uint64_t seed = p.seed_base + (uint64_t)w;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const uint32_t *thr = p.thr;
     const int width = p.width;
-    unsigned long long *hist = p.hist + (size_t)w * (size_t)p.n_bins;
     int bin = p.E[w] - p.e_lo;
     int row = bin * width + 2 * D;
     uint32_t run = 0;
-    unsigned long long acc = 0;
-    if (A == 0) return;
-    // attempt t's random numbers and list reads are issued one attempt early;
-    // a commit that moves the same list slot patches the early read
+    uint32_t acc = 0;
     uint4 r = philox10(make_uint4(0u, 0u, iter, 0u), k0, k1);
     uint32_t k = __umulhi(r.x, N), m = __umulhi(r.y, holes);
     uint32_t a = S[k], b = S[N + m];
@@ -135,7 +148,7 @@ __device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, uint64_t
             bn = S[N + mn];
         }
         const int de = jump_delta_e<D>(p, bits, a, b);
-        const uint32_t T = __ldg(thr + row + de);
+        const uint32_t T = thr[row + de];
         if (T == 0xFFFFFFFFu || r.z < T) {
             bits[a >> 5] &= ~(1u << (a & 31u));
             bits[b >> 5] |= (1u << (b & 31u));
@@ -167,75 +180,122 @@ __device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, uint64_t
     p.accepts[w] = acc;
 }
 
-template <int D>
-__device__ void chain_thread_dispatch_idx(const SysParams &p, int w, uint32_t *bits, uint64_t A,
-                                          uint32_t iter)
-{
-    if (p.idx16)
-        chain_thread<D, uint16_t>(p, w, bits, A, iter);
-    else
-        chain_thread<D, uint32_t>(p, w, bits, A, iter);
-}
-
-// Copy the bitsets of walkers [w0, w0+count) between global and shared memory
-// (contiguous in both), all threads of the block cooperating.
+// Copy n words between global and shared memory, all threads cooperating.
 __device__ __forceinline__ void block_copy_words(uint32_t *dst, const uint32_t *src, size_t n)
 {
     for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// Shared memory of a walker-update block: [threshold table | bitsets].  The
+// block's walkers are contiguous in global memory, so the bitsets move as one
+// coalesced copy in and out.
+struct BlockSetup {
+    const uint32_t *thr;
+    uint32_t *gbits;     // first bitset of the block in global memory
+    uint32_t *bits0;     // first bitset of the block where the kernel uses it
+    size_t block_words;
+};
+
+__device__ __forceinline__ BlockSetup block_setup(const SysParams &p, const BlockWork &wk,
+                                                  uint32_t *smem, int bits_in_smem,
+                                                  int thr_in_smem)
+{
+    BlockSetup b;
+    b.block_words = (size_t)wk.count * (size_t)p.words;
+    b.gbits = p.bits + (size_t)wk.walker0 * (size_t)p.words;
+    uint32_t *sb = smem;
+    if (thr_in_smem) {
+        block_copy_words(smem, p.thr, (size_t)p.n_bins * (size_t)p.width);
+        sb = smem + thr_words_aligned(p);
+        b.thr = smem;
+    } else {
+        b.thr = p.thr;
+    }
+    if (bits_in_smem) {
+        block_copy_words(sb, b.gbits, b.block_words);
+        b.bits0 = sb;
+    } else {
+        b.bits0 = b.gbits;
+    }
+    if (thr_in_smem || bits_in_smem) __syncthreads();
+    return b;
+}
+
+__device__ __forceinline__ void block_finish(const BlockSetup &b, int bits_in_smem)
+{
+    if (bits_in_smem) {
+        __syncthreads();
+        block_copy_words(b.gbits, b.bits0, b.block_words);
+    }
+}
+
 __global__ void __launch_bounds__(1024)
 walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
-                     uint64_t sweeps, uint32_t iter, int bits_in_smem)
+                     uint64_t sweeps, uint32_t iter, int bits_in_smem, int thr_in_smem)
 {
-    extern __shared__ uint32_t smem_bits[];
+    extern __shared__ __align__(16) uint32_t smem[];
     const BlockWork wk = work[blockIdx.x];
     const SysParams &p = sys[wk.sys];
+    const BlockSetup bs = block_setup(p, wk, smem, bits_in_smem, thr_in_smem);
     const int lw = threadIdx.x;
-    const size_t block_words = (size_t)wk.count * (size_t)p.words;
-    uint32_t *gbits = p.bits + (size_t)wk.walker0 * (size_t)p.words;
-    if (bits_in_smem) {
-        block_copy_words(smem_bits, gbits, block_words);
-        __syncthreads();
-    }
     if (lw < wk.count) {
         const int w = wk.walker0 + lw;
-        uint32_t *bits = bits_in_smem ? smem_bits + (size_t)lw * p.words
-                                      : gbits + (size_t)lw * p.words;
+        uint32_t *bits = bs.bits0 + (size_t)lw * p.words;
+        unsigned long long *hist = hist_row(p, w, wk.hist_row);
         const uint64_t A = sweeps * (uint64_t)p.N;
-        if (p.d == 2)
-            chain_thread_dispatch_idx<2>(p, w, bits, A, iter);
-        else
-            chain_thread_dispatch_idx<3>(p, w, bits, A, iter);
+        if (p.d == 2) {
+            if (p.idx16) chain_thread<2, uint16_t>(p, w, bits, bs.thr, hist, A, iter);
+            else chain_thread<2, uint32_t>(p, w, bits, bs.thr, hist, A, iter);
+        } else {
+            if (p.idx16) chain_thread<3, uint16_t>(p, w, bits, bs.thr, hist, A, iter);
+            else chain_thread<3, uint32_t>(p, w, bits, bs.thr, hist, A, iter);
+        }
     }
-    if (bits_in_smem) {
-        __syncthreads();
-        block_copy_words(gbits, smem_bits, block_words);
-    }
+    block_finish(bs, bits_in_smem);
 }
 
 // ---------------------------------------------------------------------------
 // G lanes per walker (G divides 32).  Lane j of a group owns attempt t0 + j of
-// the current batch: it draws its random numbers and reads its particle and
-// empty site once, then every round evaluates dE and the acceptance against
-// the walker's current state.  The first accepting lane f commits; lanes
-// before it were rejected by that same state, lanes after it re-evaluate in
-// the next round (their list entries are patched in registers when the commit
-// touched the same list slot).  The warp's groups step through the rounds in
-// lock-step so that no group's path diverges from the others'.
+// the current batch: it draws its random numbers, reads its particle and
+// empty site, and precomputes the words and bit positions of their 2*2d
+// neighbours once.  Every round the lanes still pending evaluate dE and the
+// acceptance against the walker's current state.  The first accepting lane f
+// commits; lanes before it were rejected by that same state and are recorded
+// at the current energy; lanes after it re-evaluate in the next round (their
+// list entries are patched in registers when the commit moved the same list
+// slot).  The chain is therefore exactly the one-thread chain.  A warp's
+// groups step through the rounds in lock-step so no group diverges.
 // ---------------------------------------------------------------------------
 template <int D>
-__device__ __forceinline__ int count_occupied(const uint32_t *bits, const uint32_t (&nb)[2 * D],
-                                              uint32_t skip)
+struct NbWords {
+    uint32_t word[2 * D];   // word index of each neighbour in the bitset
+    uint32_t shift[2 * D];  // bit position, or 32 to read the neighbour as empty
+};
+
+template <int D>
+__device__ __forceinline__ void nb_words(const SysParams &p, uint32_t s, uint32_t skip, NbWords<D> &o)
+{
+    uint32_t nb[2 * D];
+    neighbours<D>(p, s, nb);
+#pragma unroll
+    for (int i = 0; i < 2 * D; ++i) {
+        o.word[i] = nb[i] >> 5;
+        o.shift[i] = (nb[i] == skip) ? 32u : (nb[i] & 31u);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ int nb_count(const uint32_t *bits, const NbWords<D> &o)
 {
     int n = 0;
 #pragma unroll
-    for (int i = 0; i < 2 * D; ++i) n += (int)(occupied(bits, nb[i]) & (nb[i] != skip ? 1u : 0u));
+    for (int i = 0; i < 2 * D; ++i) n += (int)(__funnelshift_rc(bits[o.word[i]], 0u, o.shift[i]) & 1u);
     return n;
 }
 
 template <int D, typename IdxT, int G>
-__device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits, uint64_t A,
+__device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits,
+                            const uint32_t *thr, unsigned long long *hist, uint64_t A,
                             uint32_t iter)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -248,18 +308,18 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
     const uint32_t holes = (uint32_t)(p.V - p.N);
     const uint64_t seed = p.seed_base + (uint64_t)w;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const uint32_t *thr = p.thr + 2 * D;
     const int width = p.width;
-    unsigned long long *hist = active ? p.hist + (size_t)w * (size_t)p.n_bins : nullptr;
     int bin = active ? p.E[w] - p.e_lo : 0;
+    int row = bin * width + 2 * D;
     uint32_t run = 0;
-    unsigned long long acc = 0;
+    uint32_t acc = 0;
     for (uint64_t t0 = 0; t0 < A; t0 += G) {
         const uint64_t t = t0 + (uint64_t)j;
-        const int n_valid = (int)((A - t0) < (uint64_t)G ? (A - t0) : (uint64_t)G);
+        const uint64_t left = A - t0;
+        const int n_valid = left < (uint64_t)G ? (int)left : G;
         const bool valid = active && (j < n_valid);
         uint32_t k = 0, m = 0, a = 0, b = 0, r2 = 0;
-        uint32_t na[2 * D], nb[2 * D];
+        NbWords<D> wa, wb;
         if (valid) {
             const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
             k = __umulhi(r.x, N);
@@ -267,8 +327,8 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
             r2 = r.z;
             a = S[k];
             b = S[N + m];
-            neighbours<D>(p, a, na);
-            neighbours<D>(p, b, nb);
+            nb_words<D>(p, a, 0xFFFFFFFFu, wa);
+            nb_words<D>(p, b, a, wb);
         }
         int pos = 0;
         bool done = !active;
@@ -276,8 +336,8 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
             bool accept = false;
             int de = 0;
             if (!done && valid && j >= pos) {
-                de = count_occupied<D>(bits, na, 0xFFFFFFFFu) - count_occupied<D>(bits, nb, a);
-                const uint32_t T = __ldg(thr + bin * width + de);
+                de = nb_count<D>(bits, wa) - nb_count<D>(bits, wb);
+                const uint32_t T = thr[row + de];
                 accept = (T == 0xFFFFFFFFu) || (r2 < T);
             }
             const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
@@ -288,6 +348,7 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
             const uint32_t b_f = __shfl_sync(FULL, b, src);
             const uint32_t k_f = __shfl_sync(FULL, k, src);
             const uint32_t m_f = __shfl_sync(FULL, m, src);
+            bool fix_a = false, fix_b = false;
             if (!done) {
                 if (f < G) {
                     run += (uint32_t)(f - pos);      // rejected at the current energy
@@ -301,25 +362,26 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
                     if (de_f != 0) {
                         if (j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
                         bin += de_f;
+                        row += de_f * width;
                         run = 0;
                     }
                     run += 1;
-                    if (j > f) {
-                        // the commit moved list slots k_f and N + m_f
-                        if (k == k_f) {
-                            a = b_f;
-                            neighbours<D>(p, a, na);
-                        }
-                        if (m == m_f) {
-                            b = a_f;
-                            neighbours<D>(p, b, nb);
-                        }
-                    }
+                    // the commit moved list slots k_f and N + m_f
+                    fix_a = (j > f) && (k == k_f);
+                    fix_b = (j > f) && (m == m_f);
                     pos = f + 1;
                     if (pos >= n_valid) done = true;
                 } else {
                     run += (uint32_t)(n_valid - pos);
                     done = true;
+                }
+            }
+            if (__any_sync(FULL, fix_a || fix_b)) {
+                if (fix_a) a = b_f;
+                if (fix_b) b = a_f;
+                if (fix_a || fix_b) {
+                    nb_words<D>(p, a, 0xFFFFFFFFu, wa);
+                    nb_words<D>(p, b, a, wb);
                 }
             }
             __syncwarp(FULL);
@@ -339,34 +401,26 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
 template <int G>
 __global__ void __launch_bounds__(1024)
 walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
-                    uint64_t sweeps, uint32_t iter, int bits_in_smem)
+                    uint64_t sweeps, uint32_t iter, int bits_in_smem, int thr_in_smem)
 {
-    extern __shared__ uint32_t smem_bits[];
+    extern __shared__ __align__(16) uint32_t smem[];
     const BlockWork wk = work[blockIdx.x];
     const SysParams &p = sys[wk.sys];
+    const BlockSetup bs = block_setup(p, wk, smem, bits_in_smem, thr_in_smem);
     const int lw = threadIdx.x / G;
-    const size_t block_words = (size_t)wk.count * (size_t)p.words;
-    uint32_t *gbits = p.bits + (size_t)wk.walker0 * (size_t)p.words;
-    if (bits_in_smem) {
-        block_copy_words(smem_bits, gbits, block_words);
-        __syncthreads();
-    }
     const bool active = lw < wk.count;
     const int w = wk.walker0 + (active ? lw : 0);
-    uint32_t *bits = bits_in_smem ? smem_bits + (size_t)(active ? lw : 0) * p.words
-                                  : gbits + (size_t)(active ? lw : 0) * p.words;
+    uint32_t *bits = bs.bits0 + (size_t)(active ? lw : 0) * p.words;
+    unsigned long long *hist = hist_row(p, w, wk.hist_row);
     const uint64_t A = sweeps * (uint64_t)p.N;
     if (p.d == 2) {
-        if (p.idx16) chain_group<2, uint16_t, G>(p, w, active, bits, A, iter);
-        else chain_group<2, uint32_t, G>(p, w, active, bits, A, iter);
+        if (p.idx16) chain_group<2, uint16_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
+        else chain_group<2, uint32_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
     } else {
-        if (p.idx16) chain_group<3, uint16_t, G>(p, w, active, bits, A, iter);
-        else chain_group<3, uint32_t, G>(p, w, active, bits, A, iter);
+        if (p.idx16) chain_group<3, uint16_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
+        else chain_group<3, uint32_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
     }
-    if (bits_in_smem) {
-        __syncthreads();
-        block_copy_words(gbits, smem_bits, block_words);
-    }
+    block_finish(bs, bits_in_smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -440,7 +494,7 @@ __global__ void hist_reduce_kernel(SysParams p)
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= p.n_bins) return;
     const int w0 = blockIdx.y * kReduceWalkers;
-    const int w1 = min(w0 + kReduceWalkers, p.n_walkers);
+    const int w1 = min(w0 + kReduceWalkers, p.hist_rows);
     unsigned long long sum = 0;
     const unsigned long long *h = p.hist + (size_t)w0 * (size_t)p.n_bins + b;
     for (int w = w0; w < w1; ++w, h += p.n_bins) sum += *h;
@@ -510,29 +564,29 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
     const int threads = shape.walkers_per_block * shape.lanes;
     if (shape.kernel == 0) {
         walker_update_thread<<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
         return cudaGetLastError();
     }
     switch (shape.lanes) {
     case 2:
         walker_update_group<2><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
         break;
     case 4:
         walker_update_group<4><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
         break;
     case 8:
         walker_update_group<8><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
         break;
     case 16:
         walker_update_group<16><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
         break;
     case 32:
         walker_update_group<32><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem);
+            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -540,13 +594,15 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
     return cudaGetLastError();
 }
 
+size_t thr_smem_words(const SysParams &p) { return thr_words_aligned(p); }
+
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                cudaStream_t stream)
 {
     (void)dev_sys;
     for (int s = 0; s < n_sys; ++s) {
         const SysParams &p = host_sys[s];
-        dim3 grid((p.n_bins + 255) / 256, (p.n_walkers + kReduceWalkers - 1) / kReduceWalkers);
+        dim3 grid((p.n_bins + 255) / 256, (p.hist_rows + kReduceWalkers - 1) / kReduceWalkers);
         hist_reduce_kernel<<<grid, 256, 0, stream>>>(p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -256,3 +256,50 @@ def test_medium_2d_first_iteration_sampled(launch):
 def test_large_3d_first_iteration_sampled(launch):
     """3D L=32, N=3277, 8192 walkers, one iteration with non-trivial weights."""
     _sampled_full_size(workloads.LARGE_3D, 20, [0, 4097, 8191], launch=launch, lnW_seed=3)
+
+
+# ------------------------------------- production mode (per-block rows) -----
+
+@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP8, GROUP32], ids=_lid)
+def test_production_histogram_equals_oracle_sum(launch):
+    """Without per-walker histograms the rows are per block; H must still be the
+    exact sum of every walker's histogram (Eq. 2)."""
+    wl = workloads.SMALL_2D
+    d, L, N, W, lo, hi, seed = wl.systems[0]
+    lnW = workloads.random_log_weights(d * N + 1, 5, scale=0.2)
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    T = chain.thresholds(d, -d * N, 0, lnW)
+    with m.Mucal(wl.systems) as mc:
+        mc.set_launch(**launch)
+        mc.set_weights(0, lnW)
+        for it in range(2):
+            mc.run_iteration(300, it)
+            hist, _ = chain.run_walkers(d, L, N, seed, it, 300 * N, -d * N, 0, T, S, occ, E)
+            np.testing.assert_array_equal(mc.histogram(0), hist.sum(axis=0))
+
+
+@pytest.mark.parametrize("wl,sweeps,pick,launch", [
+    (workloads.MEDIUM_2D, 200, [0, 1500, 4095],
+     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=16, bits_in_smem=1)),
+    (workloads.LARGE_3D, 10, [0, 8191],
+     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=28, bits_in_smem=1)),
+], ids=["medium2d", "large3d"])
+def test_full_size_production_sampled_states(wl, sweeps, pick, launch):
+    """Full-size workloads in production mode: every walker's final state of a
+    sample equals the oracle's, and sum H counts every attempt."""
+    d, L, N, W, lo, hi, seed = wl.systems[0]
+    nb = d * N + 1
+    lnW = workloads.random_log_weights(nb, 8, 0.02)
+    with m.Mucal(wl.systems) as mc:
+        mc.set_launch(**launch)
+        mc.set_weights(0, lnW)
+        mc.run_iteration(sweeps, 4)
+        H = mc.histogram(0)
+        assert H.sum() == W * sweeps * N
+        S, occ, E = _oracle_states(d, L, N, W, seed, pick)
+        T = chain.thresholds(d, -d * N, 0, lnW)
+        hist, _ = chain.run_walkers(d, L, N, seed, 4, sweeps * N, -d * N, 0, T, S, occ, E,
+                                    walkers=pick)
+        assert (H >= hist.sum(axis=0)).all()
+        for i, w in enumerate(pick):
+            _assert_walker_equal(mc, 0, w, S[i], occ[i], E[i])
