@@ -209,6 +209,47 @@ int mucal_histogram_device_ptr(void *ctx, int32_t sys, void **dptr);
 /* Library version string. */
 const char *mucal_version(void);
 
+/* ---- weight-seeding network (not part of the paper) ---------------------
+ * A 4-128-128-1 multilayer perceptron with GELU activations (gelu(z) =
+ * z Phi(z)) that maps a caller-built feature vector of (d, L, rho, E/V) to a
+ * prediction of ln Omega(E)/V.  Its only use is to propose starting weights
+ * lnW = -V * prediction for the iteration of Sec. 2, which then runs and
+ * judges unchanged (the plain start lnW = 0 stays available).  Parameters:
+ * fp32 master copy and Adam state; the forward and backward passes use the
+ * bf16-rounded parameters, run the 128x128 layer on the tensor cores (bf16 x
+ * bf16, fp32 accumulation) and everything else in fp32.
+ * Parameter vector (fp32, 17281 = mucal_mlp_param_count()): W1[128][4],
+ * b1[128], W2[128][128] (row = output unit), b2[128], W3[128], b3.
+ * Loss: mean over the batch of (y - t)^2.  All buffers are host buffers,
+ * copied during the call; rows are 4 consecutive floats. */
+int mucal_mlp_param_count(void);
+
+/* Create a network with the given initial parameters (host fp32[n], n =
+ * 17281) on the current device; cuda_stream NULL = own stream.  Errors:
+ * INVALID_ARG, NO_DEVICE, OOM, CUDA. */
+int mucal_mlp_create(void **out, const float *params, int64_t n, void *cuda_stream);
+void mucal_mlp_destroy(void *mlp);
+const char *mucal_mlp_last_error(void *mlp);
+
+/* Copy the parameters to params[n]: the fp32 master copy (rounded = 0) or
+ * the bf16-rounded values the kernels compute with, widened to fp32
+ * (rounded = 1). */
+int mucal_mlp_get_params(void *mlp, float *params, int64_t n, int32_t rounded);
+
+/* y[B] = network(X[B][4]). */
+int mucal_mlp_forward(void *mlp, const float *X, int64_t B, float *y);
+
+/* One forward and backward pass of the mean squared error against t[B]:
+ * loss (nullable) and the gradient with respect to all 17281 parameters
+ * (grad nullable, host fp32[17281]).  Parameters are not changed. */
+int mucal_mlp_gradients(void *mlp, const float *X, const float *t, int64_t B, float *loss, float *grad);
+
+/* steps full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) with
+ * learning rate lr on (X, t), entirely on the device; loss_out (nullable)
+ * receives the loss of the last step's forward pass. */
+int mucal_mlp_train(void *mlp, const float *X, const float *t, int64_t B, int32_t steps, float lr,
+                    float *loss_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,8 @@ EXPORTED = [
     "mucal_get_launch_config", "mucal_run_iteration", "mucal_get_histogram",
     "mucal_update_weights", "mucal_set_target_window", "mucal_get_walker_state",
     "mucal_get_system_info", "mucal_get_stats", "mucal_histogram_device_ptr", "mucal_version",
+    "mucal_mlp_param_count", "mucal_mlp_create", "mucal_mlp_destroy", "mucal_mlp_last_error",
+    "mucal_mlp_get_params", "mucal_mlp_forward", "mucal_mlp_gradients", "mucal_mlp_train",
 ]
 
 
@@ -97,6 +99,14 @@ def load_library(path: str = LIB_PATH):
         "mucal_get_stats": (ctypes.c_int, [P, I32, ctypes.POINTER(mucal_stats)]),
         "mucal_histogram_device_ptr": (ctypes.c_int, [P, I32, ctypes.POINTER(P)]),
         "mucal_version": (ctypes.c_char_p, []),
+        "mucal_mlp_param_count": (ctypes.c_int, []),
+        "mucal_mlp_create": (ctypes.c_int, [ctypes.POINTER(P), P, I64, P]),
+        "mucal_mlp_destroy": (None, [P]),
+        "mucal_mlp_last_error": (ctypes.c_char_p, [P]),
+        "mucal_mlp_get_params": (ctypes.c_int, [P, P, I64, I32]),
+        "mucal_mlp_forward": (ctypes.c_int, [P, P, I64, P]),
+        "mucal_mlp_gradients": (ctypes.c_int, [P, P, P, I64, P, P]),
+        "mucal_mlp_train": (ctypes.c_int, [P, P, P, I64, I32, ctypes.c_float, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -313,3 +323,115 @@ class Mucal:
 
     def stats(self, sys=0):
         return mucal_get_stats(self.ctx, sys)
+
+
+# --------------------------------------------------------------------------
+# Weight-seeding network.
+# --------------------------------------------------------------------------
+
+def _mlp_check(rc, mlp=None):
+    if rc != MUCAL_OK:
+        msg = load_library().mucal_mlp_last_error(mlp)
+        raise MucalError(rc, msg.decode() if msg else "")
+
+
+def mucal_mlp_param_count():
+    return int(load_library().mucal_mlp_param_count())
+
+
+def mucal_mlp_create(params, cuda_stream=None):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _mlp_check(load_library().mucal_mlp_create(ctypes.byref(h), _ptr(p), p.size, cuda_stream))
+    return h
+
+
+def mucal_mlp_destroy(mlp):
+    load_library().mucal_mlp_destroy(mlp)
+
+
+def mucal_mlp_get_params(mlp, rounded=False):
+    out = np.zeros(mucal_mlp_param_count(), dtype=np.float32)
+    _mlp_check(load_library().mucal_mlp_get_params(mlp, _ptr(out), out.size, int(bool(rounded))), mlp)
+    return out
+
+
+def mucal_mlp_forward(mlp, X):
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 4)
+    y = np.zeros(X.shape[0], dtype=np.float32)
+    _mlp_check(load_library().mucal_mlp_forward(mlp, _ptr(X), X.shape[0], _ptr(y)), mlp)
+    return y
+
+
+def mucal_mlp_gradients(mlp, X, t):
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 4)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.zeros(mucal_mlp_param_count(), dtype=np.float32)
+    loss = ctypes.c_float()
+    _mlp_check(load_library().mucal_mlp_gradients(mlp, _ptr(X), _ptr(t), X.shape[0],
+                                                   ctypes.addressof(loss), _ptr(g)), mlp)
+    return loss.value, g
+
+
+def mucal_mlp_train(mlp, X, t, steps, lr):
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 4)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    loss = ctypes.c_float()
+    _mlp_check(load_library().mucal_mlp_train(mlp, _ptr(X), _ptr(t), X.shape[0], int(steps),
+                                               float(lr), ctypes.addressof(loss)), mlp)
+    return loss.value
+
+
+MLP_LAYOUT = (("W1", (128, 4)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+              ("W3", (1, 128)), ("b3", (1,)))
+
+
+def mlp_unflatten(vec):
+    """Split the flat parameter vector into named arrays (views)."""
+    out, off = {}, 0
+    for name, shape in MLP_LAYOUT:
+        n = int(np.prod(shape))
+        out[name] = np.asarray(vec[off: off + n]).reshape(shape)
+        off += n
+    return out
+
+
+def mlp_flatten(params):
+    return np.concatenate([np.asarray(params[name], dtype=np.float32).reshape(-1)
+                           for name, _ in MLP_LAYOUT])
+
+
+class Mlp:
+    """The seeding network on the GPU (one handle)."""
+
+    def __init__(self, params, cuda_stream=None):
+        self.h = mucal_mlp_create(params, cuda_stream)
+
+    def close(self):
+        if self.h is not None:
+            mucal_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def params(self, rounded=False):
+        return mucal_mlp_get_params(self.h, rounded)
+
+    def forward(self, X):
+        return mucal_mlp_forward(self.h, X)
+
+    def gradients(self, X, t):
+        return mucal_mlp_gradients(self.h, X, t)
+
+    def train(self, X, t, steps, lr):
+        return mucal_mlp_train(self.h, X, t, steps, lr)

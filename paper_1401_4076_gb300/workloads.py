@@ -75,3 +75,23 @@ def random_log_weights(n_bins: int, seed: int, scale: float = 0.3) -> np.ndarray
     rng = np.random.default_rng(seed)
     w = np.cumsum(rng.normal(scale=scale, size=n_bins))
     return w - w.max()
+
+
+def mlp_initial_params(seed: int, hidden: int = 128) -> np.ndarray:
+    """Seeded fan-in uniform initial parameters of the seeding network, as the
+    flat fp32 vector W1[128][4], b1, W2[128][128], b2, W3[128], b3."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shape, fan_in in (((hidden, 4), 4), ((hidden,), 4), ((hidden, hidden), hidden),
+                          ((hidden,), hidden), ((1, hidden), hidden), ((1,), hidden)):
+        lim = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-lim, lim, size=shape).reshape(-1))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_test_batch(n: int, seed: int):
+    """Seeded feature rows (4 columns, a few units wide) and smooth targets."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1.5, 1.5, size=(n, 4)).astype(np.float32)
+    t = (np.sin(X[:, 0]) * X[:, 1] + 0.5 * X[:, 2] ** 2 - 0.3 * X[:, 3]).astype(np.float32)
+    return X, t
