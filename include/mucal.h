@@ -100,7 +100,8 @@ typedef struct mucal_system_desc {
 typedef struct mucal_launch_config {
     int32_t kernel;            /* MUCAL_KERNEL_THREAD or MUCAL_KERNEL_GROUP */
     int32_t lanes_per_walker;  /* 1 for THREAD; 2, 4, 8, 16 or 32 for GROUP */
-    int32_t walkers_per_block; /* threads per block = walkers_per_block * lanes, <= 1024 */
+    int32_t walkers_per_block; /* threads per block = walkers_per_block * lanes: <= 1024 for
+                                  THREAD, a multiple of 32 and <= 512 for GROUP */
     int32_t bits_in_smem;      /* 1: stage each walker's occupation bitset in shared
                                   memory for the launch; 0: use it in global memory */
 } mucal_launch_config;

@@ -314,6 +314,8 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
             return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel needs lanes_per_walker in {2,4,8,16,32}");
         if ((sh.walkers_per_block * sh.lanes) % 32 != 0)
             return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel needs whole warps per block");
+        if (sh.walkers_per_block * sh.lanes > 512)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel blocks hold at most 512 threads");
     } else {
         return fail(c, MUCAL_ERR_INVALID_ARG, "unknown kernel %d", sh.kernel);
     }

@@ -19,6 +19,9 @@
 namespace mucal {
 namespace {
 
+// Largest block of the group kernel: leaves up to 128 registers per thread.
+constexpr int kGroupMaxThreads = 512;
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
 // multiply-high/low on words 0 and 2, high halves xor-ed into words 1 and 3
@@ -266,44 +269,110 @@ walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restr
 // slot).  The chain is therefore exactly the one-thread chain.  A warp's
 // groups step through the rounds in lock-step so no group diverges.
 // ---------------------------------------------------------------------------
-template <int D>
-struct NbWords {
-    uint32_t word[2 * D];   // word index of each neighbour in the bitset
-    uint32_t shift[2 * D];  // bit position, or 32 to read the neighbour as empty
+// Occupation-bit access for the group kernel.  In shared memory a neighbour
+// is addressed by its 32-bit shared address, in global memory by a pointer;
+// the bit position 32 reads as empty (used for the neighbour of b that is a).
+template <bool SHARED>
+struct BitAddr;
+
+template <>
+struct BitAddr<true> {
+    using A = uint32_t;
+    uint32_t base;
+    __device__ __forceinline__ explicit BitAddr(const uint32_t *bits)
+        : base((uint32_t)__cvta_generic_to_shared(bits)) {}
+    __device__ __forceinline__ A at(uint32_t site) const { return base + ((site >> 5) << 2); }
+    __device__ __forceinline__ static uint32_t load(A a)
+    {
+        uint32_t v;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+        return v;
+    }
 };
 
-template <int D>
-__device__ __forceinline__ void nb_words(const SysParams &p, uint32_t s, uint32_t skip, NbWords<D> &o)
-{
-    uint32_t nb[2 * D];
-    neighbours<D>(p, s, nb);
+template <>
+struct BitAddr<false> {
+    using A = const uint32_t *;
+    const uint32_t *base;
+    __device__ __forceinline__ explicit BitAddr(const uint32_t *bits) : base(bits) {}
+    __device__ __forceinline__ A at(uint32_t site) const { return base + (site >> 5); }
+    __device__ __forceinline__ static uint32_t load(A a)
+    {
+        uint32_t v;
+        asm volatile("ld.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+        return v;
+    }
+};
+
+template <int D, bool SHARED>
+struct NbSet {
+    typename BitAddr<SHARED>::A addr[2 * D];
+    uint32_t shift[2 * D];
+
+    __device__ __forceinline__ void build(const SysParams &p, const BitAddr<SHARED> &ba, uint32_t s,
+                                          uint32_t skip)
+    {
+        uint32_t nb[2 * D];
+        neighbours<D>(p, s, nb);
 #pragma unroll
-    for (int i = 0; i < 2 * D; ++i) {
-        o.word[i] = nb[i] >> 5;
-        o.shift[i] = (nb[i] == skip) ? 32u : (nb[i] & 31u);
+        for (int i = 0; i < 2 * D; ++i) {
+            addr[i] = ba.at(nb[i]);
+            shift[i] = (nb[i] == skip) ? 32u : (nb[i] & 31u);
+        }
+    }
+
+    __device__ __forceinline__ int count() const
+    {
+        uint32_t w[2 * D];
+#pragma unroll
+        for (int i = 0; i < 2 * D; ++i) w[i] = BitAddr<SHARED>::load(addr[i]);
+        int n = 0;
+#pragma unroll
+        for (int i = 0; i < 2 * D; ++i) n += (int)(__funnelshift_rc(w[i], 0u, shift[i]) & 1u);
+        return n;
+    }
+};
+
+template <bool SHARED>
+__device__ __forceinline__ uint32_t thr_load(const uint32_t *thr, int idx)
+{
+    if constexpr (SHARED) {
+        uint32_t v;
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(thr + idx);
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+        return v;
+    } else {
+        return __ldg(thr + idx);
     }
 }
 
-template <int D>
-__device__ __forceinline__ int nb_count(const uint32_t *bits, const NbWords<D> &o)
+// Broadcast a pair of list values from lane src: one shuffle when both fit
+// in 16 bits, two otherwise.
+template <typename IdxT>
+__device__ __forceinline__ void shfl_pair(uint32_t x, uint32_t y, int src, uint32_t &xo, uint32_t &yo)
 {
-    int n = 0;
-#pragma unroll
-    for (int i = 0; i < 2 * D; ++i) n += (int)(__funnelshift_rc(bits[o.word[i]], 0u, o.shift[i]) & 1u);
-    return n;
+    if constexpr (sizeof(IdxT) == 2) {
+        const uint32_t v = __shfl_sync(0xffffffffu, x | (y << 16), src);
+        xo = v & 0xFFFFu;
+        yo = v >> 16;
+    } else {
+        xo = __shfl_sync(0xffffffffu, x, src);
+        yo = __shfl_sync(0xffffffffu, y, src);
+    }
 }
 
-template <int D, typename IdxT, int G>
-__device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits,
-                            const uint32_t *thr, unsigned long long *hist, uint64_t A,
-                            uint32_t iter)
+template <int D, typename IdxT, int G, bool SB, bool ST>
+__device__ __forceinline__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits,
+                                            const uint32_t *thr, unsigned long long *hist,
+                                            uint64_t A, uint32_t iter)
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
     const int lane = threadIdx.x & 31;
     const int j = lane & (G - 1);
     const int gbase = lane - j;
-    IdxT *S = active ? walker_S<IdxT>(p, w) : nullptr;
+    IdxT *S = walker_S<IdxT>(p, w);
+    const BitAddr<SB> ba(bits);
     const uint32_t N = (uint32_t)p.N;
     const uint32_t holes = (uint32_t)(p.V - p.N);
     const uint64_t seed = p.seed_base + (uint64_t)w;
@@ -313,22 +382,32 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
     int row = bin * width + 2 * D;
     uint32_t run = 0;
     uint32_t acc = 0;
-    for (uint64_t t0 = 0; t0 < A; t0 += G) {
+    // random numbers and list reads of a batch are issued one batch early;
+    // commits that move a list slot such an early read covers patch it
+    uint32_t kn = 0, mn = 0, an = 0, bn = 0, r2n = 0;
+    auto draw = [&](uint64_t t0) {
         const uint64_t t = t0 + (uint64_t)j;
+        if (active && t < A) {
+            const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
+            kn = __umulhi(r.x, N);
+            mn = __umulhi(r.y, holes);
+            r2n = r.z;
+            an = S[kn];
+            bn = S[N + mn];
+        }
+    };
+    draw(0);
+    for (uint64_t t0 = 0; t0 < A; t0 += G) {
         const uint64_t left = A - t0;
         const int n_valid = left < (uint64_t)G ? (int)left : G;
         const bool valid = active && (j < n_valid);
-        uint32_t k = 0, m = 0, a = 0, b = 0, r2 = 0;
-        NbWords<D> wa, wb;
+        uint32_t k = kn, m = mn, a = an, b = bn;
+        const uint32_t r2 = r2n;
+        draw(t0 + G);
+        NbSet<D, SB> na, nb;
         if (valid) {
-            const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
-            k = __umulhi(r.x, N);
-            m = __umulhi(r.y, holes);
-            r2 = r.z;
-            a = S[k];
-            b = S[N + m];
-            nb_words<D>(p, a, 0xFFFFFFFFu, wa);
-            nb_words<D>(p, b, a, wb);
+            na.build(p, ba, a, 0xFFFFFFFFu);
+            nb.build(p, ba, b, a);
         }
         int pos = 0;
         bool done = !active;
@@ -336,18 +415,17 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
             bool accept = false;
             int de = 0;
             if (!done && valid && j >= pos) {
-                de = nb_count<D>(bits, wa) - nb_count<D>(bits, wb);
-                const uint32_t T = thr[row + de];
+                de = na.count() - nb.count();
+                const uint32_t T = thr_load<ST>(thr, row + de);
                 accept = (T == 0xFFFFFFFFu) || (r2 < T);
             }
             const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
             const int f = bal ? __ffs(bal) - 1 : G;
             const int src = gbase + (f < G ? f : 0);
             const int de_f = __shfl_sync(FULL, de, src);
-            const uint32_t a_f = __shfl_sync(FULL, a, src);
-            const uint32_t b_f = __shfl_sync(FULL, b, src);
-            const uint32_t k_f = __shfl_sync(FULL, k, src);
-            const uint32_t m_f = __shfl_sync(FULL, m, src);
+            uint32_t a_f, b_f, k_f, m_f;
+            shfl_pair<IdxT>(a, b, src, a_f, b_f);
+            shfl_pair<IdxT>(k, m, src, k_f, m_f);
             bool fix_a = false, fix_b = false;
             if (!done) {
                 if (f < G) {
@@ -369,6 +447,8 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
                     // the commit moved list slots k_f and N + m_f
                     fix_a = (j > f) && (k == k_f);
                     fix_b = (j > f) && (m == m_f);
+                    if (kn == k_f) an = b_f;
+                    if (mn == m_f) bn = a_f;
                     pos = f + 1;
                     if (pos >= n_valid) done = true;
                 } else {
@@ -380,8 +460,8 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
                 if (fix_a) a = b_f;
                 if (fix_b) b = a_f;
                 if (fix_a || fix_b) {
-                    nb_words<D>(p, a, 0xFFFFFFFFu, wa);
-                    nb_words<D>(p, b, a, wb);
+                    na.build(p, ba, a, 0xFFFFFFFFu);
+                    nb.build(p, ba, b, a);
                 }
             }
             __syncwarp(FULL);
@@ -398,29 +478,40 @@ __device__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bi
     }
 }
 
-template <int G>
-__global__ void __launch_bounds__(1024)
+template <int G, bool SB, bool ST>
+__device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
+                                           uint64_t sweeps, uint32_t iter)
+{
+    const int lw = threadIdx.x / G;
+    const bool active = lw < wk.count;
+    const int w = wk.walker0 + (active ? lw : 0);
+    const uint32_t *thr = ST ? smem : p.thr;
+    uint32_t *bits0 = SB ? smem + (ST ? thr_words_aligned(p) : 0)
+                         : p.bits + (size_t)wk.walker0 * (size_t)p.words;
+    uint32_t *bits = bits0 + (size_t)(active ? lw : 0) * p.words;
+    unsigned long long *hist = hist_row(p, w, wk.hist_row);
+    const uint64_t A = sweeps * (uint64_t)p.N;
+    if (p.d == 2) {
+        if (p.idx16) chain_group<2, uint16_t, G, SB, ST>(p, w, active, bits, thr, hist, A, iter);
+        else chain_group<2, uint32_t, G, SB, ST>(p, w, active, bits, thr, hist, A, iter);
+    } else {
+        if (p.idx16) chain_group<3, uint16_t, G, SB, ST>(p, w, active, bits, thr, hist, A, iter);
+        else chain_group<3, uint32_t, G, SB, ST>(p, w, active, bits, thr, hist, A, iter);
+    }
+}
+
+template <int G, bool SB, bool ST>
+__global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
-                    uint64_t sweeps, uint32_t iter, int bits_in_smem, int thr_in_smem)
+                    uint64_t sweeps, uint32_t iter)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const BlockWork wk = work[blockIdx.x];
     const SysParams &p = sys[wk.sys];
-    const BlockSetup bs = block_setup(p, wk, smem, bits_in_smem, thr_in_smem);
-    const int lw = threadIdx.x / G;
-    const bool active = lw < wk.count;
-    const int w = wk.walker0 + (active ? lw : 0);
-    uint32_t *bits = bs.bits0 + (size_t)(active ? lw : 0) * p.words;
-    unsigned long long *hist = hist_row(p, w, wk.hist_row);
-    const uint64_t A = sweeps * (uint64_t)p.N;
-    if (p.d == 2) {
-        if (p.idx16) chain_group<2, uint16_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
-        else chain_group<2, uint32_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
-    } else {
-        if (p.idx16) chain_group<3, uint16_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
-        else chain_group<3, uint32_t, G>(p, w, active, bits, bs.thr, hist, A, iter);
-    }
-    block_finish(bs, bits_in_smem);
+    const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+    (void)bs;
+    group_body<G, SB, ST>(p, wk, smem, sweeps, iter);
+    block_finish(bs, SB ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -546,14 +637,57 @@ cudaError_t walker_update_max_smem(int *bytes)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const void *fns[] = {(const void *)walker_update_thread, (const void *)walker_update_group<2>,
-                         (const void *)walker_update_group<4>, (const void *)walker_update_group<8>,
-                         (const void *)walker_update_group<16>, (const void *)walker_update_group<32>};
+#define MUCAL_GROUP_FNS(G)                                                              \
+    (const void *)walker_update_group<G, true, true>,                                   \
+        (const void *)walker_update_group<G, true, false>,                              \
+        (const void *)walker_update_group<G, false, true>,                              \
+        (const void *)walker_update_group<G, false, false>
+    const void *fns[] = {(const void *)walker_update_thread, MUCAL_GROUP_FNS(2), MUCAL_GROUP_FNS(4),
+                         MUCAL_GROUP_FNS(8), MUCAL_GROUP_FNS(16), MUCAL_GROUP_FNS(32)};
+#undef MUCAL_GROUP_FNS
     for (const void *fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, *bytes);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+template <int G, bool SB, bool ST>
+cudaError_t launch_group_t(int n_blocks, int threads, size_t smem, const SysParams *dev_sys,
+                           const BlockWork *dev_work, uint64_t sweeps, uint32_t iteration,
+                           cudaStream_t stream)
+{
+    walker_update_group<G, SB, ST><<<n_blocks, threads, smem, stream>>>(dev_sys, dev_work, sweeps,
+                                                                        iteration);
+    return cudaGetLastError();
+}
+
+template <int G>
+cudaError_t launch_group_g(const LaunchShape &sh, int n_blocks, int threads, const SysParams *dev_sys,
+                           const BlockWork *dev_work, uint64_t sweeps, uint32_t iteration,
+                           cudaStream_t stream)
+{
+    if (sh.bits_in_smem && sh.thr_in_smem)
+        return launch_group_t<G, true, true>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+    if (sh.bits_in_smem)
+        return launch_group_t<G, true, false>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+    if (sh.thr_in_smem)
+        return launch_group_t<G, false, true>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+    return launch_group_t<G, false, false>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+}
+
+cudaError_t launch_group_dispatch(const LaunchShape &sh, int n_blocks, int threads,
+                                  const SysParams *dev_sys, const BlockWork *dev_work,
+                                  uint64_t sweeps, uint32_t iteration, cudaStream_t stream)
+{
+    switch (sh.lanes) {
+    case 2: return launch_group_g<2>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 4: return launch_group_g<4>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 8: return launch_group_g<8>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 16: return launch_group_g<16>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 32: return launch_group_g<32>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
@@ -567,31 +701,7 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
             dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
         return cudaGetLastError();
     }
-    switch (shape.lanes) {
-    case 2:
-        walker_update_group<2><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
-        break;
-    case 4:
-        walker_update_group<4><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
-        break;
-    case 8:
-        walker_update_group<8><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
-        break;
-    case 16:
-        walker_update_group<16><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
-        break;
-    case 32:
-        walker_update_group<32><<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
-        break;
-    default:
-        return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return launch_group_dispatch(shape, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
 }
 
 size_t thr_smem_words(const SysParams &p) { return thr_words_aligned(p); }
