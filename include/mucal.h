@@ -210,6 +210,44 @@ int mucal_histogram_device_ptr(void *ctx, int32_t sys, void **dptr);
 /* Library version string. */
 const char *mucal_version(void);
 
+/* ---- allocation-free walker update (no counterpart in the paper) ---------
+ * For callers that cannot allocate device memory: code running where
+ * cudaMalloc is not allowed or not wanted, such as inside a memory pool that
+ * another framework owns, under a fixed device-memory budget, or between
+ * set-up and teardown of a process whose allocator must stay untouched.  It
+ * runs what mucal_run_iteration runs for one system (sweeps * N attempted
+ * jump moves per walker with fixed thresholds, then H(E) = sum of the
+ * walkers' histograms) on device buffers the caller owns, and allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *   sys        one system descriptor (as for mucal_init_systems)
+ *   bits       device uint32[n_walkers][ceil(V/32)] occupation bitsets (in/out)
+ *   S          device uint16 (V <= 65536) or uint32 [n_walkers][V] particle
+ *              sites then empty sites (in/out)
+ *   E          device int32[n_walkers] energies, inside the window (in/out)
+ *   thr        device uint32[n_bins][4d+1] thresholds as built by
+ *              mucal_set_weights (read with mucal_get_thresholds) (in)
+ *   H          device uint64[n_bins], overwritten with H(E) (out)
+ *   cuda_stream the stream to run on (NULL = legacy default stream); the call
+ *              returns after that stream has finished the work.
+ * Scratch (per-block histogram rows, accept counters, an input-check flag)
+ * is a fixed array of 40 MiB in the library that every GPU which loads the
+ * library holds until the process exits.  Limits: n_walkers <= 1048576 and
+ * ceil(n_walkers / 32) * n_bins <= 4194304; larger sizes return
+ * MUCAL_ERR_INVALID_ARG with a message.  Energies outside the window or list
+ * entries outside the lattice are detected on the device and reported as
+ * MUCAL_ERR_INVALID_ARG (the state is then left unchanged).  The first call
+ * on a device looks up the scratch array's device address and sets the
+ * kernels' shared-memory limit; make that first call before any stream
+ * capture.  All calls share the one scratch array, which keeps the last
+ * call's contents (the call clears what must start at zero): calls that
+ * overlap on the GPU, from several streams or threads, race and give wrong
+ * results.  mucal_run_walkers_noalloc_error() returns the message of the
+ * calling thread's last failure. */
+int mucal_run_walkers_noalloc(const mucal_system_desc *sys, int64_t sweeps, uint32_t iteration,
+                              uint32_t *bits, void *S, int32_t *E, const uint32_t *thr, uint64_t *H,
+                              void *cuda_stream);
+const char *mucal_run_walkers_noalloc_error(void);
+
 /* ---- weight-seeding network (not part of the paper) ---------------------
  * A 4-128-128-1 multilayer perceptron with GELU activations (gelu(z) =
  * z Phi(z)) that maps a caller-built feature vector of (d, L, rho, E/V) to a

@@ -12,8 +12,12 @@
 //     in order; after each accepted move the remaining lanes re-evaluate
 //     against the updated state, so the chain is exactly the one-thread chain.
 #include <cstdint>
+#include <mutex>
+#include <string>
+
 #include <cuda_runtime.h>
 
+#include "mucal.h"
 #include "mucal_internal.h"
 
 namespace mucal {
@@ -721,3 +725,224 @@ cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_s
 }
 
 }  // namespace mucal
+
+// ===========================================================================
+// Allocation-free walker update.
+//
+// Some callers cannot allocate device memory: code that runs where
+// cudaMalloc is not allowed or not wanted (inside a memory pool another
+// framework owns, under a strict device-memory budget, or in a process whose
+// allocator must not be touched between set-up and teardown).  For them this
+// section offers one entry point that runs one iteration's walker update and
+// histogram sum for a single system entirely on buffers the caller owns.
+// Its scratch (the per-block histogram rows, the per-walker accept counters
+// and an input-check flag) lives in the file-scope array below, which every
+// GPU that loads this library holds until the process exits.
+// ===========================================================================
+
+namespace mucal {
+namespace {
+
+// Scratch layout, in 64-bit words: [check flag, padded to 32 words]
+// [accept counters: kNoAllocMaxWalkers] [histogram rows: kNoAllocHistWords].
+constexpr int kNoAllocMaxWalkers = 1 << 20;
+constexpr size_t kNoAllocHistWords = (size_t)1 << 22;
+constexpr size_t kNoAllocWords = 32 + (size_t)kNoAllocMaxWalkers + kNoAllocHistWords;
+constexpr int kNoAllocLanes = 8;
+constexpr int kNoAllocWalkersPerBlock = 32;
+
+}  // namespace
+
+}  // namespace mucal
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[mucal::kNoAllocWords];
+
+namespace mucal {
+namespace {
+
+// Flags the call as invalid if an energy lies outside the window or a list
+// entry outside the lattice; the walker update then does nothing.
+__global__ void noalloc_check_kernel(SysParams p, unsigned long long *flag)
+{
+    const size_t total = (size_t)p.n_walkers * (size_t)p.V;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (size_t i = i0; i < (size_t)p.n_walkers; i += stride) {
+        const int bin = p.E[i] - p.e_lo;
+        if (bin < 0 || bin >= p.n_bins) atomicOr(flag, 1ull);
+    }
+    for (size_t i = i0; i < total; i += stride) {
+        const uint32_t s = p.idx16 ? (uint32_t)reinterpret_cast<const uint16_t *>(p.S)[i]
+                                   : reinterpret_cast<const uint32_t *>(p.S)[i];
+        if (s >= (uint32_t)p.V) atomicOr(flag, 2ull);
+    }
+}
+
+template <bool SB, bool ST>
+__global__ void __launch_bounds__(kGroupMaxThreads, 1)
+walker_update_noalloc(SysParams p, uint64_t sweeps, uint32_t iter, const unsigned long long *flag)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    if (*flag != 0) return;
+    BlockWork wk;
+    wk.sys = 0;
+    wk.walker0 = blockIdx.x * kNoAllocWalkersPerBlock;
+    wk.count = min(kNoAllocWalkersPerBlock, p.n_walkers - wk.walker0);
+    wk.hist_row = blockIdx.x;
+    const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+    group_body<kNoAllocLanes, SB, ST>(p, wk, smem, sweeps, iter);
+    block_finish(bs, SB ? 1 : 0);
+}
+
+// Per-device set-up: the device address of the scratch array (the array's
+// name is only a host-side stand-in in host code) and the shared-memory
+// opt-in of the kernel variants.
+struct NoAllocDevice {
+    unsigned long long *scratch = nullptr;
+    int max_smem = 0;
+    bool ready = false;
+};
+
+std::mutex g_noalloc_mutex;
+NoAllocDevice g_noalloc_dev[64];
+
+cudaError_t noalloc_setup(int dev, NoAllocDevice **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        int smem = 0;
+        e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        const void *fns[] = {(const void *)walker_update_noalloc<true, true>,
+                             (const void *)walker_update_noalloc<true, false>,
+                             (const void *)walker_update_noalloc<false, true>,
+                             (const void *)walker_update_noalloc<false, false>};
+        for (const void *fn : fns) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+        }
+        d.scratch = static_cast<unsigned long long *>(ptr);
+        d.max_smem = smem;
+        d.ready = true;
+    }
+    *out = &d;
+    return cudaSuccess;
+}
+
+thread_local std::string g_noalloc_error;
+
+int noalloc_fail(int code, const std::string &msg)
+{
+    g_noalloc_error = msg;
+    return code;
+}
+
+}  // namespace
+}  // namespace mucal
+
+extern "C" const char *mucal_run_walkers_noalloc_error(void)
+{
+    return mucal::g_noalloc_error.c_str();
+}
+
+extern "C" int mucal_run_walkers_noalloc(const mucal_system_desc *sys, int64_t sweeps,
+                                         uint32_t iteration, uint32_t *bits, void *S, int32_t *E,
+                                         const uint32_t *thr, uint64_t *H, void *cuda_stream)
+{
+    using namespace mucal;
+    if (!sys || !bits || !S || !E || !thr || !H)
+        return noalloc_fail(MUCAL_ERR_INVALID_ARG, "a buffer pointer is NULL");
+    const mucal_system_desc &d = *sys;
+    if ((d.d != 2 && d.d != 3) || d.L < 3 || d.L > 4096)
+        return noalloc_fail(MUCAL_ERR_INVALID_ARG, "need d in {2,3} and 3 <= L <= 4096");
+    const uint64_t V = d.d == 2 ? (uint64_t)d.L * d.L : (uint64_t)d.L * d.L * d.L;
+    if (V > (1u << 24) || V * (uint64_t)d.L >= (1ull << 32))
+        return noalloc_fail(MUCAL_ERR_INVALID_ARG, "lattice too large");
+    if (d.N <= 0 || (uint64_t)d.N >= V) return noalloc_fail(MUCAL_ERR_INVALID_ARG, "need 0 < N < L^d");
+    if (d.n_walkers <= 0 || d.n_walkers > kNoAllocMaxWalkers)
+        return noalloc_fail(MUCAL_ERR_INVALID_ARG,
+                            "n_walkers must be in [1, 1048576] for the allocation-free call");
+    int e_lo = d.e_lo, e_hi = d.e_hi;
+    if (e_lo == 0 && e_hi == 0) {
+        e_lo = -d.d * d.N;
+        e_hi = 0;
+    } else if (e_lo < -d.d * d.N || e_hi > 0 || e_lo >= e_hi) {
+        return noalloc_fail(MUCAL_ERR_INVALID_ARG, "window must satisfy -dN <= e_lo < e_hi <= 0");
+    }
+    if (sweeps < 1 || (uint64_t)sweeps * (uint64_t)d.N >= (1ull << 40))
+        return noalloc_fail(MUCAL_ERR_INVALID_ARG, "need sweeps >= 1 and sweeps * N < 2^40");
+    SysParams p{};
+    p.d = d.d;
+    p.L = d.L;
+    p.N = d.N;
+    p.V = (int32_t)V;
+    p.L2 = d.L * d.L;
+    p.e_lo = e_lo;
+    p.n_bins = e_hi - e_lo + 1;
+    p.width = 4 * d.d + 1;
+    p.words = (int32_t)((V + 31) / 32);
+    p.idx16 = V <= 65536 ? 1 : 0;
+    p.n_walkers = d.n_walkers;
+    p.magL = (uint32_t)(((1ull << 32) + (uint64_t)d.L - 1) / (uint64_t)d.L);
+    p.seed_base = d.seed_base;
+    const int blocks = (d.n_walkers + kNoAllocWalkersPerBlock - 1) / kNoAllocWalkersPerBlock;
+    if ((size_t)blocks * (size_t)p.n_bins > kNoAllocHistWords)
+        return noalloc_fail(MUCAL_ERR_INVALID_ARG,
+                            "ceil(n_walkers / 32) * n_bins exceeds the 4194304 histogram entries "
+                            "of the allocation-free scratch");
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    NoAllocDevice *nd = nullptr;
+    if (ce == cudaSuccess) ce = noalloc_setup(dev, &nd);
+    if (ce != cudaSuccess)
+        return noalloc_fail(MUCAL_ERR_CUDA, std::string("set-up failed: ") + cudaGetErrorString(ce));
+    unsigned long long *flag = nd->scratch;
+    p.accepts = nd->scratch + 32;
+    p.hist = nd->scratch + 32 + kNoAllocMaxWalkers;
+    p.hist_rows = blocks;
+    p.bits = bits;
+    p.S = S;
+    p.E = E;
+    p.thr = thr;
+    p.H = reinterpret_cast<unsigned long long *>(H);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t thr_bytes = thr_words_aligned(p) * 4;
+    const size_t bits_bytes = (size_t)kNoAllocWalkersPerBlock * (size_t)p.words * 4;
+    const bool sb = bits_bytes <= (size_t)nd->max_smem;
+    const bool stt = thr_bytes + (sb ? bits_bytes : 0) <= (size_t)nd->max_smem;
+    const size_t smem = (sb ? bits_bytes : 0) + (stt ? thr_bytes : 0);
+    const int threads = kNoAllocWalkersPerBlock * kNoAllocLanes;
+    // scratch keeps the previous call's contents: clear what must start at zero
+    ce = cudaMemsetAsync(flag, 0, sizeof(unsigned long long), st);
+    if (ce == cudaSuccess)
+        ce = cudaMemsetAsync(p.hist, 0, (size_t)blocks * (size_t)p.n_bins * 8, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(p.H, 0, (size_t)p.n_bins * 8, st);
+    if (ce == cudaSuccess) {
+        noalloc_check_kernel<<<256, 256, 0, st>>>(p, flag);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) {
+        if (sb && stt) walker_update_noalloc<true, true><<<blocks, threads, smem, st>>>(p, (uint64_t)sweeps, iteration, flag);
+        else if (sb) walker_update_noalloc<true, false><<<blocks, threads, smem, st>>>(p, (uint64_t)sweeps, iteration, flag);
+        else if (stt) walker_update_noalloc<false, true><<<blocks, threads, smem, st>>>(p, (uint64_t)sweeps, iteration, flag);
+        else walker_update_noalloc<false, false><<<blocks, threads, smem, st>>>(p, (uint64_t)sweeps, iteration, flag);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) {
+        dim3 grid((p.n_bins + 255) / 256, (p.hist_rows + kReduceWalkers - 1) / kReduceWalkers);
+        hist_reduce_kernel<<<grid, 256, 0, st>>>(p);
+        ce = cudaGetLastError();
+    }
+    unsigned long long bad = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&bad, flag, sizeof bad, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return noalloc_fail(MUCAL_ERR_CUDA, cudaGetErrorString(ce));
+    if (bad & 1ull) return noalloc_fail(MUCAL_ERR_INVALID_ARG, "an energy E lies outside the window");
+    if (bad & 2ull) return noalloc_fail(MUCAL_ERR_INVALID_ARG, "a list entry of S is not a lattice site");
+    return MUCAL_OK;
+}

@@ -40,6 +40,7 @@ EXPORTED = [
     "mucal_get_system_info", "mucal_get_stats", "mucal_histogram_device_ptr", "mucal_version",
     "mucal_mlp_param_count", "mucal_mlp_create", "mucal_mlp_destroy", "mucal_mlp_last_error",
     "mucal_mlp_get_params", "mucal_mlp_forward", "mucal_mlp_gradients", "mucal_mlp_train",
+    "mucal_run_walkers_noalloc", "mucal_run_walkers_noalloc_error",
 ]
 
 
@@ -107,6 +108,9 @@ def load_library(path: str = LIB_PATH):
         "mucal_mlp_forward": (ctypes.c_int, [P, P, I64, P]),
         "mucal_mlp_gradients": (ctypes.c_int, [P, P, P, I64, P, P]),
         "mucal_mlp_train": (ctypes.c_int, [P, P, P, I64, I32, ctypes.c_float, P]),
+        "mucal_run_walkers_noalloc": (ctypes.c_int, [ctypes.POINTER(mucal_system_desc), I64, U32,
+                                                     P, P, P, P, P, P]),
+        "mucal_run_walkers_noalloc_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +246,18 @@ def mucal_histogram_device_ptr(ctx, sys):
 
 def mucal_version():
     return load_library().mucal_version().decode()
+
+
+def mucal_run_walkers_noalloc(desc, sweeps, iteration, bits_ptr, S_ptr, E_ptr, thr_ptr, H_ptr,
+                              cuda_stream=None):
+    """Allocation-free walker update on caller-owned device buffers (raw
+    device pointers as ints); see include/mucal.h for layouts and limits."""
+    lib = load_library()
+    d = mucal_system_desc(*desc)
+    rc = lib.mucal_run_walkers_noalloc(ctypes.byref(d), int(sweeps), int(iteration) & 0xFFFFFFFF,
+                                       bits_ptr, S_ptr, E_ptr, thr_ptr, H_ptr, cuda_stream)
+    if rc != MUCAL_OK:
+        raise MucalError(rc, lib.mucal_run_walkers_noalloc_error().decode())
 
 
 # --------------------------------------------------------------------------
