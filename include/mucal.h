@@ -256,7 +256,8 @@ const char *mucal_run_walkers_noalloc_error(void);
  * judges unchanged (the plain start lnW = 0 stays available).  Parameters:
  * fp32 master copy and Adam state; the forward and backward passes use the
  * bf16-rounded parameters, run the 128x128 layer on the tensor cores (bf16 x
- * bf16, fp32 accumulation) and everything else in fp32.
+ * bf16, fp32 accumulation; the layer-1 activations enter it as two bf16 terms,
+ * hi + lo) and everything else in fp32.
  * Parameter vector (fp32, 17281 = mucal_mlp_param_count()): W1[128][4],
  * b1[128], W2[128][128] (row = output unit), b2[128], W3[128], b3.
  * Loss: mean over the batch of (y - t)^2.  All buffers are host buffers,

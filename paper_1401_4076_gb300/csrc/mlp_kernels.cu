@@ -7,7 +7,10 @@
 // Numerics: parameters kept in fp32 (master copy, Adam state) and used in
 // bf16; the 128x128 contractions run on the tensor cores as bf16 x bf16 with
 // fp32 accumulation (mma.sync m16n8k16); the K=4 input layer, the N=1 output
-// layer, GELU and all reductions are fp32.
+// layer, GELU and all reductions are fp32.  In the forward pass the layer-1
+// activations enter the tensor cores split into two bf16 terms (hi + lo),
+// which keeps the network's output smooth in its inputs to about 1e-5
+// relative instead of the 4e-3 steps a single bf16 rounding would leave.
 //
 // Parameter vector (fp32, 17281 entries): W1[128][4], b1[128], W2[128][128]
 // (row = output unit), b2[128], W3[128], b3.
@@ -93,7 +96,8 @@ __device__ __forceinline__ void load_b(uint32_t (&b)[2], const __nv_bfloat16 *Mt
 struct MlpShared {
     __nv_bfloat16 w2[H * LDS];     // W2[out][in]
     __nv_bfloat16 w2t[H * LDS];    // W2^T[in][out]
-    __nv_bfloat16 h1[WARPS][ROWS_PER_WARP * LDS];
+    __nv_bfloat16 h1[WARPS][ROWS_PER_WARP * LDS];     // bf16(h1)
+    __nv_bfloat16 h1lo[WARPS][ROWS_PER_WARP * LDS];   // bf16(h1 - bf16(h1))
     __nv_bfloat16 dz2[WARPS][ROWS_PER_WARP * LDS];
     float w1[H * 4], b1[H], b2[H], w3[H];
     float b3;
@@ -137,7 +141,10 @@ mlp_rows_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restrict__ 
 
     const int64_t r0 = (int64_t)blockIdx.x * ROWS_PER_BLOCK + (int64_t)warp * ROWS_PER_WARP;
     __nv_bfloat16 *h1s = sm.h1[warp];
-    // ---- layer 1 (K = 4, fp32): lane owns units n = lane + 32 q for all 16 rows
+    __nv_bfloat16 *h1l = sm.h1lo[warp];
+    // ---- layer 1 (K = 4, fp32): lane owns units n = lane + 32 q for all 16 rows.
+    // h1 enters the tensor cores as the sum of two bf16 numbers (hi + lo), so
+    // the activations keep about 16 bits of precision while W2 stays bf16.
     float xr[ROWS_PER_WARP][4];
 #pragma unroll
     for (int r = 0; r < ROWS_PER_WARP; ++r) {
@@ -153,8 +160,10 @@ mlp_rows_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restrict__ 
 #pragma unroll
         for (int r = 0; r < ROWS_PER_WARP; ++r) {
             const float z = bb + xr[r][0] * w0 + xr[r][1] * w1 + xr[r][2] * w2 + xr[r][3] * w3;
-            const __nv_bfloat16 h = __float2bfloat16_rn(gelu_f(z));
+            const float hf = gelu_f(z);
+            const __nv_bfloat16 h = __float2bfloat16_rn(hf);
             h1s[r * LDS + n] = h;
+            h1l[r * LDS + n] = __float2bfloat16_rn(hf - __bfloat162float(h));
             if (TRAIN) {
                 const int64_t row = r0 + r;
                 if (row < ldT) h1T[(size_t)n * ldT + row] = h;
@@ -170,13 +179,15 @@ mlp_rows_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restrict__ 
         for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
 #pragma unroll
     for (int ks = 0; ks < H / 16; ++ks) {
-        uint32_t a[4];
+        uint32_t a[4], al[4];
         load_a(a, h1s, LDS, ks * 16, lane);
+        load_a(al, h1l, LDS, ks * 16, lane);
 #pragma unroll
         for (int nt = 0; nt < H / 8; ++nt) {
             uint32_t b[2];
             load_b(b, sm.w2, LDS, nt * 8, ks * 16, lane);
             mma16816(acc[nt], a, b);
+            mma16816(acc[nt], al, b);
         }
     }
     // ---- epilogue: h2 = gelu(z2 + b2), y = h2 . W3 + b3 (rows g and g + 8)

@@ -1,0 +1,346 @@
+"""Learned seeding of the multicanonical weights (not part of the paper).
+
+The iteration of Sec. 2 starts from some W^0 and improves it with every
+histogram; W = 1/Omega is its fixed point.  This module trains the library's
+GPU network on ln Omega estimates that converged runs of the method itself
+produced on small lattices, and uses it to propose W^0 = 1/Omega_pred for a
+larger lattice.  The proposal only changes where the iteration starts: the
+walkers, the recursion and the flatness judgement are unchanged, and the
+plain start lnW = 0 remains available as fallback and reference.
+
+Network input: (d, L, rho, E/V), encoded as
+    x = (2 (d - 2.5), 16 / L, 10 rho - 0.5, 2 (E/V) / (d rho) + 1);
+output: ln Omega(E) / V divided by the ideal-gas entropy density
+ln C(V, N) / V, i.e. ln Omega(E) / ln C(V, N), a number in [0, 1].
+
+All simulation and training runs in libmucal on the GPU; this module only
+arranges inputs and collects results.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import mucal as m
+
+
+def ln_binomial(V: int, N: int) -> float:
+    return math.lgamma(V + 1) - math.lgamma(N + 1) - math.lgamma(V - N + 1)
+
+
+def features(d: int, L: int, N: int, E: np.ndarray) -> np.ndarray:
+    """Network inputs for energies E of a d-dimensional L^d lattice with N particles."""
+    V = L ** d
+    rho = N / V
+    e = np.asarray(E, dtype=np.float64) / V
+    X = np.empty((len(e), 4), dtype=np.float32)
+    X[:, 0] = 2.0 * (d - 2.5)
+    X[:, 1] = 16.0 / L
+    X[:, 2] = 10.0 * rho - 0.5
+    X[:, 3] = 2.0 * e / (d * rho) + 1.0
+    return X
+
+
+def ln_omega_estimate(lnW: np.ndarray, H: np.ndarray, V: int, N: int) -> np.ndarray:
+    """ln Omega(E) = ln H(E) - lnW(E) on visited bins (W = 1/Omega makes H flat,
+    Sec. 2), shifted so that the visited bins carry all C(V, N) states; NaN
+    where H = 0."""
+    H = np.asarray(H)
+    out = np.full(len(H), np.nan)
+    vis = H > 0
+    out[vis] = np.log(H[vis].astype(np.float64)) - np.asarray(lnW)[vis]
+    mx = out[vis].max()
+    lse = mx + math.log(np.exp(out[vis] - mx).sum())
+    out[vis] += ln_binomial(V, N) - lse
+    return out
+
+
+@dataclass
+class RunResult:
+    desc: tuple
+    iterations: int
+    flatness: list
+    converged: bool
+    wall_s: float
+    lnW: np.ndarray
+    H: np.ndarray
+    attempts: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None, goal=0.5,
+                    scheme=m.MUCAL_SCHEME_RECURSIVE, cuda_stream=None, launch=None,
+                    final_sweeps: int = 0, relax_iters: int = 0, relax_tol: float = 0.0):
+    """Run the weight iteration of Sec. 2 for several systems in one context
+    (one launch per iteration) until each reaches flatness >= goal inside its
+    target window (t_lo, t_hi) or max_iter iterations.  A system that has
+    converged keeps running with frozen weights (its histogram then serves the
+    ln Omega estimate).  Returns one RunResult per system.
+
+    relax_iters: iterations run with the starting weights held fixed before
+    the first update (their histograms are discarded).  Walkers start from
+    random placements, which are equilibrium states of lnW = 0 only; the
+    update of Sec. 2 assumes equilibrium runs, so a start from other weights
+    first lets the walkers relax to them.  These iterations count towards
+    the reported iterations and wall time.  With relax_tol > 0, relax_iters is
+    a cap and the relaxation of a system ends early once the mean energy of
+    its histogram moves by less than relax_tol times the window width from
+    one iteration to the next.
+    """
+    n = len(systems)
+    t0 = time.perf_counter()
+    with m.Mucal(systems, cuda_stream=cuda_stream) as mc:
+        if launch:
+            mc.set_launch(**launch)
+        for i in range(n):
+            if lnW0 is not None and lnW0[i] is not None:
+                mc.set_weights(i, lnW0[i])
+            if targets is not None and targets[i] is not None:
+                mc.set_target_window(i, *targets[i])
+        done = [False] * n
+        iters = [0] * n
+        flat = [[] for _ in range(n)]
+        walls = [0.0] * n
+        attempts = [0] * n
+        Hs = [None] * n
+        relaxing = [relax_iters > 0] * n
+        relaxed = [0] * n
+        last_mean = [None] * n
+        for it in range(max_iter):
+            mc.run_iteration(sweeps, it)
+            for i in range(n):
+                if done[i]:
+                    continue
+                iters[i] = it + 1
+                attempts[i] += sweeps * systems[i][2] * systems[i][3]
+                if relaxing[i]:
+                    flat[i].append(float("nan"))
+                    relaxed[i] += 1
+                    stop = relaxed[i] >= relax_iters
+                    if not stop and relax_tol > 0:
+                        H = mc.histogram(i).astype(np.float64)
+                        mean = float((H * np.arange(len(H))).sum() / max(H.sum(), 1.0))
+                        if last_mean[i] is not None and abs(mean - last_mean[i]) < relax_tol * len(H):
+                            stop = True
+                        last_mean[i] = mean
+                    if stop:
+                        relaxing[i] = False
+                    continue
+                H = mc.histogram(i)
+                lnW, f = mc.update_weights(i, scheme)
+                flat[i].append(f)
+                Hs[i] = H
+                if f >= goal:
+                    done[i] = True
+                    walls[i] = time.perf_counter() - t0
+            if all(done):
+                break
+        for i in range(n):
+            if not done[i]:
+                walls[i] = time.perf_counter() - t0
+        results = []
+        final_H = [None] * n
+        lnWs = [mc.weights(i) for i in range(n)]
+        if final_sweeps:
+            # one more iteration with the final weights for the ln Omega estimate
+            for i in range(n):
+                mc.set_weights(i, lnWs[i])
+            mc.run_iteration(final_sweeps, max_iter + 1)
+            for i in range(n):
+                final_H[i] = mc.histogram(i)
+        for i in range(n):
+            results.append(RunResult(tuple(systems[i]), iters[i], flat[i], done[i], walls[i],
+                                     lnWs[i], final_H[i] if final_sweeps else Hs[i],
+                                     attempts[i]))
+    return results
+
+
+def training_set(results):
+    """(X, t) rows from converged runs: every visited bin of the final
+    histogram with its ln Omega estimate, normalised by ln C(V, N)."""
+    Xs, ts = [], []
+    for r in results:
+        d, L, N, W, lo, hi, seed = r.desc
+        V = L ** d
+        e_lo = -d * N if (lo == 0 and hi == 0) else lo
+        lo_est = ln_omega_estimate(r.lnW, r.H, V, N)
+        ok = ~np.isnan(lo_est)
+        E = e_lo + np.nonzero(ok)[0]
+        Xs.append(features(d, L, N, E))
+        ts.append((lo_est[ok] / ln_binomial(V, N)).astype(np.float32))
+    return np.concatenate(Xs), np.concatenate(ts)
+
+
+def train(X, t, steps: int = 3000, lr: float = 2e-3, seed: int = 0, cuda_stream=None):
+    """Train the GPU network (full-batch Adam in the library) and return it."""
+    from .workloads import mlp_initial_params
+    net = m.Mlp(mlp_initial_params(seed), cuda_stream=cuda_stream)
+    loss = None
+    done = 0
+    while done < steps:
+        k = min(500, steps - done)
+        loss = net.train(X, t, steps=k, lr=lr)
+        done += k
+    return net, loss
+
+
+def seed_weights(net, d: int, L: int, N: int, e_lo: int, e_hi: int) -> np.ndarray:
+    """lnW^0(E) = -ln Omega_pred(E) over the window, shifted to max 0."""
+    E = np.arange(e_lo, e_hi + 1)
+    y = net.forward(features(d, L, N, E)).astype(np.float64)
+    lnW = -y * ln_binomial(L ** d, N)
+    return lnW - lnW.max()
+
+
+def window_fraction(d: int, N: int, frac: float):
+    """Energy window [-frac * d * N, 0]: the upper part of the full range
+    [-dN, 0], from the gas side down to frac of the maximal bond count."""
+    return (-int(frac * d * N), 0)
+
+
+def small_training_systems(frac: float = 0.5, walkers: int = 512, seed_base: int = 0,
+                           L2=(12, 16, 20, 24, 28, 32, 40), L3=(6, 8, 10, 12, 14),
+                           rhos=(0.05, 0.07, 0.09, 0.1, 0.11, 0.13)):
+    """Descriptors of the small systems whose converged weights train the network."""
+    out = []
+    seed = seed_base
+    for d, Ls in ((2, L2), (3, L3)):
+        for L in Ls:
+            for rho in rhos:
+                N = int(round(rho * L ** d))
+                lo, hi = window_fraction(d, N, frac)
+                out.append((d, L, N, walkers, lo, hi, seed))
+                seed += walkers
+    return out
+
+
+def compare_plain_and_seeded(net, desc, sweeps: int, max_iter: int, relax_iters: int = 30,
+                             relax_tol: float = 0.01, cuda_stream=None):
+    """Iterations and wall time to flatness from lnW = 0 and from the network's
+    seed, same system, seeds, sweeps and window."""
+    d, L, N, W, lo, hi, seed = desc
+    seedW = seed_weights(net, d, L, N, lo, hi)
+    plain = iterate_to_flat([desc], sweeps, max_iter, cuda_stream=cuda_stream)[0]
+    seeded = iterate_to_flat([desc], sweeps, max_iter, lnW0=[seedW], relax_iters=relax_iters,
+                             relax_tol=relax_tol, cuda_stream=cuda_stream)[0]
+    return plain, seeded, seedW
+
+
+def ladder(net, rungs, frac: float, walkers: int, sweeps: int, max_iter: int, X, t,
+           train_steps: int = 5000, compare: bool = True, log=None, seed_base: int = 10 ** 7):
+    """Climb in lattice size: seed each rung from the current network, run the
+    iteration to flatness, add the converged ln Omega estimate to the training
+    rows and continue training (warm start) before the next rung.  Every rung
+    is trained only on smaller lattices.  Returns (network, records)."""
+    records = []
+    for k, (d, L, rho) in enumerate(rungs):
+        N = int(round(rho * L ** d))
+        lo, hi = window_fraction(d, N, frac)
+        desc = (d, L, N, walkers, lo, hi, seed_base + k * walkers)
+        seedW = None
+        if compare:
+            plain, seeded, seedW = compare_plain_and_seeded(net, desc, sweeps, max_iter)
+        else:
+            plain = None
+            seeded = iterate_to_flat([desc], sweeps, max_iter,
+                                     lnW0=[seed_weights(net, d, L, N, lo, hi)],
+                                     relax_iters=30, relax_tol=0.01)[0]
+        rec = {"system": {"d": d, "L": L, "N": N, "walkers": walkers, "window": [lo, hi],
+                          "sweeps_per_iteration": sweeps},
+               "seeded": {"iterations": seeded.iterations, "converged": seeded.converged,
+                          "wall_s": round(seeded.wall_s, 3), "flatness": seeded.flatness[-1],
+                          "relax_iterations": int(np.isnan(seeded.flatness).sum())}}
+        if plain is not None:
+            rec["plain"] = {"iterations": plain.iterations, "converged": plain.converged,
+                            "wall_s": round(plain.wall_s, 3), "flatness": plain.flatness[-1]}
+            if plain.converged:
+                # seed error against the weights the plain run converged to
+                diff = seedW - plain.lnW
+                rec["seed_error"] = {"range": round(float(np.ptp(diff)), 3),
+                                     "slope_rms": round(float(np.sqrt(np.mean(np.diff(diff) ** 2))), 4)}
+        records.append(rec)
+        if log:
+            log(rec)
+        if seeded.converged:
+            # a longer run at the converged weights for the ln Omega estimate
+            fin = iterate_to_flat([desc], sweeps, 1, lnW0=[seeded.lnW], relax_iters=0,
+                                  final_sweeps=4 * sweeps, goal=2.0)[0]
+            Xk, tk = training_set([RunResult(desc, 0, [], True, 0.0, seeded.lnW, fin.H)])
+            X = np.concatenate([X, Xk])
+            t = np.concatenate([t, tk])
+            params = net.params()
+            net.close()
+            net = m.Mlp(params)
+            done = 0
+            while done < train_steps:
+                step = min(500, train_steps - done)
+                net.train(X, t, steps=step, lr=5e-4)
+                done += step
+    return net, records
+
+
+def main(argv=None):
+    """Train on small systems, then compare plain and seeded convergence on
+    larger ones; prints one JSON line per target system."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--frac", type=float, default=0.5)
+    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--targets", default="2:48:0.1:4096:50,3:16:0.1:4096:50",
+                    help="comma list of d:L:rho:walkers:sweeps")
+    ap.add_argument("--max-iter", type=int, default=300)
+    ap.add_argument("--relax", type=int, default=30, help="cap on relaxation iterations")
+    ap.add_argument("--relax-tol", type=float, default=0.01)
+    ap.add_argument("--ladder", default="",
+                    help="rungs d:L:rho separated by commas, climbed after training")
+    ap.add_argument("--ladder-walkers", type=int, default=4096)
+    ap.add_argument("--ladder-sweeps", type=int, default=50)
+    args = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    small = small_training_systems(args.frac)
+    res = iterate_to_flat(small, sweeps=100, max_iter=200, final_sweeps=1000)
+    X, t = training_set([r for r in res if r.converged])
+    t_runs = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    net, loss = train(X, t, steps=args.train_steps, lr=1e-3)
+    print(json.dumps({"training_systems": len(small),
+                      "converged": int(sum(r.converged for r in res)), "rows": int(len(t)),
+                      "training_runs_s": round(t_runs, 3),
+                      "network_training_s": round(time.perf_counter() - t1, 3),
+                      "final_loss": loss}))
+    if args.ladder:
+        rungs = []
+        for spec in args.ladder.split(","):
+            d, L, rho = spec.split(":")
+            rungs.append((int(d), int(L), float(rho)))
+        net, _ = ladder(net, rungs, args.frac, args.ladder_walkers, args.ladder_sweeps,
+                        args.max_iter, X, t, log=lambda r: print(json.dumps({"rung": r}), flush=True))
+        net.close()
+        return
+    for spec in args.targets.split(","):
+        d, L, rho, W, sweeps = spec.split(":")
+        d, L, W, sweeps = int(d), int(L), int(W), int(sweeps)
+        N = int(round(float(rho) * L ** d))
+        lo, hi = window_fraction(d, N, args.frac)
+        desc = (d, L, N, W, lo, hi, 10 ** 6)
+        plain, seeded, seedW = compare_plain_and_seeded(net, desc, sweeps, args.max_iter, args.relax,
+                                                        args.relax_tol)
+        print(json.dumps({"system": {"d": d, "L": L, "N": N, "walkers": W, "window": [lo, hi],
+                                     "sweeps_per_iteration": sweeps},
+                          "plain": {"iterations": plain.iterations, "converged": plain.converged,
+                                    "wall_s": round(plain.wall_s, 3),
+                                    "flatness": plain.flatness[-1]},
+                          "seeded": {"iterations": seeded.iterations,
+                                     "converged": seeded.converged,
+                                     "wall_s": round(seeded.wall_s, 3),
+                                     "flatness": seeded.flatness[-1],
+                                     "relax_iterations": int(sum(np.isnan(seeded.flatness)))}}))
+    net.close()
+
+
+if __name__ == "__main__":
+    main()
