@@ -408,21 +408,17 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
         uint32_t k = kn, m = mn, a = an, b = bn;
         const uint32_t r2 = r2n;
         draw(t0 + G);
+        // lanes without an attempt read site 0's neighbourhood so that every
+        // lane can evaluate unconditionally
         NbSet<D, SB> na, nb;
-        if (valid) {
-            na.build(p, ba, a, 0xFFFFFFFFu);
-            nb.build(p, ba, b, a);
-        }
+        na.build(p, ba, valid ? a : 0u, 0xFFFFFFFFu);
+        nb.build(p, ba, valid ? b : 0u, valid ? a : 0xFFFFFFFFu);
         int pos = 0;
         bool done = !active;
         while (__any_sync(FULL, !done)) {
-            bool accept = false;
-            int de = 0;
-            if (!done && valid && j >= pos) {
-                de = na.count() - nb.count();
-                const uint32_t T = thr_load<ST>(thr, row + de);
-                accept = (T == 0xFFFFFFFFu) || (r2 < T);
-            }
+            const int de = na.count() - nb.count();
+            const uint32_t T = thr_load<ST>(thr, row + de);
+            const bool accept = !done && valid && j >= pos && ((T == 0xFFFFFFFFu) || (r2 < T));
             const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
             const int f = bal ? __ffs(bal) - 1 : G;
             const int src = gbase + (f < G ? f : 0);
@@ -430,39 +426,38 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
             uint32_t a_f, b_f, k_f, m_f;
             shfl_pair<IdxT>(a, b, src, a_f, b_f);
             shfl_pair<IdxT>(k, m, src, k_f, m_f);
-            bool fix_a = false, fix_b = false;
-            if (!done) {
-                if (f < G) {
-                    run += (uint32_t)(f - pos);      // rejected at the current energy
-                    if (j == f) {
-                        bits[a_f >> 5] &= ~(1u << (a_f & 31u));
-                        bits[b_f >> 5] |= 1u << (b_f & 31u);
-                        S[k_f] = (IdxT)b_f;
-                        S[N + m_f] = (IdxT)a_f;
-                    }
-                    ++acc;
-                    if (de_f != 0) {
-                        if (j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
-                        bin += de_f;
-                        row += de_f * width;
-                        run = 0;
-                    }
-                    run += 1;
-                    // the commit moved list slots k_f and N + m_f
-                    fix_a = (j > f) && (k == k_f);
-                    fix_b = (j > f) && (m == m_f);
-                    if (kn == k_f) an = b_f;
-                    if (mn == m_f) bn = a_f;
-                    pos = f + 1;
-                    if (pos >= n_valid) done = true;
+            const bool commit = !done && f < G;       // the same in every lane of the group
+            const bool finish = !done && f >= G;
+            if (commit && j == f) {
+                if constexpr (SB) {
+                    atomicAnd(bits + (a_f >> 5), ~(1u << (a_f & 31u)));
+                    atomicOr(bits + (b_f >> 5), 1u << (b_f & 31u));
                 } else {
-                    run += (uint32_t)(n_valid - pos);
-                    done = true;
+                    bits[a_f >> 5] &= ~(1u << (a_f & 31u));
+                    bits[b_f >> 5] |= 1u << (b_f & 31u);
                 }
+                S[k_f] = (IdxT)b_f;
+                S[N + m_f] = (IdxT)a_f;
             }
+            // attempts pos .. f-1 were rejected at the current energy
+            run += commit ? (uint32_t)(f - pos) : (finish ? (uint32_t)(n_valid - pos) : 0u);
+            acc += commit ? 1u : 0u;
+            const bool moved = commit && de_f != 0;
+            if (moved && j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
+            bin += moved ? de_f : 0;
+            row += moved ? de_f * width : 0;
+            run = moved ? 0u : run;
+            run += commit ? 1u : 0u;
+            // the commit moved list slots k_f and N + m_f
+            const bool fix_a = commit && j > f && k == k_f;
+            const bool fix_b = commit && j > f && m == m_f;
+            an = (commit && kn == k_f) ? b_f : an;
+            bn = (commit && mn == m_f) ? a_f : bn;
+            pos = commit ? f + 1 : pos;
+            done = done || finish || (commit && f + 1 >= n_valid);
             if (__any_sync(FULL, fix_a || fix_b)) {
-                if (fix_a) a = b_f;
-                if (fix_b) b = a_f;
+                a = fix_a ? b_f : a;
+                b = fix_b ? a_f : b;
                 if (fix_a || fix_b) {
                     na.build(p, ba, a, 0xFFFFFFFFu);
                     nb.build(p, ba, b, a);
