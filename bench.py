@@ -46,6 +46,26 @@ def alg_ops_per_attempt(d: int) -> int:
     return 100 + 2 + 2 + 2 * 5 * d + 2 * 2 * d * 3 + 6 + 2
 
 
+# DRAM bytes (read + write) of one walker-update launch of a workload's
+# default iteration, from the one-pass ncu capture summarised under profiles/,
+# valid only for the kernel source it was taken with (sha256 prefix of
+# walker_kernels.cu); any change to the kernel makes the figure stale (null).
+TRAFFIC_MEASURED = {
+    "2d-L64-N410-w4096": {"bytes": 36.08e6 + 342.14e6, "kernel_sha": "58f6e9aed9313f3b"},
+}
+
+
+def _measured_traffic(workload: str, sweeps_default: bool):
+    import hashlib
+    rec = TRAFFIC_MEASURED.get(workload)
+    if rec is None or not sweeps_default:
+        return None
+    src = os.path.join(ROOT, "paper_1401_4076_gb300", "csrc", "walker_kernels.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return rec["bytes"] if sha == rec["kernel_sha"] else None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -325,7 +345,8 @@ def main(argv=None):
     peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6  # thread-instr/s
     achieved = ops_launch / (k_ms / 1000.0)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                "unit": "Tops/s", "frac": achieved / peak_ops,
+                "traffic": _measured_traffic(wl.name, sweeps == wl.sweeps),
                 "peak_source": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz"
                                f" ({peak_kind} max clock)",
                 "kernel": "walker_update", "kernel_ms": k_ms,
