@@ -18,17 +18,12 @@ arranges inputs and collects results.
 """
 from __future__ import annotations
 
-import math
 import time
-from dataclasses import dataclass, field
 
 import numpy as np
 
 from . import mucal as m
-
-
-def ln_binomial(V: int, N: int) -> float:
-    return math.lgamma(V + 1) - math.lgamma(N + 1) - math.lgamma(V - N + 1)
+from .iterate import RunResult, iterate_to_flat, ln_binomial, ln_omega_estimate  # noqa: F401
 
 
 def features(d: int, L: int, N: int, E: np.ndarray) -> np.ndarray:
@@ -42,120 +37,6 @@ def features(d: int, L: int, N: int, E: np.ndarray) -> np.ndarray:
     X[:, 2] = 10.0 * rho - 0.5
     X[:, 3] = 2.0 * e / (d * rho) + 1.0
     return X
-
-
-def ln_omega_estimate(lnW: np.ndarray, H: np.ndarray, V: int, N: int) -> np.ndarray:
-    """ln Omega(E) = ln H(E) - lnW(E) on visited bins (W = 1/Omega makes H flat,
-    Sec. 2), shifted so that the visited bins carry all C(V, N) states; NaN
-    where H = 0."""
-    H = np.asarray(H)
-    out = np.full(len(H), np.nan)
-    vis = H > 0
-    out[vis] = np.log(H[vis].astype(np.float64)) - np.asarray(lnW)[vis]
-    mx = out[vis].max()
-    lse = mx + math.log(np.exp(out[vis] - mx).sum())
-    out[vis] += ln_binomial(V, N) - lse
-    return out
-
-
-@dataclass
-class RunResult:
-    desc: tuple
-    iterations: int
-    flatness: list
-    converged: bool
-    wall_s: float
-    lnW: np.ndarray
-    H: np.ndarray
-    attempts: int = 0
-    extra: dict = field(default_factory=dict)
-
-
-def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None, goal=0.5,
-                    scheme=m.MUCAL_SCHEME_RECURSIVE, cuda_stream=None, launch=None,
-                    final_sweeps: int = 0, relax_iters: int = 0, relax_tol: float = 0.0):
-    """Run the weight iteration of Sec. 2 for several systems in one context
-    (one launch per iteration) until each reaches flatness >= goal inside its
-    target window (t_lo, t_hi) or max_iter iterations.  A system that has
-    converged keeps running with frozen weights (its histogram then serves the
-    ln Omega estimate).  Returns one RunResult per system.
-
-    relax_iters: iterations run with the starting weights held fixed before
-    the first update (their histograms are discarded).  Walkers start from
-    random placements, which are equilibrium states of lnW = 0 only; the
-    update of Sec. 2 assumes equilibrium runs, so a start from other weights
-    first lets the walkers relax to them.  These iterations count towards
-    the reported iterations and wall time.  With relax_tol > 0, relax_iters is
-    a cap and the relaxation of a system ends early once the mean energy of
-    its histogram moves by less than relax_tol times the window width from
-    one iteration to the next.
-    """
-    n = len(systems)
-    t0 = time.perf_counter()
-    with m.Mucal(systems, cuda_stream=cuda_stream) as mc:
-        if launch:
-            mc.set_launch(**launch)
-        for i in range(n):
-            if lnW0 is not None and lnW0[i] is not None:
-                mc.set_weights(i, lnW0[i])
-            if targets is not None and targets[i] is not None:
-                mc.set_target_window(i, *targets[i])
-        done = [False] * n
-        iters = [0] * n
-        flat = [[] for _ in range(n)]
-        walls = [0.0] * n
-        attempts = [0] * n
-        Hs = [None] * n
-        relaxing = [relax_iters > 0] * n
-        relaxed = [0] * n
-        last_mean = [None] * n
-        for it in range(max_iter):
-            mc.run_iteration(sweeps, it)
-            for i in range(n):
-                if done[i]:
-                    continue
-                iters[i] = it + 1
-                attempts[i] += sweeps * systems[i][2] * systems[i][3]
-                if relaxing[i]:
-                    flat[i].append(float("nan"))
-                    relaxed[i] += 1
-                    stop = relaxed[i] >= relax_iters
-                    if not stop and relax_tol > 0:
-                        H = mc.histogram(i).astype(np.float64)
-                        mean = float((H * np.arange(len(H))).sum() / max(H.sum(), 1.0))
-                        if last_mean[i] is not None and abs(mean - last_mean[i]) < relax_tol * len(H):
-                            stop = True
-                        last_mean[i] = mean
-                    if stop:
-                        relaxing[i] = False
-                    continue
-                H = mc.histogram(i)
-                lnW, f = mc.update_weights(i, scheme)
-                flat[i].append(f)
-                Hs[i] = H
-                if f >= goal:
-                    done[i] = True
-                    walls[i] = time.perf_counter() - t0
-            if all(done):
-                break
-        for i in range(n):
-            if not done[i]:
-                walls[i] = time.perf_counter() - t0
-        results = []
-        final_H = [None] * n
-        lnWs = [mc.weights(i) for i in range(n)]
-        if final_sweeps:
-            # one more iteration with the final weights for the ln Omega estimate
-            for i in range(n):
-                mc.set_weights(i, lnWs[i])
-            mc.run_iteration(final_sweeps, max_iter + 1)
-            for i in range(n):
-                final_H[i] = mc.histogram(i)
-        for i in range(n):
-            results.append(RunResult(tuple(systems[i]), iters[i], flat[i], done[i], walls[i],
-                                     lnWs[i], final_H[i] if final_sweeps else Hs[i],
-                                     attempts[i]))
-    return results
 
 
 def training_set(results):
