@@ -210,6 +210,28 @@ int mucal_histogram_device_ptr(void *ctx, int32_t sys, void **dptr);
 /* Library version string. */
 const char *mucal_version(void);
 
+/* ---- checkpoint / resume ---------------------------------------------------
+ * A checkpoint of system sys holds every walker's state (bitset, particle and
+ * empty-site lists, energy), the weights and the recursion memory (visited
+ * set, accumulated pair weights) and the flatness target.  The random
+ * numbers depend only on (seed, iteration, attempt), so a system restored
+ * into a context with the same descriptor continues bit-for-bit when the
+ * caller passes the same iteration numbers.  Layout (host byte order): a
+ * header (magic "MUCALCK1", d, L, N, n_walkers, e_lo, e_hi, seed_base, list
+ * entry bytes, bitset words, n_bins, target), then bits, lists, energies,
+ * lnW (float64), visited (uint8), accumulated weights (float64).
+ * mucal_checkpoint_size: bytes of the checkpoint of sys.
+ * mucal_checkpoint_save: write it into the caller's host buffer of exactly
+ *   that size (waits for the context's stream).
+ * mucal_checkpoint_load: restore from such a buffer; it must come from a
+ *   system with the same descriptor.  Energies outside the window, list
+ *   entries off the lattice and non-finite weights are rejected with
+ *   MUCAL_ERR_INVALID_ARG before anything is changed.  The thresholds are
+ *   rebuilt from the restored weights. */
+int mucal_checkpoint_size(void *ctx, int32_t sys, int64_t *bytes);
+int mucal_checkpoint_save(void *ctx, int32_t sys, void *buf, int64_t bytes);
+int mucal_checkpoint_load(void *ctx, int32_t sys, const void *buf, int64_t bytes);
+
 /* ---- allocation-free walker update (no counterpart in the paper) ---------
  * For callers that cannot allocate device memory: code running where
  * cudaMalloc is not allowed or not wanted, such as inside a memory pool that

@@ -760,3 +760,137 @@ int mucal_histogram_device_ptr(void *ctx, int32_t sys, void **dptr)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume.  Random numbers are counter-based (seed, iteration,
+// attempt), so a restored system continues bit-for-bit.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CheckpointHeader {
+    char magic[8];          // "MUCALCK1"
+    int32_t d, L, N, n_walkers, e_lo, e_hi;
+    uint64_t seed_base;
+    int32_t index_bytes, words, n_bins, target_default;
+    int32_t t_lo, t_hi;
+};
+
+size_t checkpoint_bytes(const System &s)
+{
+    const SysParams &p = s.p;
+    const size_t nw = (size_t)p.n_walkers;
+    return sizeof(CheckpointHeader) + nw * p.words * 4 + nw * (size_t)p.V * (p.idx16 ? 2 : 4) +
+           nw * 4 + (size_t)p.n_bins * (8 + 1 + 8);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mucal_checkpoint_size(void *ctx, int32_t sys, int64_t *bytes)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    if (!bytes) return fail(c, MUCAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = (int64_t)checkpoint_bytes(c->sys[sys]);
+    return MUCAL_OK;
+}
+
+int mucal_checkpoint_save(void *ctx, int32_t sys, void *buf, int64_t bytes)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    const System &s = c->sys[sys];
+    const SysParams &p = s.p;
+    if (!buf || bytes != (int64_t)checkpoint_bytes(s))
+        return fail(c, MUCAL_ERR_INVALID_ARG, "checkpoint buffer must hold %zu bytes", checkpoint_bytes(s));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    char *o = static_cast<char *>(buf);
+    CheckpointHeader h{};
+    std::memcpy(h.magic, "MUCALCK1", 8);
+    h.d = p.d; h.L = p.L; h.N = p.N; h.n_walkers = p.n_walkers;
+    h.e_lo = s.desc.e_lo; h.e_hi = s.desc.e_hi; h.seed_base = p.seed_base;
+    h.index_bytes = p.idx16 ? 2 : 4; h.words = p.words; h.n_bins = p.n_bins;
+    h.target_default = s.target_default ? 1 : 0; h.t_lo = s.t_lo; h.t_hi = s.t_hi;
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const size_t nw = (size_t)p.n_walkers;
+    const size_t b_bits = nw * p.words * 4, b_S = nw * (size_t)p.V * (p.idx16 ? 2 : 4), b_E = nw * 4;
+    CUDA_TRY(c, cudaMemcpyAsync(o, p.bits, b_bits, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(o + b_bits, p.S, b_S, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(o + b_bits + b_S, p.E, b_E, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    o += b_bits + b_S + b_E;
+    std::memcpy(o, s.lnW.data(), (size_t)p.n_bins * 8);
+    o += (size_t)p.n_bins * 8;
+    std::memcpy(o, s.visited.data(), (size_t)p.n_bins);
+    o += p.n_bins;
+    std::memcpy(o, s.pacc.data(), (size_t)p.n_bins * 8);
+    return MUCAL_OK;
+}
+
+int mucal_checkpoint_load(void *ctx, int32_t sys, const void *buf, int64_t bytes)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    System &s = c->sys[sys];
+    const SysParams &p = s.p;
+    if (!buf || bytes != (int64_t)checkpoint_bytes(s))
+        return fail(c, MUCAL_ERR_INVALID_ARG, "checkpoint must hold %zu bytes", checkpoint_bytes(s));
+    const char *in = static_cast<const char *>(buf);
+    CheckpointHeader h;
+    std::memcpy(&h, in, sizeof h);
+    if (std::memcmp(h.magic, "MUCALCK1", 8) != 0 || h.d != p.d || h.L != p.L || h.N != p.N ||
+        h.n_walkers != p.n_walkers || h.e_lo != s.desc.e_lo || h.e_hi != s.desc.e_hi ||
+        h.seed_base != p.seed_base || h.index_bytes != (p.idx16 ? 2 : 4) || h.words != p.words ||
+        h.n_bins != p.n_bins)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "checkpoint does not belong to system %d", sys);
+    const size_t nw = (size_t)p.n_walkers;
+    const size_t b_bits = nw * p.words * 4, b_S = nw * (size_t)p.V * (p.idx16 ? 2 : 4), b_E = nw * 4;
+    const char *bits = in + sizeof h;
+    const char *S = bits + b_bits;
+    const char *E = S + b_S;
+    const char *w = E + b_E;
+    // validate before touching the device: energies inside the window, list
+    // entries on the lattice, finite weights
+    for (size_t i = 0; i < nw; ++i) {
+        int32_t e;
+        std::memcpy(&e, E + 4 * i, 4);
+        if (e < s.desc.e_lo || e > s.desc.e_hi)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "checkpoint energy of walker %zu outside the window", i);
+    }
+    for (size_t i = 0; i < nw * (size_t)p.V; ++i) {
+        uint32_t v;
+        if (p.idx16) {
+            uint16_t x;
+            std::memcpy(&x, S + 2 * i, 2);
+            v = x;
+        } else {
+            std::memcpy(&v, S + 4 * i, 4);
+        }
+        if (v >= (uint32_t)p.V) return fail(c, MUCAL_ERR_INVALID_ARG, "checkpoint list entry %zu is not a site", i);
+    }
+    std::vector<double> lnW((size_t)p.n_bins);
+    std::memcpy(lnW.data(), w, (size_t)p.n_bins * 8);
+    for (double x : lnW)
+        if (!std::isfinite(x)) return fail(c, MUCAL_ERR_INVALID_ARG, "checkpoint weight is not finite");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(p.bits, bits, b_bits, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(p.S, S, b_S, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(p.E, E, b_E, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    s.lnW = lnW;
+    std::memcpy(s.visited.data(), w + (size_t)p.n_bins * 8, (size_t)p.n_bins);
+    std::memcpy(s.pacc.data(), w + (size_t)p.n_bins * 9, (size_t)p.n_bins * 8);
+    s.target_default = h.target_default != 0;
+    s.t_lo = h.t_lo;
+    s.t_hi = h.t_hi;
+    s.hist_on_host = false;
+    return upload_thresholds(c, s);
+}
+
+}  // extern "C"

@@ -41,6 +41,7 @@ EXPORTED = [
     "mucal_mlp_param_count", "mucal_mlp_create", "mucal_mlp_destroy", "mucal_mlp_last_error",
     "mucal_mlp_get_params", "mucal_mlp_forward", "mucal_mlp_gradients", "mucal_mlp_train",
     "mucal_run_walkers_noalloc", "mucal_run_walkers_noalloc_error",
+    "mucal_checkpoint_size", "mucal_checkpoint_save", "mucal_checkpoint_load",
 ]
 
 
@@ -111,6 +112,9 @@ def load_library(path: str = LIB_PATH):
         "mucal_run_walkers_noalloc": (ctypes.c_int, [ctypes.POINTER(mucal_system_desc), I64, U32,
                                                      P, P, P, P, P, P]),
         "mucal_run_walkers_noalloc_error": (ctypes.c_char_p, []),
+        "mucal_checkpoint_size": (ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
+        "mucal_checkpoint_save": (ctypes.c_int, [P, I32, P, I64]),
+        "mucal_checkpoint_load": (ctypes.c_int, [P, I32, P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -248,6 +252,21 @@ def mucal_version():
     return load_library().mucal_version().decode()
 
 
+def mucal_checkpoint_save(ctx, sys):
+    """Checkpoint of system sys as a bytes-like numpy uint8 array."""
+    lib = load_library()
+    n = ctypes.c_int64()
+    _check(lib.mucal_checkpoint_size(ctx, sys, ctypes.byref(n)), ctx)
+    buf = np.zeros(n.value, dtype=np.uint8)
+    _check(lib.mucal_checkpoint_save(ctx, sys, _ptr(buf), buf.size), ctx)
+    return buf
+
+
+def mucal_checkpoint_load(ctx, sys, buf):
+    b = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load_library().mucal_checkpoint_load(ctx, sys, _ptr(b), b.size), ctx)
+
+
 def mucal_run_walkers_noalloc(desc, sweeps, iteration, bits_ptr, S_ptr, E_ptr, thr_ptr, H_ptr,
                               cuda_stream=None):
     """Allocation-free walker update on caller-owned device buffers (raw
@@ -339,6 +358,12 @@ class Mucal:
 
     def stats(self, sys=0):
         return mucal_get_stats(self.ctx, sys)
+
+    def checkpoint(self, sys=0):
+        return mucal_checkpoint_save(self.ctx, sys)
+
+    def restore(self, sys, buf):
+        mucal_checkpoint_load(self.ctx, sys, buf)
 
 
 # --------------------------------------------------------------------------
