@@ -79,7 +79,8 @@ extern "C" {
 #define MUCAL_SCHEME_RECURSIVE  1
 
 /* ---- walker-update kernels (mucal_launch_config.kernel) ------------------ */
-/* One thread advances one walker, attempt after attempt. */
+/* One thread advances one walker, attempt after attempt; the random numbers
+ * and list reads of the next attempts are in flight while one is evaluated. */
 #define MUCAL_KERNEL_THREAD     0
 /* A group of lanes advances one walker: the lanes evaluate consecutive
  * attempts against the same state in parallel and commit them in order,
@@ -100,8 +101,8 @@ typedef struct mucal_system_desc {
 typedef struct mucal_launch_config {
     int32_t kernel;            /* MUCAL_KERNEL_THREAD or MUCAL_KERNEL_GROUP */
     int32_t lanes_per_walker;  /* 1 for THREAD; 2, 4, 8, 16 or 32 for GROUP */
-    int32_t walkers_per_block; /* threads per block = walkers_per_block * lanes: <= 1024 for
-                                  THREAD, a multiple of 32 and <= 512 for GROUP */
+    int32_t walkers_per_block; /* threads per block = walkers_per_block * lanes: <= 512;
+                                  a multiple of 32 for GROUP */
     int32_t bits_in_smem;      /* 1: stage each walker's occupation bitset in shared
                                   memory for the launch; 0: use it in global memory */
 } mucal_launch_config;

@@ -21,7 +21,7 @@ def candidates(max_threads: int = 1024):
     that a one-wave launch can match walkers to SMs when shared memory limits
     the blocks per SM."""
     out = []
-    for wpb in (4, 8, 16, 32):
+    for wpb in (2, 4, 6, 8, 12, 16, 27, 32, 64):
         for smem in (1, 0):
             out.append(dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1,
                             walkers_per_block=wpb, bits_in_smem=smem))

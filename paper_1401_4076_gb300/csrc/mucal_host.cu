@@ -309,6 +309,8 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     if (sh.kernel == MUCAL_KERNEL_THREAD) {
         if (sh.lanes != 1)
             return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
+        if (sh.walkers_per_block > 512)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel blocks hold at most 512 threads");
     } else if (sh.kernel == MUCAL_KERNEL_GROUP) {
         if (sh.lanes != 2 && sh.lanes != 4 && sh.lanes != 8 && sh.lanes != 16 && sh.lanes != 32)
             return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel needs lanes_per_walker in {2,4,8,16,32}");

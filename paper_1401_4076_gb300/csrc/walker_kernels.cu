@@ -79,25 +79,6 @@ __device__ __forceinline__ uint32_t occupied(const uint32_t *bits, uint32_t s)
     return (bits[s >> 5] >> (s & 31u)) & 1u;
 }
 
-// Energy change of moving the particle at a to the empty site b: occupied
-// neighbours of a are lost bonds, occupied neighbours of b other than a are
-// gained bonds; E = -#bonds, so dE = n_a - n_b.
-template <int D>
-__device__ __forceinline__ int jump_delta_e(const SysParams &p, const uint32_t *bits, uint32_t a,
-                                            uint32_t b)
-{
-    uint32_t na[2 * D], nbb[2 * D];
-    neighbours<D>(p, a, na);
-    neighbours<D>(p, b, nbb);
-    int n_a = 0, n_b = 0;
-#pragma unroll
-    for (int i = 0; i < 2 * D; ++i) {
-        n_a += (int)occupied(bits, na[i]);
-        n_b += (int)(occupied(bits, nbb[i]) & (nbb[i] != a ? 1u : 0u));
-    }
-    return n_a - n_b;
-}
-
 template <typename IdxT>
 __device__ __forceinline__ IdxT *walker_S(const SysParams &p, int w)
 {
@@ -117,74 +98,6 @@ __device__ __forceinline__ unsigned long long *hist_row(const SysParams &p, int 
 {
     const int row = block_row >= 0 ? block_row : w;
     return p.hist + (size_t)row * (size_t)p.n_bins;
-}
-
-// ---------------------------------------------------------------------------
-// One thread, one walker: A attempts in order.  The histogram is kept as a
-// run length (current bin, count) and added to the histogram row only when
-// the energy changes, which records exactly one entry per attempt.  Attempt
-// t+1's random numbers and list reads are issued during attempt t; a commit
-// that moves the same list slot patches the early read.
-// ---------------------------------------------------------------------------
-template <int D, typename IdxT>
-__device__ void chain_thread(const SysParams &p, int w, uint32_t *bits, const uint32_t *thr,
-                             unsigned long long *hist, uint64_t A, uint32_t iter)
-{
-    IdxT *S = walker_S<IdxT>(p, w);
-    const uint32_t N = (uint32_t)p.N;
-    const uint32_t holes = (uint32_t)(p.V - p.N);
-    const uint64_t seed = p.seed_base + (uint64_t)w;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const int width = p.width;
-    int bin = p.E[w] - p.e_lo;
-    int row = bin * width + 2 * D;
-    uint32_t run = 0;
-    uint32_t acc = 0;
-    uint4 r = philox10(make_uint4(0u, 0u, iter, 0u), k0, k1);
-    uint32_t k = __umulhi(r.x, N), m = __umulhi(r.y, holes);
-    uint32_t a = S[k], b = S[N + m];
-    for (uint64_t t = 0; t < A; ++t) {
-        const uint64_t tn = t + 1;
-        uint32_t kn = 0, mn = 0, an = 0, bn = 0;
-        uint4 rn = make_uint4(0, 0, 0, 0);
-        if (tn < A) {
-            rn = philox10(make_uint4((uint32_t)tn, (uint32_t)(tn >> 32), iter, 0u), k0, k1);
-            kn = __umulhi(rn.x, N);
-            mn = __umulhi(rn.y, holes);
-            an = S[kn];
-            bn = S[N + mn];
-        }
-        const int de = jump_delta_e<D>(p, bits, a, b);
-        const uint32_t T = thr[row + de];
-        if (T == 0xFFFFFFFFu || r.z < T) {
-            bits[a >> 5] &= ~(1u << (a & 31u));
-            bits[b >> 5] |= (1u << (b & 31u));
-            S[k] = (IdxT)b;
-            S[N + m] = (IdxT)a;
-            if (kn == k) an = b;
-            if (mn == m) bn = a;
-            ++acc;
-            if (de != 0) {
-                if (run) atomicAdd(hist + bin, (unsigned long long)run);
-                bin += de;
-                row += de * width;
-                run = 0;
-            }
-        }
-        ++run;
-        if (run == 0x80000000u) {
-            atomicAdd(hist + bin, (unsigned long long)run);
-            run = 0;
-        }
-        r = rn;
-        k = kn;
-        m = mn;
-        a = an;
-        b = bn;
-    }
-    if (run) atomicAdd(hist + bin, (unsigned long long)run);
-    p.E[w] = bin + p.e_lo;
-    p.accepts[w] = acc;
 }
 
 // Copy n words between global and shared memory, all threads cooperating.
@@ -234,31 +147,6 @@ __device__ __forceinline__ void block_finish(const BlockSetup &b, int bits_in_sm
         __syncthreads();
         block_copy_words(b.gbits, b.bits0, b.block_words);
     }
-}
-
-__global__ void __launch_bounds__(1024)
-walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
-                     uint64_t sweeps, uint32_t iter, int bits_in_smem, int thr_in_smem)
-{
-    extern __shared__ __align__(16) uint32_t smem[];
-    const BlockWork wk = work[blockIdx.x];
-    const SysParams &p = sys[wk.sys];
-    const BlockSetup bs = block_setup(p, wk, smem, bits_in_smem, thr_in_smem);
-    const int lw = threadIdx.x;
-    if (lw < wk.count) {
-        const int w = wk.walker0 + lw;
-        uint32_t *bits = bs.bits0 + (size_t)lw * p.words;
-        unsigned long long *hist = hist_row(p, w, wk.hist_row);
-        const uint64_t A = sweeps * (uint64_t)p.N;
-        if (p.d == 2) {
-            if (p.idx16) chain_thread<2, uint16_t>(p, w, bits, bs.thr, hist, A, iter);
-            else chain_thread<2, uint32_t>(p, w, bits, bs.thr, hist, A, iter);
-        } else {
-            if (p.idx16) chain_thread<3, uint16_t>(p, w, bits, bs.thr, hist, A, iter);
-            else chain_thread<3, uint32_t>(p, w, bits, bs.thr, hist, A, iter);
-        }
-    }
-    block_finish(bs, bits_in_smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -477,6 +365,144 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
     }
 }
 
+// ---------------------------------------------------------------------------
+// One thread, one walker: A attempts in order, software-pipelined.  The
+// random numbers and list reads of the next PF attempts are in flight in a
+// register ring while the current attempt is evaluated; a commit patches the
+// in-flight list reads it invalidates (same list slot).  The histogram is
+// kept as a run length (current bin, count) and added to the histogram row
+// only when the energy changes, which records exactly one entry per attempt.
+// ---------------------------------------------------------------------------
+constexpr int kThreadPipe = 4;
+
+template <int D, typename IdxT, bool SB, bool ST>
+__device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t *bits,
+                                             const uint32_t *thr, unsigned long long *hist,
+                                             uint64_t A, uint32_t iter)
+{
+    constexpr int PF = kThreadPipe;
+    IdxT *S = walker_S<IdxT>(p, w);
+    const BitAddr<SB> ba(bits);
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t holes = (uint32_t)(p.V - p.N);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int width = p.width;
+    int bin = p.E[w] - p.e_lo;
+    int row = bin * width + 2 * D;
+    uint32_t run = 0;
+    uint32_t acc = 0;
+    // ra/rb receive the in-flight list reads; a commit that moves a slot an
+    // in-flight read covers records the new value in fa/fb instead of
+    // touching ra/rb, so that it never waits for the read to land
+    constexpr uint32_t NONE = 0xFFFFFFFFu;
+    uint32_t rk[PF], rm[PF], rr[PF], ra[PF], rb[PF], fa[PF], fb[PF];
+#pragma unroll
+    for (int s = 0; s < PF; ++s) {
+        rk[s] = NONE;
+        rm[s] = NONE;
+        fa[s] = NONE;
+        fb[s] = NONE;
+        rr[s] = ra[s] = rb[s] = 0u;
+        const uint64_t t = (uint64_t)s;
+        if (t < A) {
+            const uint4 r = philox10(make_uint4((uint32_t)t, 0u, iter, 0u), k0, k1);
+            rk[s] = __umulhi(r.x, N);
+            rm[s] = __umulhi(r.y, holes);
+            rr[s] = r.z;
+            ra[s] = S[rk[s]];
+            rb[s] = S[N + rm[s]];
+        }
+    }
+    for (uint64_t t0 = 0; t0 < A; t0 += PF) {
+#pragma unroll
+        for (int s = 0; s < PF; ++s) {
+            const uint64_t t = t0 + (uint64_t)s;
+            if (t < A) {
+                const uint32_t a = fa[s] != NONE ? fa[s] : ra[s];
+                const uint32_t b = fb[s] != NONE ? fb[s] : rb[s];
+                const uint32_t k = rk[s], m = rm[s];
+                NbSet<D, SB> na, nb;
+                na.build(p, ba, a, 0xFFFFFFFFu);
+                nb.build(p, ba, b, a);
+                const int de = na.count() - nb.count();
+                const uint32_t T = thr_load<ST>(thr, row + de);
+                if (T == 0xFFFFFFFFu || rr[s] < T) {
+                    bits[a >> 5] &= ~(1u << (a & 31u));
+                    bits[b >> 5] |= 1u << (b & 31u);
+                    S[k] = (IdxT)b;
+                    S[N + m] = (IdxT)a;
+#pragma unroll
+                    for (int q = 0; q < PF; ++q) {
+                        if (q == s) continue;
+                        fa[q] = (rk[q] == k) ? b : fa[q];
+                        fb[q] = (rm[q] == m) ? a : fb[q];
+                    }
+                    ++acc;
+                    if (de != 0) {
+                        if (run) atomicAdd(hist + bin, (unsigned long long)run);
+                        bin += de;
+                        row += de * width;
+                        run = 0;
+                    }
+                }
+                ++run;
+                if (run == 0x80000000u) {
+                    atomicAdd(hist + bin, (unsigned long long)run);
+                    run = 0;
+                }
+                // refill this slot with attempt t + PF
+                const uint64_t tn = t + PF;
+                rk[s] = NONE;
+                rm[s] = NONE;
+                fa[s] = NONE;
+                fb[s] = NONE;
+                if (tn < A) {
+                    const uint4 r = philox10(make_uint4((uint32_t)tn, (uint32_t)(tn >> 32), iter, 0u),
+                                             k0, k1);
+                    rk[s] = __umulhi(r.x, N);
+                    rm[s] = __umulhi(r.y, holes);
+                    rr[s] = r.z;
+                    ra[s] = S[rk[s]];
+                    rb[s] = S[N + rm[s]];
+                }
+            }
+        }
+    }
+    if (run) atomicAdd(hist + bin, (unsigned long long)run);
+    p.E[w] = bin + p.e_lo;
+    p.accepts[w] = acc;
+}
+
+template <bool SB, bool ST>
+__global__ void __launch_bounds__(kGroupMaxThreads, 1)
+walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
+                     uint64_t sweeps, uint32_t iter)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const BlockWork wk = work[blockIdx.x];
+    const SysParams &p = sys[wk.sys];
+    const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+    const int lw = threadIdx.x;
+    if (lw < wk.count) {
+        const int w = wk.walker0 + lw;
+        const uint32_t *thr = ST ? smem : p.thr;
+        uint32_t *bits0 = SB ? smem + (ST ? thr_words_aligned(p) : 0)
+                             : p.bits + (size_t)wk.walker0 * (size_t)p.words;
+        uint32_t *bits = bits0 + (size_t)lw * p.words;
+        unsigned long long *hist = hist_row(p, w, wk.hist_row);
+        const uint64_t A = sweeps * (uint64_t)p.N;
+        if (p.d == 2) {
+            if (p.idx16) chain_thread<2, uint16_t, SB, ST>(p, w, bits, thr, hist, A, iter);
+            else chain_thread<2, uint32_t, SB, ST>(p, w, bits, thr, hist, A, iter);
+        } else {
+            if (p.idx16) chain_thread<3, uint16_t, SB, ST>(p, w, bits, thr, hist, A, iter);
+            else chain_thread<3, uint32_t, SB, ST>(p, w, bits, thr, hist, A, iter);
+        }
+    }
+    block_finish(bs, SB ? 1 : 0);
+}
+
 template <int G, bool SB, bool ST>
 __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
                                            uint64_t sweeps, uint32_t iter)
@@ -641,7 +667,10 @@ cudaError_t walker_update_max_smem(int *bytes)
         (const void *)walker_update_group<G, true, false>,                              \
         (const void *)walker_update_group<G, false, true>,                              \
         (const void *)walker_update_group<G, false, false>
-    const void *fns[] = {(const void *)walker_update_thread, MUCAL_GROUP_FNS(2), MUCAL_GROUP_FNS(4),
+    const void *fns[] = {(const void *)walker_update_thread<true, true>,
+                         (const void *)walker_update_thread<true, false>,
+                         (const void *)walker_update_thread<false, true>,
+                         (const void *)walker_update_thread<false, false>, MUCAL_GROUP_FNS(2), MUCAL_GROUP_FNS(4),
                          MUCAL_GROUP_FNS(8), MUCAL_GROUP_FNS(16), MUCAL_GROUP_FNS(32)};
 #undef MUCAL_GROUP_FNS
     for (const void *fn : fns) {
@@ -696,8 +725,14 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
     if (n_blocks <= 0) return cudaSuccess;
     const int threads = shape.walkers_per_block * shape.lanes;
     if (shape.kernel == 0) {
-        walker_update_thread<<<n_blocks, threads, shape.smem_bytes, stream>>>(
-            dev_sys, dev_work, sweeps, iteration, shape.bits_in_smem, shape.thr_in_smem);
+        if (shape.bits_in_smem && shape.thr_in_smem)
+            walker_update_thread<true, true><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
+        else if (shape.bits_in_smem)
+            walker_update_thread<true, false><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
+        else if (shape.thr_in_smem)
+            walker_update_thread<false, true><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
+        else
+            walker_update_thread<false, false><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
         return cudaGetLastError();
     }
     return launch_group_dispatch(shape, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);

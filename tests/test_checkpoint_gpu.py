@@ -72,3 +72,15 @@ def test_corrupted_checkpoints_are_rejected():
         a.restore(0, ck)
         a.run_iteration(10, 0)
         assert a.histogram(0).sum() == H_before.sum()
+
+
+def test_allocation_failure_is_reported_cleanly():
+    """A system far larger than the device: the allocation fails inside the
+    library, which returns MUCAL_ERR_OOM and frees what it had taken."""
+    huge = (2, 4096, 100, 1 << 20, 0, 0, 0)      # lists alone would need ~35 TB
+    with pytest.raises(m.MucalError) as ei:
+        m.Mucal([huge])
+    assert ei.value.code == m.MUCAL_ERR_OOM
+    with m.Mucal([(2, 8, 10, 4, 0, 0, 1)]) as ok:    # the device is still usable
+        ok.run_iteration(5, 0)
+        assert ok.histogram(0).sum() == 4 * 5 * 10
