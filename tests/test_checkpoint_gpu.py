@@ -77,7 +77,7 @@ def test_corrupted_checkpoints_are_rejected():
 def test_allocation_failure_is_reported_cleanly():
     """A system far larger than the device: the allocation fails inside the
     library, which returns MUCAL_ERR_OOM and frees what it had taken."""
-    huge = (2, 4096, 100, 1 << 20, 0, 0, 0)      # lists alone would need ~35 TB
+    huge = (2, 1024, 100, 1 << 22, 0, 0, 0)      # bitsets alone would need 512 GiB
     with pytest.raises(m.MucalError) as ei:
         m.Mucal([huge])
     assert ei.value.code == m.MUCAL_ERR_OOM
