@@ -213,15 +213,25 @@ struct NbSet {
         }
     }
 
-    __device__ __forceinline__ int count() const
+    __device__ __forceinline__ void load(uint32_t (&w)[2 * D]) const
     {
-        uint32_t w[2 * D];
 #pragma unroll
         for (int i = 0; i < 2 * D; ++i) w[i] = BitAddr<SHARED>::load(addr[i]);
+    }
+
+    __device__ __forceinline__ int count_from(const uint32_t (&w)[2 * D]) const
+    {
         int n = 0;
 #pragma unroll
         for (int i = 0; i < 2 * D; ++i) n += (int)(__funnelshift_rc(w[i], 0u, shift[i]) & 1u);
         return n;
+    }
+
+    __device__ __forceinline__ int count() const
+    {
+        uint32_t w[2 * D];
+        load(w);
+        return count_from(w);
     }
 };
 
@@ -301,10 +311,20 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
         NbSet<D, SB> na, nb;
         na.build(p, ba, valid ? a : 0u, 0xFFFFFFFFu);
         nb.build(p, ba, valid ? b : 0u, valid ? a : 0xFFFFFFFFu);
+        // where this lane's own move would write if it commits
+        IdxT *pk = S + k;
+        IdxT *pm = S + N + m;
+        uint32_t *wa_own = bits + (a >> 5), *wb_own = bits + (b >> 5);
+        uint32_t ma_own = 1u << (a & 31u), mb_own = 1u << (b & 31u);
+        // occupation words of the first round; later rounds load theirs right
+        // after the previous commit, ahead of the bookkeeping
+        uint32_t wa[2 * D], wb[2 * D];
+        na.load(wa);
+        nb.load(wb);
         int pos = 0;
         bool done = !active;
         while (__any_sync(FULL, !done)) {
-            const int de = na.count() - nb.count();
+            const int de = na.count_from(wa) - nb.count_from(wb);
             const uint32_t T = thr_load<ST>(thr, row + de);
             const bool accept = !done && valid && j >= pos && ((T == 0xFFFFFFFFu) || (r2 < T));
             const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
@@ -318,15 +338,34 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
             const bool finish = !done && f >= G;
             if (commit && j == f) {
                 if constexpr (SB) {
-                    atomicAnd(bits + (a_f >> 5), ~(1u << (a_f & 31u)));
-                    atomicOr(bits + (b_f >> 5), 1u << (b_f & 31u));
+                    atomicAnd(wa_own, ~ma_own);
+                    atomicOr(wb_own, mb_own);
                 } else {
-                    bits[a_f >> 5] &= ~(1u << (a_f & 31u));
-                    bits[b_f >> 5] |= 1u << (b_f & 31u);
+                    *wa_own &= ~ma_own;
+                    *wb_own |= mb_own;
                 }
-                S[k_f] = (IdxT)b_f;
-                S[N + m_f] = (IdxT)a_f;
+                *pk = (IdxT)b;
+                *pm = (IdxT)a;
             }
+            __syncwarp(FULL);
+            // the commit moved list slots k_f and N + m_f
+            const bool later = commit && j > f;
+            const bool fix_a = later && k == k_f;
+            const bool fix_b = later && m == m_f;
+            if (__any_sync(FULL, fix_a || fix_b)) {
+                a = fix_a ? b_f : a;
+                b = fix_b ? a_f : b;
+                if (fix_a || fix_b) {
+                    na.build(p, ba, a, 0xFFFFFFFFu);
+                    nb.build(p, ba, b, a);
+                    wa_own = bits + (a >> 5);
+                    wb_own = bits + (b >> 5);
+                    ma_own = 1u << (a & 31u);
+                    mb_own = 1u << (b & 31u);
+                }
+            }
+            na.load(wa);
+            nb.load(wb);
             // attempts pos .. f-1 were rejected at the current energy
             run += commit ? (uint32_t)(f - pos) : (finish ? (uint32_t)(n_valid - pos) : 0u);
             acc += commit ? 1u : 0u;
@@ -336,22 +375,10 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
             row += moved ? de_f * width : 0;
             run = moved ? 0u : run;
             run += commit ? 1u : 0u;
-            // the commit moved list slots k_f and N + m_f
-            const bool fix_a = commit && j > f && k == k_f;
-            const bool fix_b = commit && j > f && m == m_f;
             an = (commit && kn == k_f) ? b_f : an;
             bn = (commit && mn == m_f) ? a_f : bn;
             pos = commit ? f + 1 : pos;
             done = done || finish || (commit && f + 1 >= n_valid);
-            if (__any_sync(FULL, fix_a || fix_b)) {
-                a = fix_a ? b_f : a;
-                b = fix_b ? a_f : b;
-                if (fix_a || fix_b) {
-                    na.build(p, ba, a, 0xFFFFFFFFu);
-                    nb.build(p, ba, b, a);
-                }
-            }
-            __syncwarp(FULL);
         }
         if (run >= 0x40000000u) {
             if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)run);
