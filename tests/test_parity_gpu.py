@@ -303,3 +303,33 @@ def test_full_size_production_sampled_states(wl, sweeps, pick, launch):
         assert (H >= hist.sum(axis=0)).all()
         for i, w in enumerate(pick):
             _assert_walker_equal(mc, 0, w, S[i], occ[i], E[i])
+
+
+def test_batched_uneven_systems_full_size_sampled():
+    """The 27-system batch (2D L 32..128, 3D L 16..40, rho 0.02..0.1, 16384
+    walkers) in one launch, in the launch shape the benchmark picks for it:
+    per system sum H counts every attempt and sampled walkers of every system
+    end in the oracle's state."""
+    wl = workloads.batched_uneven()
+    sweeps = 5
+    launch = dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16, walkers_per_block=8,
+                  bits_in_smem=1)
+    with m.Mucal(wl.systems) as mc:
+        mc.set_launch(**launch)
+        lnWs = []
+        for i, (d, L, N, W, lo, hi, seed) in enumerate(wl.systems):
+            lnW = workloads.random_log_weights(d * N + 1, 100 + i, scale=0.05)
+            mc.set_weights(i, lnW)
+            lnWs.append(lnW)
+        mc.run_iteration(sweeps, 9)
+        for i, (d, L, N, W, lo, hi, seed) in enumerate(wl.systems):
+            H = mc.histogram(i)
+            assert H.sum() == W * sweeps * N
+            pick = sorted({0, W // 2, W - 1})
+            S, occ, E = _oracle_states(d, L, N, W, seed, pick)
+            T = chain.thresholds(d, -d * N, 0, lnWs[i])
+            hist, _ = chain.run_walkers(d, L, N, seed, 9, sweeps * N, -d * N, 0, T, S, occ, E,
+                                        walkers=pick)
+            assert (H >= hist.sum(axis=0)).all()
+            for q, w in enumerate(pick):
+                _assert_walker_equal(mc, i, w, S[q], occ[q], E[q])
