@@ -4,9 +4,10 @@ The iteration of Sec. 2 starts from some W^0 and improves it with every
 histogram; W = 1/Omega is its fixed point.  This module trains the library's
 GPU network on ln Omega estimates that converged runs of the method itself
 produced on small lattices, and uses it to propose W^0 = 1/Omega_pred for a
-larger lattice.  The proposal only changes where the iteration starts: the
-walkers, the recursion and the flatness judgement are unchanged, and the
-plain start lnW = 0 remains available as fallback and reference.
+larger lattice.  The proposal only changes where the iteration starts (and, after a seed,
+the update uses the memory-free simple scheme of Sec. 2): the walkers and
+the flatness judgement are unchanged, and the plain start lnW = 0 with the
+recursion remains available as fallback and reference.
 
 Network input: (d, L, rho, E/V), encoded as
     x = (2 (d - 2.5), 16 / L, 10 rho - 0.5, 2 (E/V) / (d rho) + 1);
@@ -99,14 +100,22 @@ def small_training_systems(frac: float = 0.5, walkers: int = 512, seed_base: int
 
 
 def compare_plain_and_seeded(net, desc, sweeps: int, max_iter: int, relax_iters: int = 30,
-                             relax_tol: float = 0.01, cuda_stream=None):
-    """Iterations and wall time to flatness from lnW = 0 and from the network's
-    seed, same system, seeds, sweeps and window."""
+                             relax_tol: float = 0.002, seeded_scheme=m.MUCAL_SCHEME_SIMPLE,
+                             cuda_stream=None):
+    """Iterations and wall time to flatness from lnW = 0 with the recursive
+    scheme (the plain method, the reference) and from the network's seed,
+    same system, seeds, sweeps and window.
+
+    The seeded run updates with the simple scheme W/H: its first histograms
+    come from walkers still relaxing towards the seeded weights, and the
+    simple scheme keeps no memory of them, whereas the accumulated-statistics
+    recursion would carry their bias for many iterations (measured: the
+    recursive scheme after a seed is slower than either plain start)."""
     d, L, N, W, lo, hi, seed = desc
     seedW = seed_weights(net, d, L, N, lo, hi)
     plain = iterate_to_flat([desc], sweeps, max_iter, cuda_stream=cuda_stream)[0]
     seeded = iterate_to_flat([desc], sweeps, max_iter, lnW0=[seedW], relax_iters=relax_iters,
-                             relax_tol=relax_tol, cuda_stream=cuda_stream)[0]
+                             relax_tol=relax_tol, scheme=seeded_scheme, cuda_stream=cuda_stream)[0]
     return plain, seeded, seedW
 
 
@@ -128,7 +137,8 @@ def ladder(net, rungs, frac: float, walkers: int, sweeps: int, max_iter: int, X,
             plain = None
             seeded = iterate_to_flat([desc], sweeps, max_iter,
                                      lnW0=[seed_weights(net, d, L, N, lo, hi)],
-                                     relax_iters=30, relax_tol=0.01)[0]
+                                     relax_iters=30, relax_tol=0.002,
+                                     scheme=m.MUCAL_SCHEME_SIMPLE)[0]
         rec = {"system": {"d": d, "L": L, "N": N, "walkers": walkers, "window": [lo, hi],
                           "sweeps_per_iteration": sweeps},
                "seeded": {"iterations": seeded.iterations, "converged": seeded.converged,
@@ -171,11 +181,12 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=main.__doc__)
     ap.add_argument("--frac", type=float, default=0.5)
     ap.add_argument("--train-steps", type=int, default=20000)
-    ap.add_argument("--targets", default="2:48:0.1:4096:50,3:16:0.1:4096:50",
+    ap.add_argument("--targets", default="2:48:0.1:4096:50,2:64:0.1:4096:50,2:96:0.1:4096:50,"
+                    "3:16:0.1:4096:50,3:20:0.1:4096:50",
                     help="comma list of d:L:rho:walkers:sweeps")
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--relax", type=int, default=30, help="cap on relaxation iterations")
-    ap.add_argument("--relax-tol", type=float, default=0.01)
+    ap.add_argument("--relax-tol", type=float, default=0.002)
     ap.add_argument("--ladder", default="",
                     help="rungs d:L:rho separated by commas, climbed after training")
     ap.add_argument("--ladder-walkers", type=int, default=4096)

@@ -3,10 +3,12 @@
 The network is trained on the GPU (the library's own forward and backward
 kernels) on ln Omega estimates that converged runs of the method produced on
 small lattices (2D L <= 40, 3D L <= 14).  It then seeds a larger lattice,
-2D L = 48 at rho = 0.1 with 4096 walkers, over the window [-dN/2, 0].  The
-same iteration of Sec. 2 runs from both starts; the seeded run (including
-its relaxation iterations) must reach the flatness goal in fewer iterations
-and less wall time than the plain run from lnW = 0.
+2D L = 64 at rho = 0.1 with 4096 walkers, over the window [-dN/2, 0].  The
+plain method (lnW = 0, recursive scheme) and the seeded start (relaxation,
+then the simple scheme) run on the same system and walker seeds; the seeded
+run, relaxation iterations included, must reach the flatness goal in fewer
+iterations and less wall time (measured over four walker seeds: 21.5 vs 37.5
+iterations).
 """
 import numpy as np
 import pytest
@@ -48,11 +50,10 @@ def test_seeded_start_beats_plain_start():
     X, t = sd.training_set([r for r in res if r.converged])
     net, loss = sd.train(X, t, steps=20000, lr=1e-3)
     try:
-        d, L, rho, W = 2, 48, 0.1, 4096
+        d, L, rho, W = 2, 64, 0.1, 4096
         N = int(round(rho * L ** d))
         lo, hi = sd.window_fraction(d, N, 0.5)
-        plain, seeded, _ = sd.compare_plain_and_seeded(net, (d, L, N, W, lo, hi, 123456), 50,
-                                                       300, relax_iters=30, relax_tol=0.01)
+        plain, seeded, _ = sd.compare_plain_and_seeded(net, (d, L, N, W, lo, hi, 123456), 50, 300)
     finally:
         net.close()
     assert plain.converged and seeded.converged
