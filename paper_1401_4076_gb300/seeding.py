@@ -56,15 +56,20 @@ def training_set(results):
     return np.concatenate(Xs), np.concatenate(ts)
 
 
-def train(X, t, steps: int = 3000, lr: float = 2e-3, seed: int = 0, cuda_stream=None):
-    """Train the GPU network (full-batch Adam in the library) and return it."""
+def train(X, t, steps: int = 3000, lr: float = 2e-3, seed: int = 0, cuda_stream=None,
+          final_lr_fraction: float = 0.05):
+    """Train the GPU network (full-batch Adam in the library) and return it.
+    The learning rate decays geometrically in chunks of 500 steps from lr to
+    final_lr_fraction * lr, so that training ends in a settled minimum."""
     from .workloads import mlp_initial_params
     net = m.Mlp(mlp_initial_params(seed), cuda_stream=cuda_stream)
     loss = None
     done = 0
-    while done < steps:
+    chunks = max(1, (steps + 499) // 500)
+    for c in range(chunks):
         k = min(500, steps - done)
-        loss = net.train(X, t, steps=k, lr=lr)
+        rate = lr * final_lr_fraction ** (c / max(1, chunks - 1))
+        loss = net.train(X, t, steps=k, lr=rate)
         done += k
     return net, loss
 
