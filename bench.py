@@ -222,7 +222,8 @@ def _config(wl, args):
             "walkers": sum(s[3] for s in wl.systems),
             "sweeps_per_iteration": args.sweeps or wl.sweeps,
             "attempts_per_step": (args.sweeps or wl.sweeps) * sum(s[2] * s[3] for s in wl.systems),
-            "weights": "recursive update from lnW=0; timed steps are iterations W..W+K-1",
+            "weights": "recursive update from lnW=0; timed steps are iterations P+W..P+W+K-1",
+            "prerun_iterations": args.prerun,
             "l2": "flushed (512 MB write) before every timed step",
             "launch": args.launch_desc}
 
@@ -242,6 +243,9 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run after the warm-up steps)")
     ap.add_argument("--tune-sweeps", type=int, default=10)
+    ap.add_argument("--prerun", type=int, default=0,
+                    help="untimed iterations of the recursion before the warm-up (to measure "
+                         "a later stage of the weight iteration; 0 = start at lnW = 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -290,7 +294,9 @@ def main(argv=None):
         for s in range(len(systems)):
             mc.update_weights(s, m.MUCAL_SCHEME_RECURSIVE)
 
-    for it in range(args.warmup):
+    for it in range(args.prerun):
+        step(it)
+    for it in range(args.prerun, args.prerun + args.warmup):
         step(it)
     torch.cuda.synchronize(device)
     explicit = args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0
@@ -321,7 +327,7 @@ def main(argv=None):
     for i in range(args.steps):
         flush.fill_(float(i))
         starts[i].record(stream)
-        step(args.warmup + i)
+        step(args.prerun + args.warmup + i)
         ends[i].record(stream)
         st = mc.stats(0)
         kernel_ms.append(st["kernel_ms"])

@@ -264,9 +264,10 @@ size_t smem_for(const LaunchShape &sh, const SysParams &p)
 int build_work(Context *c, const LaunchShape &sh)
 {
     std::vector<BlockWork> work;
+    std::vector<int32_t> rows_of(c->sys.size(), 0);
     const bool per_walker = (c->flags & MUCAL_FLAG_PER_WALKER_HIST) != 0;
     for (int s = 0; s < (int)c->sys.size(); ++s) {
-        SysParams &p = c->sys[s].p;
+        const SysParams &p = c->sys[s].p;
         int rows = 0;
         for (int w0 = 0; w0 < p.n_walkers; w0 += sh.walkers_per_block) {
             BlockWork bw{};
@@ -278,24 +279,39 @@ int build_work(Context *c, const LaunchShape &sh)
             work.push_back(bw);
         }
         // blocks never outnumber walkers, so the per-walker allocation holds them
-        p.hist_rows = per_walker ? p.n_walkers : rows;
+        rows_of[s] = per_walker ? p.n_walkers : rows;
     }
     std::stable_sort(work.begin(), work.end(), [&](const BlockWork &a, const BlockWork &b) {
         const double ca = (double)c->sys[a.sys].p.N * c->sys[a.sys].p.d;
         const double cb = (double)c->sys[b.sys].p.N * c->sys[b.sys].p.d;
         return ca > cb;
     });
-    if (c->d_work) {
-        cudaFree(c->d_work);
-        c->d_work = nullptr;
-    }
-    CUDA_TRY(c, cudaMalloc(&c->d_work, std::max<size_t>(1, work.size()) * sizeof(BlockWork)));
-    CUDA_TRY(c, cudaMemcpy(c->d_work, work.data(), work.size() * sizeof(BlockWork),
-                           cudaMemcpyHostToDevice));
-    c->n_blocks = (int)work.size();
+    // build the new tables completely before replacing the old ones, so that
+    // a failure leaves the previous launch shape usable
+    BlockWork *d_work = nullptr;
+    cudaError_t e = cudaMalloc(&d_work, std::max<size_t>(1, work.size()) * sizeof(BlockWork));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_work, work.data(), work.size() * sizeof(BlockWork), cudaMemcpyHostToDevice);
     std::vector<SysParams> hp(c->sys.size());
-    for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
-    CUDA_TRY(c, cudaMemcpy(c->d_sys, hp.data(), hp.size() * sizeof(SysParams), cudaMemcpyHostToDevice));
+    for (size_t i = 0; i < c->sys.size(); ++i) {
+        hp[i] = c->sys[i].p;
+        hp[i].hist_rows = rows_of[i];
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_sys, hp.data(), hp.size() * sizeof(SysParams), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_work);
+        // restore the device table of the current shape
+        std::vector<SysParams> cur(c->sys.size());
+        for (size_t i = 0; i < c->sys.size(); ++i) cur[i] = c->sys[i].p;
+        cudaMemcpy(c->d_sys, cur.data(), cur.size() * sizeof(SysParams), cudaMemcpyHostToDevice);
+        return fail(c, e == cudaErrorMemoryAllocation ? MUCAL_ERR_OOM : MUCAL_ERR_CUDA,
+                    "launch table upload failed: %s", cudaGetErrorString(e));
+    }
+    cudaFree(c->d_work);
+    c->d_work = d_work;
+    c->n_blocks = (int)work.size();
+    for (size_t i = 0; i < c->sys.size(); ++i) c->sys[i].p.hist_rows = rows_of[i];
     return MUCAL_OK;
 }
 
