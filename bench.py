@@ -223,9 +223,9 @@ def _config(wl, args):
             "sweeps_per_iteration": args.sweeps or wl.sweeps,
             "attempts_per_step": (args.sweeps or wl.sweeps) * sum(s[2] * s[3] for s in wl.systems),
             "weights": "recursive update from lnW=0; timed steps are iterations P+W..P+W+K-1",
-            "prerun_iterations": args.prerun,
+            "prerun_iterations": getattr(args, "prerun", 0),
             "l2": "flushed (512 MB write) before every timed step",
-            "launch": args.launch_desc}
+            "launch": getattr(args, "launch_desc", None)}
 
 
 def main(argv=None):
