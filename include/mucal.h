@@ -275,8 +275,8 @@ const char *mucal_run_walkers_noalloc_error(void);
  * A 4-128-128-1 multilayer perceptron with GELU activations (gelu(z) =
  * z Phi(z)) that maps a caller-built feature vector of (d, L, rho, E/V) to a
  * prediction of ln Omega(E)/V.  Its only use is to propose starting weights
- * lnW = -V * prediction for the iteration of Sec. 2, which then runs and
- * judges unchanged (the plain start lnW = 0 stays available).  Parameters:
+ * lnW = -V * prediction for the iteration of Sec. 2, which then runs
+ * unchanged (the plain start lnW = 0 stays available).  Parameters:
  * fp32 master copy and Adam state; the forward and backward passes use the
  * bf16-rounded parameters, run the 128x128 layer on the tensor cores (bf16 x
  * bf16, fp32 accumulation; the layer-1 activations enter it as two bf16 terms,

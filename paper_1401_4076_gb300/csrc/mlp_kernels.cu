@@ -1,8 +1,8 @@
 // Weight-seeding network of libmucal: a 4-128-128-1 GELU multilayer
 // perceptron mapping features of (d, L, rho, E/V) to ln Omega(E)/V, trained
 // and evaluated on the GPU.  Not part of the paper: it only proposes starting
-// weights W = 1/Omega_pred for the iteration of Sec. 2, which then runs and
-// judges unchanged.
+// weights W = 1/Omega_pred for the iteration of Sec. 2, which then runs
+// unchanged and decides convergence as before.
 //
 // Numerics: parameters kept in fp32 (master copy, Adam state) and used in
 // bf16; the 128x128 contractions run on the tensor cores as bf16 x bf16 with
