@@ -395,12 +395,13 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
 // ---------------------------------------------------------------------------
 // One thread, one walker: A attempts in order, software-pipelined.  The
 // random numbers and list reads of the next PF attempts are in flight in a
-// register ring while the current attempt is evaluated; a commit patches the
+// register ring while the current attempt is evaluated (the slot just
+// consumed is refilled while its occupation words are being read); a commit patches the
 // in-flight list reads it invalidates (same list slot).  The histogram is
 // kept as a run length (current bin, count) and added to the histogram row
 // only when the energy changes, which records exactly one entry per attempt.
 // ---------------------------------------------------------------------------
-constexpr int kThreadPipe = 4;
+constexpr int kThreadPipe = 6;
 
 template <int D, typename IdxT, bool SB, bool ST>
 __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t *bits,
@@ -448,20 +449,39 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
             if (t < A) {
                 const uint32_t a = fa[s] != NONE ? fa[s] : ra[s];
                 const uint32_t b = fb[s] != NONE ? fb[s] : rb[s];
-                const uint32_t k = rk[s], m = rm[s];
+                const uint32_t k = rk[s], m = rm[s], r2 = rr[s];
                 NbSet<D, SB> na, nb;
                 na.build(p, ba, a, 0xFFFFFFFFu);
                 nb.build(p, ba, b, a);
-                const int de = na.count() - nb.count();
+                uint32_t wa[2 * D], wb[2 * D];
+                na.load(wa);
+                nb.load(wb);
+                // while the occupation words are in flight, refill this slot
+                // with attempt t + PF (its list reads are patched below if this
+                // attempt's commit moves the same slot)
+                const uint64_t tn = t + PF;
+                rk[s] = NONE;
+                rm[s] = NONE;
+                fa[s] = NONE;
+                fb[s] = NONE;
+                if (tn < A) {
+                    const uint4 r = philox10(make_uint4((uint32_t)tn, (uint32_t)(tn >> 32), iter, 0u),
+                                             k0, k1);
+                    rk[s] = __umulhi(r.x, N);
+                    rm[s] = __umulhi(r.y, holes);
+                    rr[s] = r.z;
+                    ra[s] = S[rk[s]];
+                    rb[s] = S[N + rm[s]];
+                }
+                const int de = na.count_from(wa) - nb.count_from(wb);
                 const uint32_t T = thr_load<ST>(thr, row + de);
-                if (T == 0xFFFFFFFFu || rr[s] < T) {
+                if (T == 0xFFFFFFFFu || r2 < T) {
                     bits[a >> 5] &= ~(1u << (a & 31u));
                     bits[b >> 5] |= 1u << (b & 31u);
                     S[k] = (IdxT)b;
                     S[N + m] = (IdxT)a;
 #pragma unroll
                     for (int q = 0; q < PF; ++q) {
-                        if (q == s) continue;
                         fa[q] = (rk[q] == k) ? b : fa[q];
                         fb[q] = (rm[q] == m) ? a : fb[q];
                     }
@@ -477,21 +497,6 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
                 if (run == 0x80000000u) {
                     atomicAdd(hist + bin, (unsigned long long)run);
                     run = 0;
-                }
-                // refill this slot with attempt t + PF
-                const uint64_t tn = t + PF;
-                rk[s] = NONE;
-                rm[s] = NONE;
-                fa[s] = NONE;
-                fb[s] = NONE;
-                if (tn < A) {
-                    const uint4 r = philox10(make_uint4((uint32_t)tn, (uint32_t)(tn >> 32), iter, 0u),
-                                             k0, k1);
-                    rk[s] = __umulhi(r.x, N);
-                    rm[s] = __umulhi(r.y, holes);
-                    rr[s] = r.z;
-                    ra[s] = S[rk[s]];
-                    rb[s] = S[N + rm[s]];
                 }
             }
         }
