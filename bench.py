@@ -249,6 +249,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-convergence", action="store_true",
+                    help="skip the learned-vs-plain convergence comparison (run after the timing)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -371,6 +373,8 @@ def main(argv=None):
 
     if not args.no_e2e:
         line["e2e"] = e2e_measure(wl, args, systems, stream, device, world)
+    if rank == 0 and world == 1 and not args.no_convergence:
+        line["convergence"] = convergence_measure(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle.build import build_oracle
         build_oracle()
@@ -383,6 +387,37 @@ def main(argv=None):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def convergence_measure(stream):
+    """Iterations and wall time to a flat histogram (min/max >= 0.5), plain
+    start lnW = 0 with the recursion against the learned seed, on 2D L=64,
+    N=410, 4096 walkers, 50 sweeps per iteration, window [-dN/2, 0].  The
+    network is trained on the GPU first on small lattices run to flatness by
+    the method itself (its time is reported separately)."""
+    try:
+        from paper_1401_4076_gb300 import seeding as sd
+        t0 = time.perf_counter()
+        small = sd.small_training_systems(0.5)
+        res = sd.iterate_to_flat(small, sweeps=100, max_iter=200, final_sweeps=1000,
+                                 cuda_stream=stream.cuda_stream)
+        X, t = sd.training_set([r for r in res if r.converged])
+        net, loss = sd.train(X, t, steps=20000, lr=1e-3, cuda_stream=stream.cuda_stream)
+        prep = time.perf_counter() - t0
+        d, L, N, W = 2, 64, 410, 4096
+        lo, hi = sd.window_fraction(d, N, 0.5)
+        plain, seeded, _ = sd.compare_plain_and_seeded(net, (d, L, N, W, lo, hi, 123456), 50, 300,
+                                                       cuda_stream=stream.cuda_stream)
+        net.close()
+        return {"system": "2D L=64 N=410, 4096 walkers, window [-410, 0], 50 sweeps/iteration",
+                "goal": "min/max H >= 0.5",
+                "plain": {"iterations": plain.iterations, "wall_s": round(plain.wall_s, 3),
+                          "converged": plain.converged},
+                "learned": {"iterations": seeded.iterations, "wall_s": round(seeded.wall_s, 3),
+                            "converged": seeded.converged},
+                "training_s": round(prep, 3), "training_rows": int(len(t))}
+    except Exception as exc:  # reported, never fatal for the benchmark line
+        return {"error": repr(exc)[:200]}
 
 
 def e2e_measure(wl, args, systems, stream, device, world):
