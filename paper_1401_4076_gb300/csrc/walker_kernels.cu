@@ -352,17 +352,15 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
             const bool later = commit && j > f;
             const bool fix_a = later && k == k_f;
             const bool fix_b = later && m == m_f;
-            if (__any_sync(FULL, fix_a || fix_b)) {
+            if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
                 a = fix_a ? b_f : a;
                 b = fix_b ? a_f : b;
-                if (fix_a || fix_b) {
-                    na.build(p, ba, a, 0xFFFFFFFFu);
-                    nb.build(p, ba, b, a);
-                    wa_own = bits + (a >> 5);
-                    wb_own = bits + (b >> 5);
-                    ma_own = 1u << (a & 31u);
-                    mb_own = 1u << (b & 31u);
-                }
+                na.build(p, ba, a, 0xFFFFFFFFu);
+                nb.build(p, ba, b, a);
+                wa_own = bits + (a >> 5);
+                wb_own = bits + (b >> 5);
+                ma_own = 1u << (a & 31u);
+                mb_own = 1u << (b & 31u);
             }
             na.load(wa);
             nb.load(wb);
