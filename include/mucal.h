@@ -233,6 +233,79 @@ int mucal_checkpoint_size(void *ctx, int32_t sys, int64_t *bytes);
 int mucal_checkpoint_save(void *ctx, int32_t sys, void *buf, int64_t bytes);
 int mucal_checkpoint_load(void *ctx, int32_t sys, const void *buf, int64_t bytes);
 
+/* ---- reweighting to canonical temperatures (Sec. 3) -----------------------
+ * Multicanonical data are taken with the weights W(E) and reweighted to the
+ * temperatures of interest afterwards.  A histogram H(E) sampled with
+ * lnW(E) = ln W(E) estimates Omega(E), up to a constant factor, by
+ * H(E) / W(E), so the canonical distribution at inverse temperature beta is
+ *     P_beta(E) = H(E) exp(-beta E - lnW(E)) / Z_beta        (Eq. 1)
+ * over the visited bins (H > 0).  Bin b holds energy e_lo + b.  For each
+ * beta[i], i < n_beta:
+ *   mean_E[i]  = sum_E P_beta(E) E,   mean_E2[i] = sum_E P_beta(E) E^2
+ *   (both nullable, host float64[n_beta]);
+ *   obs_out[i * n_obs + k] = sum_b P_beta(b) obs[k * n_bins + b] /
+ *                            sum_b P_beta(b), both sums over the bins with
+ *   H > 0 and a finite obs value (obs holds n_obs microcanonical means, for
+ *   example the mean largest droplet at each energy, NaN where nothing was
+ *   measured); NaN if no bin qualifies.  obs may be NULL with n_obs = 0.
+ * Double precision on the host: exponents shifted by their maximum, bins
+ * summed in ascending order.  Errors: INVALID_ARG (NULL H, lnW or beta with
+ * n_beta > 0; n_bins < 1; n_beta or n_obs < 0; a negative H; no visited bin;
+ * a non-finite lnW or beta).  Message: mucal_last_error(NULL). */
+int mucal_reweight(const int64_t *H, const double *lnW, int32_t n_bins, int32_t e_lo,
+                   const double *beta, int32_t n_beta, const double *obs, int32_t n_obs,
+                   double *mean_E, double *mean_E2, double *obs_out);
+
+/* mucal_reweight of system sys's last summed histogram with the weights it
+ * was sampled with (those in force at the last mucal_run_iteration, not the
+ * ones a later mucal_update_weights or mucal_set_weights installed).  Waits
+ * for the context's stream.  Errors: as mucal_reweight, NOT_READY, CUDA. */
+int mucal_reweight_system(void *ctx, int32_t sys, const double *beta, int32_t n_beta,
+                          const double *obs, int32_t n_obs, double *mean_E, double *mean_E2,
+                          double *obs_out);
+
+/* ---- largest droplet (Sec. 3) ---------------------------------------------
+ * A droplet is a cluster of occupied sites connected through nearest-
+ * neighbour bonds of the periodic lattice; its size is its number of
+ * particles, and V_D below is the size of the largest one (0 for N = 0).
+ * mucal_measure_droplets labels the clusters of every walker's current
+ * configuration of every system on the device (asynchronous on the
+ * context's stream), stores each walker's V_D, and adds to per-system
+ * accumulators indexed by the walker's energy bin: count[b] += 1,
+ * sum[b] += V_D, sum2[b] += V_D^2 (exact 64-bit integers).  Call it between
+ * iterations as often as measurements are wanted; sum/count is the
+ * microcanonical mean that mucal_reweight takes as an observable.
+ * mucal_get_droplet_stats: copy the accumulators of sys (each host
+ *   int64[n_bins], any may be NULL); waits for the stream.
+ * mucal_get_largest_droplets: V_D of each walker of sys at the last
+ *   measurement (host int32[n_walkers]); waits for the stream.
+ * mucal_reset_droplet_stats: zero the accumulators of every system.
+ * Errors: INVALID_ARG, NOT_READY (no measurement yet), CUDA, OOM; an
+ * internal consistency failure of the labelling reports MUCAL_ERR_CUDA. */
+int mucal_measure_droplets(void *ctx);
+int mucal_get_droplet_stats(void *ctx, int32_t sys, int64_t *count, int64_t *sum, int64_t *sum2,
+                            int32_t n_bins);
+int mucal_get_largest_droplets(void *ctx, int32_t sys, int32_t *V_D, int32_t n_walkers);
+int mucal_reset_droplet_stats(void *ctx);
+
+/* ---- droplet theory (Sec. 3, Eqs. 8-10) -----------------------------------
+ * mucal_droplet_delta: with the background density rho0, the reduced
+ *   compressibility kappa_hat and the surface free energy tau_W, the excess
+ *   volume V_L = (N - rho0 V) / (1 - 2 rho0) (Eq. 8) and the dimensionless
+ *   Delta = (1 - 2 rho0)^2 / (2 kappa_hat tau_W) * V_L^((d+1)/d) / V
+ *   (Eq. 10); Delta = 0 when V_L <= 0.  Either output may be NULL.
+ * mucal_droplet_lambda: the infinite-volume fraction lambda in [0, 1) of the
+ *   excess held by the largest droplet, the global minimiser over [0, 1] of
+ *   lambda^((d-1)/d) + Delta (1 - lambda)^2 (the bracket of Eq. 9): 0 below
+ *   the critical Delta_c, and the larger root of the stationarity condition
+ *   above it (bisection to double precision).  Where both minima are equal
+ *   (Delta = Delta_c) it returns 0.
+ * Errors: INVALID_ARG for d outside {2, 3}, V < 1, N < 0, rho0 outside
+ *   [0, 1/2), kappa_hat or tau_W <= 0, Delta < 0 or non-finite. */
+int mucal_droplet_delta(int32_t d, int64_t V, int64_t N, double rho0, double kappa_hat,
+                        double tau_W, double *Delta, double *V_L);
+int mucal_droplet_lambda(int32_t d, double Delta, double *lambda);
+
 /* ---- allocation-free walker update (no counterpart in the paper) ---------
  * For callers that cannot allocate device memory: code running where
  * cudaMalloc is not allowed or not wanted, such as inside a memory pool that

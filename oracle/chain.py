@@ -148,5 +148,12 @@ def ising_fixed_m(d: int, L: int, n_up: int, seed: int, beta_ising: float,
     return me.value, me2.value
 
 
+def largest_droplet(d: int, L: int, occ: np.ndarray) -> int:
+    """Particles in the largest nearest-neighbour cluster (Sec. 3), periodic."""
+    o = np.ascontiguousarray(occ, dtype=np.uint8).reshape(-1)
+    assert o.size == volume(d, L)
+    return int(load_oracle().orc_largest_cluster(d, L, _ptr(o)))
+
+
 def num_threads() -> int:
     return int(load_oracle().orc_num_threads())

@@ -117,6 +117,53 @@ def reweight_mean_energy(lnW, H, e_lo, beta):
     return num / den
 
 
+def reweight_moments(lnW, H, e_lo, beta):
+    """(<E>_beta, <E^2>_beta) from a multicanonical histogram sampled with
+    weights lnW (Sec. 3: the data are reweighted to the temperatures of
+    interest): P_beta(E) ~ H(E) exp(-beta E - lnW(E))."""
+    logs = []
+    for b in range(len(H)):
+        if H[b] > 0:
+            e = e_lo + b
+            logs.append((e, math.log(float(H[b])) - beta * e - lnW[b]))
+    mx = max(v for _, v in logs)
+    m0 = m1 = m2 = 0.0
+    for e, v in logs:
+        w = math.exp(v - mx)
+        m0 += w
+        m1 += w * e
+        m2 += w * e * e
+    return m1 / m0, m2 / m0
+
+
+def reweight_observable(lnW, H, e_lo, beta, obs):
+    """Canonical mean at beta of a microcanonical observable obs[b] (NaN where
+    unmeasured) from a multicanonical histogram (Sec. 3): weights
+    H(E) exp(-beta E - lnW(E)) over bins with H > 0 and finite obs."""
+    logs = []
+    for b in range(len(H)):
+        if H[b] > 0 and math.isfinite(obs[b]):
+            logs.append((b, math.log(float(H[b])) - beta * (e_lo + b) - lnW[b]))
+    if not logs:
+        return float("nan")
+    mx = max(v for _, v in logs)
+    z = s = 0.0
+    for b, v in logs:
+        w = math.exp(v - mx)
+        z += w
+        s += w * obs[b]
+    return s / z
+
+
+def exact_moments(omega: dict, beta: float):
+    """(<E>_beta, <E^2>_beta) from an exact density of states (Eq. 1)."""
+    mx = max(-beta * e for e in omega)
+    z = sum(c * math.exp(-beta * e - mx) for e, c in omega.items())
+    m1 = sum(c * e * math.exp(-beta * e - mx) for e, c in omega.items())
+    m2 = sum(c * e * e * math.exp(-beta * e - mx) for e, c in omega.items())
+    return m1 / z, m2 / z
+
+
 def exact_mean_energy(omega: dict, beta: float) -> float:
     """<E>_beta from an exact density of states (Eq. 1, canonical)."""
     mx = max(-beta * e for e in omega)

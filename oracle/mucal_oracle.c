@@ -429,3 +429,37 @@ int orc_ising_fixed_m(int d, int L, int n_up, uint64_t seed, double beta_ising,
     free(spin); free(up); free(down);
     return 0;
 }
+
+/* Largest droplet (Sec. 3): the number of particles in the largest set of
+ * occupied sites connected through nearest-neighbour bonds of the periodic
+ * lattice; 0 for an empty lattice.  Breadth-first search from every
+ * not-yet-seen particle, with an explicit queue. */
+int64_t orc_largest_cluster(int d, int L, const uint8_t *occ)
+{
+    int64_t V = orc_volume(d, L);
+    uint8_t *seen = (uint8_t *)calloc((size_t)V, 1);
+    int64_t *queue = (int64_t *)malloc((size_t)V * sizeof(int64_t));
+    int64_t best = 0;
+    int64_t nb[6];
+    for (int64_t start = 0; start < V; ++start) {
+        if (!occ[start] || seen[start]) continue;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = start;
+        seen[start] = 1;
+        while (head < tail) {
+            int64_t s = queue[head++];
+            orc_neighbours(d, L, s, nb);
+            for (int k = 0; k < 2 * d; ++k) {
+                int64_t t = nb[k];
+                if (occ[t] && !seen[t]) {
+                    seen[t] = 1;
+                    queue[tail++] = t;
+                }
+            }
+        }
+        if (tail > best) best = tail;
+    }
+    free(seen);
+    free(queue);
+    return best;
+}

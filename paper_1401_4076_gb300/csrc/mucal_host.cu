@@ -36,6 +36,9 @@ struct System {
     uint32_t *thr_pinned = nullptr; // staging buffer of the threshold upload
     size_t thr_count = 0;
     uint64_t last_attempts = 0;
+    std::vector<double> lnW_run;    // the weights of the last iteration's thresholds
+    unsigned long long *drop_acc = nullptr;  // device [3][n_bins] droplet accumulators
+    int32_t *drop_last = nullptr;            // device [n_walkers] V_D of the last measurement
 };
 
 struct Context {
@@ -53,6 +56,10 @@ struct Context {
     bool ran = false;
     uint64_t sweeps_last = 0;
     uint64_t launches = 0;
+    int *d_drop_err = nullptr;           // droplet labelling failure flag
+    uint32_t *drop_scratch = nullptr;    // global parent arrays for lattices too large for smem
+    size_t drop_scratch_words = 0;
+    bool measured = false;
     std::string err;
 };
 
@@ -229,8 +236,12 @@ void free_system(System &s)
     cudaFree(s.p.accepts);
     cudaFree(s.p.H);
     if (s.thr_pinned) cudaFreeHost(s.thr_pinned);
+    cudaFree(s.drop_acc);
+    cudaFree(s.drop_last);
     s.p = SysParams{};
     s.thr_pinned = nullptr;
+    s.drop_acc = nullptr;
+    s.drop_last = nullptr;
 }
 
 void destroy_context(Context *c)
@@ -241,6 +252,8 @@ void destroy_context(Context *c)
     for (auto &s : c->sys) free_system(s);
     cudaFree(c->d_sys);
     cudaFree(c->d_work);
+    cudaFree(c->d_drop_err);
+    cudaFree(c->drop_scratch);
     if (c->ev_it0) cudaEventDestroy(c->ev_it0);
     if (c->ev_k0) cudaEventDestroy(c->ev_k0);
     if (c->ev_k1) cudaEventDestroy(c->ev_k1);
@@ -378,7 +391,21 @@ int fetch_histogram(Context *c, System &s)
     return MUCAL_OK;
 }
 
+int check_droplet_error(Context *c)
+{
+    int flag = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_drop_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (flag == 1) return fail(c, MUCAL_ERR_CUDA, "droplet labelling exceeded its iteration limit");
+    if (flag == 2) return fail(c, MUCAL_ERR_CUDA, "droplet measurement met an energy outside the window");
+    return MUCAL_OK;
+}
+
 }  // namespace
+
+namespace mucal {
+void set_init_error(const char *msg) { g_init_error = msg; }
+}  // namespace mucal
 
 extern "C" {
 
@@ -486,12 +513,29 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
         s.visited.assign(p.n_bins, 0);
         s.pacc.assign(p.n_bins, 0.0);
         s.H.assign(p.n_bins, 0);
+        s.lnW_run.assign(p.n_bins, 0.0);
+        if (cudaMalloc(&ptr, 3 * (size_t)p.n_bins * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of droplet accumulators failed"));
+        }
+        s.drop_acc = static_cast<unsigned long long *>(ptr);
+        if (cudaMalloc(&ptr, nw * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of droplet sizes failed"));
+        }
+        s.drop_last = static_cast<int32_t *>(ptr);
+        if (cudaMemsetAsync(s.drop_acc, 0, 3 * (size_t)p.n_bins * 8, c->stream) != cudaSuccess ||
+            cudaMemsetAsync(s.drop_last, 0, nw * sizeof(int32_t), c->stream) != cudaSuccess)
+            return bail(fail(nullptr, MUCAL_ERR_CUDA, "memset failed"));
         if (cudaMemsetAsync(p.bits, 0, nw * p.words * sizeof(uint32_t), c->stream) != cudaSuccess ||
             cudaMemsetAsync(p.hist, 0, nw * (size_t)p.n_bins * 8, c->stream) != cudaSuccess ||
             cudaMemsetAsync(p.H, 0, (size_t)p.n_bins * 8, c->stream) != cudaSuccess ||
             cudaMemsetAsync(p.accepts, 0, nw * 8, c->stream) != cudaSuccess)
             return bail(fail(nullptr, MUCAL_ERR_CUDA, "memset failed"));
     }
+    if (cudaMalloc(&c->d_drop_err, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(c->d_drop_err, 0, sizeof(int), c->stream) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of the droplet error flag failed"));
     if (cudaMalloc(&c->d_sys, n_sys * sizeof(SysParams)) != cudaSuccess)
         return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of system table failed"));
     std::vector<SysParams> hp(n_sys);
@@ -611,6 +655,7 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
         CUDA_TRY(c, cudaMemsetAsync(s.p.H, 0, (size_t)s.p.n_bins * 8, c->stream));
         s.hist_on_host = false;
         s.last_attempts = (uint64_t)sweeps * (uint64_t)s.p.N * nw;
+        s.lnW_run = s.lnW;
     }
     CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
     CUDA_TRY(c, mucal::launch_walker_update(c->d_sys, c->d_work, c->n_blocks, c->shape,
@@ -774,6 +819,101 @@ int mucal_histogram_device_ptr(void *ctx, int32_t sys, void **dptr)
     if (rc != MUCAL_OK) return rc;
     if (!dptr) return fail(c, MUCAL_ERR_INVALID_ARG, "dptr is NULL");
     *dptr = c->sys[sys].p.H;
+    return MUCAL_OK;
+}
+
+int mucal_reweight_system(void *ctx, int32_t sys, const double *beta, int32_t n_beta,
+                          const double *obs, int32_t n_obs, double *mean_E, double *mean_E2,
+                          double *obs_out)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    System &s = c->sys[sys];
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    rc = fetch_histogram(c, s);
+    if (rc != MUCAL_OK) return rc;
+    rc = mucal_reweight(s.H.data(), s.lnW_run.data(), s.p.n_bins, s.p.e_lo, beta, n_beta, obs, n_obs,
+                        mean_E, mean_E2, obs_out);
+    if (rc != MUCAL_OK) c->err = mucal_last_error(nullptr);
+    return rc;
+}
+
+int mucal_measure_droplets(void *ctx)
+{
+    Context *c = as_ctx(ctx);
+    if (!c) return MUCAL_ERR_INVALID_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    std::vector<mucal::DropletPlan> plans(c->sys.size());
+    size_t scratch = 0;
+    for (size_t i = 0; i < c->sys.size(); ++i) {
+        CUDA_TRY(c, mucal::droplet_plan(c->sys[i].p, &plans[i]));
+        scratch = std::max(scratch, plans[i].scratch_words);
+    }
+    if (scratch > c->drop_scratch_words) {
+        // the previous scratch may still be read by an earlier measurement
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->drop_scratch);
+        c->drop_scratch = nullptr;
+        c->drop_scratch_words = 0;
+        CUDA_TRY(c, cudaMalloc(&c->drop_scratch, scratch * sizeof(uint32_t)));
+        c->drop_scratch_words = scratch;
+    }
+    for (size_t i = 0; i < c->sys.size(); ++i) {
+        const System &s = c->sys[i];
+        const mucal::DropletOut o{s.drop_acc, s.drop_last, c->d_drop_err};
+        CUDA_TRY(c, mucal::launch_droplets(s.p, o, plans[i], c->drop_scratch, c->stream));
+    }
+    c->measured = true;
+    return MUCAL_OK;
+}
+
+int mucal_get_droplet_stats(void *ctx, int32_t sys, int64_t *count, int64_t *sum, int64_t *sum2,
+                            int32_t n_bins)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    const System &s = c->sys[sys];
+    if (n_bins != s.p.n_bins) return fail(c, MUCAL_ERR_INVALID_ARG, "n_bins must be %d", s.p.n_bins);
+    if (!c->measured) return fail(c, MUCAL_ERR_NOT_READY, "no droplet measurement yet");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    rc = check_droplet_error(c);
+    if (rc != MUCAL_OK) return rc;
+    int64_t *dst[3] = {count, sum, sum2};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k])
+            CUDA_TRY(c, cudaMemcpyAsync(dst[k], s.drop_acc + (size_t)k * s.p.n_bins,
+                                        (size_t)s.p.n_bins * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MUCAL_OK;
+}
+
+int mucal_get_largest_droplets(void *ctx, int32_t sys, int32_t *V_D, int32_t n_walkers)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    const System &s = c->sys[sys];
+    if (!V_D || n_walkers != s.p.n_walkers)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "V_D must hold n_walkers = %d", s.p.n_walkers);
+    if (!c->measured) return fail(c, MUCAL_ERR_NOT_READY, "no droplet measurement yet");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    rc = check_droplet_error(c);
+    if (rc != MUCAL_OK) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(V_D, s.drop_last, (size_t)n_walkers * 4, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MUCAL_OK;
+}
+
+int mucal_reset_droplet_stats(void *ctx)
+{
+    Context *c = as_ctx(ctx);
+    if (!c) return MUCAL_ERR_INVALID_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    for (const System &s : c->sys)
+        CUDA_TRY(c, cudaMemsetAsync(s.drop_acc, 0, 3 * (size_t)s.p.n_bins * 8, c->stream));
     return MUCAL_OK;
 }
 

@@ -62,4 +62,23 @@ cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_s
                                cudaStream_t stream);
 cudaError_t walker_update_max_smem(int *bytes);
 
+// Largest-droplet measurement (droplet_kernels.cu).
+struct DropletOut {
+    unsigned long long *acc;   // [3][n_bins]: count, sum V_D, sum V_D^2 per energy bin
+    int32_t *last;             // [n_walkers] V_D at the last measurement
+    int *err;                  // set non-zero on a labelling or energy-range failure
+};
+struct DropletPlan {
+    bool shared;               // parent array in shared memory (else global scratch)
+    int grid;                  // blocks; each strides over the walkers
+    size_t smem;               // dynamic shared memory per block
+    size_t scratch_words;      // uint32 words of global scratch the launch needs
+};
+cudaError_t droplet_plan(const SysParams &p, DropletPlan *plan);
+cudaError_t launch_droplets(const SysParams &p, const DropletOut &o, const DropletPlan &plan,
+                            uint32_t *scratch, cudaStream_t stream);
+
+// Error message of calls that have no context (mucal_host.cu).
+void set_init_error(const char *msg);
+
 }  // namespace mucal

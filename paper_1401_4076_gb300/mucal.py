@@ -42,6 +42,9 @@ EXPORTED = [
     "mucal_mlp_get_params", "mucal_mlp_forward", "mucal_mlp_gradients", "mucal_mlp_train",
     "mucal_run_walkers_noalloc", "mucal_run_walkers_noalloc_error",
     "mucal_checkpoint_size", "mucal_checkpoint_save", "mucal_checkpoint_load",
+    "mucal_reweight", "mucal_reweight_system", "mucal_measure_droplets", "mucal_get_droplet_stats",
+    "mucal_get_largest_droplets", "mucal_reset_droplet_stats", "mucal_droplet_delta",
+    "mucal_droplet_lambda",
 ]
 
 
@@ -115,6 +118,15 @@ def load_library(path: str = LIB_PATH):
         "mucal_checkpoint_size": (ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
         "mucal_checkpoint_save": (ctypes.c_int, [P, I32, P, I64]),
         "mucal_checkpoint_load": (ctypes.c_int, [P, I32, P, I64]),
+        "mucal_reweight": (ctypes.c_int, [P, P, I32, I32, P, I32, P, I32, P, P, P]),
+        "mucal_reweight_system": (ctypes.c_int, [P, I32, P, I32, P, I32, P, P, P]),
+        "mucal_measure_droplets": (ctypes.c_int, [P]),
+        "mucal_get_droplet_stats": (ctypes.c_int, [P, I32, P, P, P, I32]),
+        "mucal_get_largest_droplets": (ctypes.c_int, [P, I32, P, I32]),
+        "mucal_reset_droplet_stats": (ctypes.c_int, [P]),
+        "mucal_droplet_delta": (ctypes.c_int, [I32, I64, I64, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, P, P]),
+        "mucal_droplet_lambda": (ctypes.c_int, [I32, ctypes.c_double, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -279,6 +291,84 @@ def mucal_run_walkers_noalloc(desc, sweeps, iteration, bits_ptr, S_ptr, E_ptr, t
         raise MucalError(rc, lib.mucal_run_walkers_noalloc_error().decode())
 
 
+def _f64(a):
+    return np.ascontiguousarray(np.atleast_1d(np.asarray(a, dtype=np.float64)))
+
+
+def _reweight_args(beta, obs, n_bins):
+    b = _f64(beta)
+    if obs is None:
+        o = None
+        n_obs = 0
+    else:
+        o = np.ascontiguousarray(np.atleast_2d(np.asarray(obs, dtype=np.float64)))
+        if o.shape[1] != n_bins:
+            raise ValueError(f"obs rows must hold n_bins = {n_bins} values")
+        n_obs = o.shape[0]
+    mE = np.zeros(b.size)
+    mE2 = np.zeros(b.size)
+    out = np.zeros((b.size, n_obs)) if n_obs else None
+    return b, o, n_obs, mE, mE2, out
+
+
+def mucal_reweight(H, lnW, e_lo, beta, obs=None):
+    """(<E>, <E^2>[, obs means]) at each beta from a histogram H sampled with
+    lnW (Sec. 3 reweighting); obs: (n_obs, n_bins) microcanonical means, NaN
+    where unmeasured."""
+    h = np.ascontiguousarray(H, dtype=np.int64)
+    w = np.ascontiguousarray(lnW, dtype=np.float64)
+    if w.size != h.size:
+        raise ValueError("H and lnW differ in length")
+    b, o, n_obs, mE, mE2, out = _reweight_args(beta, obs, h.size)
+    _check(load_library().mucal_reweight(_ptr(h), _ptr(w), h.size, int(e_lo), _ptr(b), b.size,
+                                         _ptr(o), n_obs, _ptr(mE), _ptr(mE2), _ptr(out)), None)
+    return (mE, mE2) if out is None else (mE, mE2, out)
+
+
+def mucal_reweight_system(ctx, sys, n_bins, beta, obs=None):
+    b, o, n_obs, mE, mE2, out = _reweight_args(beta, obs, n_bins)
+    _check(load_library().mucal_reweight_system(ctx, sys, _ptr(b), b.size, _ptr(o), n_obs,
+                                                _ptr(mE), _ptr(mE2), _ptr(out)), ctx)
+    return (mE, mE2) if out is None else (mE, mE2, out)
+
+
+def mucal_measure_droplets(ctx):
+    _check(load_library().mucal_measure_droplets(ctx), ctx)
+
+
+def mucal_get_droplet_stats(ctx, sys, n_bins):
+    """(count, sum V_D, sum V_D^2) per energy bin, int64 arrays."""
+    out = [np.zeros(n_bins, dtype=np.int64) for _ in range(3)]
+    _check(load_library().mucal_get_droplet_stats(ctx, sys, *[_ptr(a) for a in out], n_bins), ctx)
+    return tuple(out)
+
+
+def mucal_get_largest_droplets(ctx, sys, n_walkers):
+    out = np.zeros(n_walkers, dtype=np.int32)
+    _check(load_library().mucal_get_largest_droplets(ctx, sys, _ptr(out), n_walkers), ctx)
+    return out
+
+
+def mucal_reset_droplet_stats(ctx):
+    _check(load_library().mucal_reset_droplet_stats(ctx), ctx)
+
+
+def mucal_droplet_delta(d, V, N, rho0, kappa_hat, tau_W):
+    """(Delta, V_L) of Eqs. 8 and 10."""
+    delta = ctypes.c_double()
+    vl = ctypes.c_double()
+    _check(load_library().mucal_droplet_delta(int(d), int(V), int(N), float(rho0), float(kappa_hat),
+                                              float(tau_W), ctypes.addressof(delta),
+                                              ctypes.addressof(vl)), None)
+    return delta.value, vl.value
+
+
+def mucal_droplet_lambda(d, Delta):
+    lam = ctypes.c_double()
+    _check(load_library().mucal_droplet_lambda(int(d), float(Delta), ctypes.addressof(lam)), None)
+    return lam.value
+
+
 # --------------------------------------------------------------------------
 # Convenience wrapper.
 # --------------------------------------------------------------------------
@@ -364,6 +454,21 @@ class Mucal:
 
     def restore(self, sys, buf):
         mucal_checkpoint_load(self.ctx, sys, buf)
+
+    def reweight(self, sys, beta, obs=None):
+        return mucal_reweight_system(self.ctx, sys, self.info[sys]["n_bins"], beta, obs)
+
+    def measure_droplets(self):
+        mucal_measure_droplets(self.ctx)
+
+    def droplet_stats(self, sys):
+        return mucal_get_droplet_stats(self.ctx, sys, self.info[sys]["n_bins"])
+
+    def largest_droplets(self, sys):
+        return mucal_get_largest_droplets(self.ctx, sys, self.info[sys]["n_walkers"])
+
+    def reset_droplet_stats(self):
+        mucal_reset_droplet_stats(self.ctx)
 
 
 # --------------------------------------------------------------------------

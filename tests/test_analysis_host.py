@@ -1,0 +1,144 @@
+"""Host-side analysis functions of libmucal against the oracle (no GPU).
+
+mucal_reweight, mucal_droplet_delta and mucal_droplet_lambda run in double
+precision on the host; they are compared with the oracle's plain versions
+(Sec. 3, Eqs. 1 and 8-10) and with brute-force sums over every configuration
+of a small lattice.
+"""
+import math
+import os
+from fractions import Fraction
+from itertools import combinations
+
+import numpy as np
+import pytest
+
+from oracle import chain, droplet, muca
+from paper_1401_4076_gb300 import mucal as m
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_1401_4076_gb300 import _build_ext
+    _build_ext.build_library()
+    return m.load_library()
+
+
+def test_reweight_matches_oracle_on_random_histograms():
+    rng = np.random.default_rng(5)
+    for nb in (1, 7, 41, 300):
+        H = rng.integers(0, 10 ** 9, nb)
+        H[rng.random(nb) < 0.3] = 0
+        H[rng.integers(nb)] = 17
+        lnW = rng.normal(scale=30.0, size=nb)
+        e_lo = -int(rng.integers(0, 2 * nb))
+        betas = np.array([0.0, 0.3, 2.6667, -1.0, 7.0])
+        obs = rng.normal(size=(2, nb))
+        obs[1, rng.random(nb) < 0.4] = np.nan
+        mE, mE2, out = m.mucal_reweight(H, lnW, e_lo, betas, obs)
+        for i, bt in enumerate(betas):
+            e1, e2 = muca.reweight_moments(lnW, H, e_lo, bt)
+            assert mE[i] == pytest.approx(e1, rel=1e-12, abs=1e-12)
+            assert mE2[i] == pytest.approx(e2, rel=1e-12, abs=1e-12)
+            for k in range(2):
+                ref = muca.reweight_observable(lnW, H, e_lo, bt, obs[k])
+                if math.isnan(ref):
+                    assert math.isnan(out[i, k])
+                else:
+                    assert out[i, k] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_reweight_of_exact_histogram_is_canonical_enumeration():
+    """4x4, N = 8: an exact multicanonical histogram with arbitrary weights,
+    reweighted, gives <E>, <E^2> and <V_D> equal to the plain canonical sums
+    over all C(16, 8) configurations."""
+    d, L, N, V = 2, 4, 8, 16
+    e_lo = -d * N
+    nb = d * N + 1
+    per_e = {}
+    configs = []
+    for combo in combinations(range(V), N):
+        occ = np.zeros(V, np.uint8)
+        occ[list(combo)] = 1
+        e = chain.energy(d, L, occ)
+        vd = chain.largest_droplet(d, L, occ)
+        configs.append((e, vd))
+        per_e.setdefault(e, []).append(vd)
+    rng = np.random.default_rng(3)
+    lnW = rng.normal(size=nb)
+    H = np.zeros(nb, np.int64)
+    obs = np.full(nb, np.nan)
+    scale = 1e12
+    z0 = sum(len(v) * math.exp(lnW[e - e_lo]) for e, v in per_e.items())
+    for e, v in per_e.items():
+        H[e - e_lo] = int(round(scale * len(v) * math.exp(lnW[e - e_lo]) / z0))
+        obs[e - e_lo] = sum(v) / len(v)
+    for beta in (0.0, 0.8, 2.0):
+        mE, mE2, out = m.mucal_reweight(H, lnW, e_lo, [beta], obs[None, :])
+        w = np.array([math.exp(-beta * e) for e, _ in configs])
+        E = np.array([e for e, _ in configs], float)
+        D = np.array([v for _, v in configs], float)
+        # H is rounded to integers of order 1e12, so agreement is to ~1e-10
+        assert mE[0] == pytest.approx((w * E).sum() / w.sum(), rel=1e-9)
+        assert mE2[0] == pytest.approx((w * E * E).sum() / w.sum(), rel=1e-9)
+        assert out[0, 0] == pytest.approx((w * D).sum() / w.sum(), rel=1e-9)
+
+
+def test_reweight_rejects_bad_input():
+    H = np.array([0, 3, 4])
+    w = np.zeros(3)
+    with pytest.raises(m.MucalError):
+        m.mucal_reweight(np.zeros(3, np.int64), w, 0, [1.0])
+    with pytest.raises(m.MucalError):
+        m.mucal_reweight(np.array([1, -1, 2]), w, 0, [1.0])
+    with pytest.raises(m.MucalError):
+        m.mucal_reweight(H, np.array([0.0, np.inf, 0.0]), 0, [1.0])
+    with pytest.raises(m.MucalError):
+        m.mucal_reweight(H, w, 0, [np.nan])
+    assert "beta" in m.mucal_last_error(None)
+
+
+def test_droplet_delta_matches_oracle():
+    for d, V, N, rho0, kap, tau in ((2, 6400, 100, 0.00675, 0.02708, 1.06125),
+                                    (3, 32768, 300, 0.002739, 0.00608, 2.861),
+                                    (2, 100, 0, 0.0, 1.0, 1.0), (3, 1000, 2, 0.01, 0.1, 0.2)):
+        D, vl = m.mucal_droplet_delta(d, V, N, rho0, kap, tau)
+        assert vl == pytest.approx(droplet.excess_volume(V, N, rho0), rel=1e-14, abs=1e-14)
+        assert D == pytest.approx(droplet.delta(d, V, N, rho0, kap, tau), rel=1e-13, abs=0)
+    with pytest.raises(m.MucalError):
+        m.mucal_droplet_delta(4, 10, 1, 0.0, 1.0, 1.0)
+    with pytest.raises(m.MucalError):
+        m.mucal_droplet_delta(2, 10, 1, 0.5, 1.0, 1.0)
+
+
+def test_droplet_lambda_matches_brute_force():
+    for d in (2, 3):
+        dc = (1 / d) * ((d + 1) / 2) ** ((d + 1) / d)
+        for D in np.concatenate([np.linspace(0, 3, 61), [5.0, 10.0, 50.0, 1e3]]):
+            if abs(D - dc) < 1e-3:
+                continue
+            ref = droplet.lambda_of_delta(d, D)
+            assert m.mucal_droplet_lambda(d, D) == pytest.approx(ref, abs=1e-6), (d, D)
+    with pytest.raises(m.MucalError):
+        m.mucal_droplet_lambda(2, -1.0)
+
+
+def test_droplet_lambda_critical_point_is_the_printed_one():
+    """The library's jump location, found by bisection on its output, against
+    the Delta_c and lambda_c printed in Sec. 3."""
+    for line in open(os.path.join(GOLDEN, "droplet_critical.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        d, dc, lc = line.split()
+        d, dc, lc = int(d), float(dc), float(Fraction(lc))
+        lo, hi = 0.5, 1.5
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if m.mucal_droplet_lambda(d, mid) > 0:
+                hi = mid
+            else:
+                lo = mid
+        assert hi == pytest.approx(dc, abs=5e-5)
+        assert m.mucal_droplet_lambda(d, hi) == pytest.approx(lc, abs=1e-6)

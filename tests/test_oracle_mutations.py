@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case copies the oracle's C source, plants one mistake (a flipped sign,
-a dropped exclusion, a wrong constant, a double count, a wrong rounding),
+a dropped exclusion, a wrong constant, a double count, a wrong rounding, a
+half-followed bond),
 builds it with gcc into a temporary directory and runs the pin that should
 catch it against the mutant.  The pin must fail on every mutant and pass on
 the unmodified oracle.  Nothing here touches a GPU.
@@ -25,6 +26,7 @@ MUTATIONS = {
     "threshold rounded up": ("double x = floor(ldexp(exp(delta), 32));",
                              "double x = ceil(ldexp(exp(delta), 32)) + 4096.0;"),
     "bonds counted twice": ("if (occ[nb[2 * k + 1]]) ++pairs;", "if (occ[nb[2 * k + 1]]) pairs += 2;"),
+    "cluster search follows +1 bonds only": ("int64_t t = nb[k];", "int64_t t = nb[k | 1];"),
 }
 
 
@@ -110,6 +112,21 @@ def pin_thresholds_bound(lib):
     return True
 
 
+def pin_largest_cluster(lib):
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(11)
+    for d, L in ((2, 6), (3, 4)):
+        V = L ** d
+        g = nx.grid_graph(dim=[L] * d, periodic=True)
+        for _ in range(20):
+            occ = (rng.random(V) < 0.45).astype(np.uint8)
+            keep = [t for t in g.nodes if occ[sum(int(t[k]) * L ** k for k in range(d))]]
+            ref = max((len(c) for c in nx.connected_components(g.subgraph(keep))), default=0)
+            if lib.orc_largest_cluster(d, L, _p(occ)) != ref:
+                return False
+    return True
+
+
 def pin_philox_triton(lib, tmp_path):
     here = os.path.dirname(os.path.abspath(__file__))
     rng = np.random.default_rng(7)
@@ -134,6 +151,7 @@ CASES = [
     ("Philox key increment wrong", "philox"),
     ("threshold rounded up", "thresholds"),
     ("bonds counted twice", "energy"),
+    ("cluster search follows +1 bonds only", "largest cluster"),
 ]
 
 
@@ -144,6 +162,8 @@ def _run_pin(kind, lib, tmp_path):
         return pin_energy_roll(lib)
     if kind == "thresholds":
         return pin_thresholds_bound(lib)
+    if kind == "largest cluster":
+        return pin_largest_cluster(lib)
     if kind == "philox":
         pytest.importorskip("triton")
         return pin_philox_triton(lib, tmp_path)

@@ -157,3 +157,19 @@ def test_multicanonical_simple_scheme_flattens_3x3():
     sysm = muca.System(2, 3, 4, 16, 7)
     iters, H, f = muca.run_to_flat(sysm, 1000, 30, "simple", t_lo=-4, t_hi=-2)
     assert f >= 0.5
+
+
+def test_reweighting_exact_from_exact_histogram():
+    """Reweighting (Sec. 3) of an exact multicanonical histogram to any beta
+    gives the canonical moments of the enumerated density of states."""
+    rng = np.random.default_rng(9)
+    lnW = rng.normal(size=NB)
+    H = _exact_hist(OM, lnW, E_LO)
+    for beta in (0.0, 0.5, 1.3, -0.4):
+        e1, e2 = muca.reweight_moments(lnW, H, E_LO, beta)
+        x1, x2 = muca.exact_moments(OM, beta)
+        assert e1 == pytest.approx(x1, rel=1e-10)
+        assert e2 == pytest.approx(x2, rel=1e-10)
+    # infinite temperature: the plain average over all C(16, 8) states
+    mean = sum(c * e for e, c in OM.items()) / math.comb(16, 8)
+    assert muca.exact_moments(OM, 0.0)[0] == pytest.approx(mean, rel=1e-12)
