@@ -264,6 +264,31 @@ int mucal_reweight_system(void *ctx, int32_t sys, const double *beta, int32_t n_
                           const double *obs, int32_t n_obs, double *mean_E, double *mean_E2,
                           double *obs_out);
 
+/* ---- replica exchange (parallel tempering, Sec. 3) ------------------------
+ * The energy ranges of the multicanonical runs come from short parallel-
+ * tempering runs.  A context whose n_sys systems are copies of one lattice
+ * (same d, L, N, walker count and window), system k set to the canonical
+ * weights lnW_k(E) = -beta[k] E with mucal_set_weights, is a tempering
+ * ladder: walker w of system k is replica w at inverse temperature beta[k],
+ * and mucal_run_iteration is its canonical Metropolis update.
+ * mucal_replica_exchange proposes, for every walker w and every pair of
+ * systems (k, k+1) with k = parity, parity + 2, ... (k + 1 < n_sys), to
+ * exchange the configurations of walker w of the two systems, accepted with
+ * probability min(1, exp((beta[k] - beta[k+1]) (E_k - E_k+1))): per pair
+ * and energy difference the host builds in double precision a uint32
+ * threshold T (0xFFFFFFFF if the exponent is >= 0, else
+ * min(floor(2^32 exp(exponent)), 0xFFFFFFFE)) and the device accepts iff
+ * T == 0xFFFFFFFF or r < T, r = word 0 of Philox4x32-10 with walker w's key
+ * of system k (seed_base_k + w) and counter (round, 0, 0, 2).  Asynchronous
+ * on the context's stream; accepted (nullable, host int64[n_sys - 1])
+ * receives the accepted exchanges per pair (pairs not of this parity get 0),
+ * in which case the call waits for the stream.  Histograms and weights are
+ * not touched.
+ * Errors: INVALID_ARG (NULL beta, n_sys not the context's system count or
+ * < 2, parity not 0/1, systems that differ, non-finite beta), OOM, CUDA. */
+int mucal_replica_exchange(void *ctx, const double *beta, int32_t n_sys, uint32_t round,
+                           int32_t parity, int64_t *accepted);
+
 /* ---- largest droplet (Sec. 3) ---------------------------------------------
  * A droplet is a cluster of occupied sites connected through nearest-
  * neighbour bonds of the periodic lattice; its size is its number of

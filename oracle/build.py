@@ -55,6 +55,7 @@ def _bind(lib):
         "orc_delta_e_mask": (c.c_int, [c.c_int, c.c_int, u64, i64, i64]),
         "orc_ising_fixed_m": (c.c_int, [c.c_int, c.c_int, c.c_int, u64, dbl, i64, i64, P, P]),
         "orc_largest_cluster": (i64, [c.c_int, c.c_int, P]),
+        "orc_replica_exchange": (None, [c.c_int, i64, i64, P, P, u32, c.c_int, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

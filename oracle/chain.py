@@ -155,5 +155,20 @@ def largest_droplet(d: int, L: int, occ: np.ndarray) -> int:
     return int(load_oracle().orc_largest_cluster(d, L, _ptr(o)))
 
 
+def replica_exchange(beta, seeds, round_: int, parity: int, S: np.ndarray, occ: np.ndarray,
+                     E: np.ndarray) -> np.ndarray:
+    """Parallel-tempering exchange between neighbouring systems, in place on
+    S[K, W, V], occ[K, W, V], E[K, W]; returns accepted exchanges per pair."""
+    K, W, V = S.shape
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+    assert b.size == K and sd.size == K
+    assert S.dtype == np.int32 and occ.dtype == np.uint8 and E.dtype == np.int64
+    acc = np.zeros(max(K - 1, 1), dtype=np.int64)
+    load_oracle().orc_replica_exchange(K, W, V, _ptr(sd), _ptr(b), np.uint32(round_), int(parity),
+                                       _ptr(S), _ptr(occ), _ptr(E), _ptr(acc))
+    return acc[: K - 1]
+
+
 def num_threads() -> int:
     return int(load_oracle().orc_num_threads())

@@ -463,3 +463,53 @@ int64_t orc_largest_cluster(int d, int L, const uint8_t *occ)
     free(queue);
     return best;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Replica exchange (parallel tempering; Sec. 3 takes its energy ranges     */
+/* from short tempering runs).  K copies of one lattice at inverse          */
+/* temperatures beta[k], n_walkers replicas each; arrays are               */
+/* S[K][n_walkers][V], occ[K][n_walkers][V], E[K][n_walkers].  For each     */
+/* pair (k, k+1) with k = parity, parity + 2, ... and each walker w, the    */
+/* configurations of the two systems' walker w trade places with            */
+/* probability min(1, exp((beta_k - beta_k+1) (E_k - E_k+1))), in the same */
+/* uint32 form as the move acceptance (always if the exponent is >= 0,      */
+/* else iff r < min(floor(2^32 e^x), 0xFFFFFFFE)) with r = word 0 of        */
+/* Philox(counter = (round, 0, 0, 2), key = seeds[k] + w).  accepted[k]     */
+/* counts the exchanges of pair k (the caller zeroes it).                    */
+/* ------------------------------------------------------------------------ */
+void orc_replica_exchange(int K, int64_t n_walkers, int64_t V, const uint64_t *seeds,
+                          const double *beta, uint32_t round, int parity, int32_t *S,
+                          uint8_t *occ, int64_t *E, int64_t *accepted)
+{
+    for (int k = parity; k + 1 < K; k += 2) {
+        for (int64_t w = 0; w < n_walkers; ++w) {
+            int64_t ia = (int64_t)k * n_walkers + w;
+            int64_t ib = (int64_t)(k + 1) * n_walkers + w;
+            uint32_t key[2], ctr[4] = {round, 0u, 0u, 2u}, r[4];
+            orc_key_of_seed(seeds[k] + (uint64_t)w, key);
+            orc_philox4x32_10(ctr, key, r);
+            double x = (beta[k] - beta[k + 1]) * (double)(E[ia] - E[ib]);
+            int take;
+            if (x >= 0.0) {
+                take = 1;
+            } else {
+                double q = floor(ldexp(exp(x), 32));
+                uint32_t t = (q >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)q;
+                take = r[0] < t;
+            }
+            if (!take) continue;
+            ++accepted[k];
+            for (int64_t i = 0; i < V; ++i) {
+                int32_t ts = S[ia * V + i];
+                S[ia * V + i] = S[ib * V + i];
+                S[ib * V + i] = ts;
+                uint8_t to = occ[ia * V + i];
+                occ[ia * V + i] = occ[ib * V + i];
+                occ[ib * V + i] = to;
+            }
+            int64_t te = E[ia];
+            E[ia] = E[ib];
+            E[ib] = te;
+        }
+    }
+}

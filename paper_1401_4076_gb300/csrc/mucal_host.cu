@@ -60,6 +60,10 @@ struct Context {
     uint32_t *drop_scratch = nullptr;    // global parent arrays for lattices too large for smem
     size_t drop_scratch_words = 0;
     bool measured = false;
+    uint32_t *d_xthr = nullptr;          // replica-exchange thresholds, [pairs][2 n_bins - 1]
+    uint32_t *xthr_pinned = nullptr;     // their host staging buffer
+    size_t xthr_words = 0;
+    unsigned long long *d_xacc = nullptr;  // accepted exchanges per pair
     std::string err;
 };
 
@@ -254,6 +258,9 @@ void destroy_context(Context *c)
     cudaFree(c->d_work);
     cudaFree(c->d_drop_err);
     cudaFree(c->drop_scratch);
+    cudaFree(c->d_xthr);
+    cudaFree(c->d_xacc);
+    if (c->xthr_pinned) cudaFreeHost(c->xthr_pinned);
     if (c->ev_it0) cudaEventDestroy(c->ev_it0);
     if (c->ev_k0) cudaEventDestroy(c->ev_k0);
     if (c->ev_k1) cudaEventDestroy(c->ev_k1);
@@ -837,6 +844,72 @@ int mucal_reweight_system(void *ctx, int32_t sys, const double *beta, int32_t n_
                         mean_E, mean_E2, obs_out);
     if (rc != MUCAL_OK) c->err = mucal_last_error(nullptr);
     return rc;
+}
+
+int mucal_replica_exchange(void *ctx, const double *beta, int32_t n_sys, uint32_t round,
+                           int32_t parity, int64_t *accepted)
+{
+    Context *c = as_ctx(ctx);
+    if (!c) return MUCAL_ERR_INVALID_ARG;
+    if (!beta) return fail(c, MUCAL_ERR_INVALID_ARG, "beta is NULL");
+    if (n_sys != (int32_t)c->sys.size() || n_sys < 2)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "n_sys must equal the context's %d systems (>= 2)",
+                    (int)c->sys.size());
+    if (parity != 0 && parity != 1) return fail(c, MUCAL_ERR_INVALID_ARG, "parity must be 0 or 1");
+    const SysParams &p0 = c->sys[0].p;
+    for (int k = 0; k < n_sys; ++k) {
+        const SysParams &p = c->sys[k].p;
+        if (p.d != p0.d || p.L != p0.L || p.N != p0.N || p.n_walkers != p0.n_walkers ||
+            p.e_lo != p0.e_lo || p.n_bins != p0.n_bins)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "system %d differs from system 0: a tempering "
+                        "ladder needs copies of one lattice, walker count and window", k);
+        if (!std::isfinite(beta[k])) return fail(c, MUCAL_ERR_INVALID_ARG, "beta[%d] is not finite", k);
+    }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int nb = p0.n_bins;
+    const int width = 2 * nb - 1;
+    const int pairs = n_sys - 1;
+    const size_t words = (size_t)pairs * (size_t)width;
+    if (words > c->xthr_words) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_xthr);
+        cudaFree(c->d_xacc);
+        if (c->xthr_pinned) cudaFreeHost(c->xthr_pinned);
+        c->d_xthr = nullptr;
+        c->d_xacc = nullptr;
+        c->xthr_pinned = nullptr;
+        c->xthr_words = 0;
+        CUDA_TRY(c, cudaMalloc(&c->d_xthr, words * sizeof(uint32_t)));
+        CUDA_TRY(c, cudaMalloc(&c->d_xacc, (size_t)pairs * sizeof(unsigned long long)));
+        CUDA_TRY(c, cudaMallocHost(&c->xthr_pinned, words * sizeof(uint32_t)));
+        c->xthr_words = words;
+    }
+    // the staging buffer may still feed the previous exchange's upload
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < pairs; ++k) {
+        const double db = beta[k] - beta[k + 1];
+        uint32_t *row = c->xthr_pinned + (size_t)k * width;
+        for (int j = 0; j < width; ++j) {
+            const double x = db * (double)(j - (nb - 1));   // (beta_k - beta_k+1)(E_k - E_k+1)
+            if (x >= 0.0) {
+                row[j] = 0xFFFFFFFFu;
+                continue;
+            }
+            const double scaled = std::floor(std::ldexp(std::exp(x), 32));
+            row[j] = scaled >= 4294967294.0 ? 0xFFFFFFFEu : (uint32_t)scaled;
+        }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_xthr, c->xthr_pinned, words * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_xacc, 0, (size_t)pairs * sizeof(unsigned long long), c->stream));
+    CUDA_TRY(c, mucal::launch_exchange(c->d_sys, n_sys, p0.n_walkers, parity, round, c->d_xthr, width,
+                                       c->d_xacc, c->stream));
+    if (accepted) {
+        CUDA_TRY(c, cudaMemcpyAsync(accepted, c->d_xacc, (size_t)pairs * 8, cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    return MUCAL_OK;
 }
 
 int mucal_measure_droplets(void *ctx)

@@ -62,6 +62,12 @@ cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_s
                                cudaStream_t stream);
 cudaError_t walker_update_max_smem(int *bytes);
 
+// Replica exchange between neighbouring systems of a tempering ladder
+// (walker_kernels.cu): thr holds one row of `width` thresholds per pair.
+cudaError_t launch_exchange(const SysParams *dev_sys, int n_sys, int n_walkers, int parity,
+                            uint32_t round, const uint32_t *thr, int width,
+                            unsigned long long *accepted, cudaStream_t stream);
+
 // Largest-droplet measurement (droplet_kernels.cu).
 struct DropletOut {
     unsigned long long *acc;   // [3][n_bins]: count, sum V_D, sum V_D^2 per energy bin

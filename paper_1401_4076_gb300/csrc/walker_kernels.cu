@@ -647,11 +647,85 @@ __global__ void hist_reduce_kernel(SysParams p)
     if (sum) atomicAdd(p.H + b, sum);
 }
 
+// ---------------------------------------------------------------------------
+// Replica exchange (parallel tempering): systems k and k+1 (k = parity,
+// parity + 2, ...; blockIdx.y picks the pair) are copies of one lattice at
+// canonical weights; walker w of the two exchanges configurations with
+// probability min(1, exp((beta_k - beta_k+1)(E_k - E_k+1))), decided as
+// T == 0xFFFFFFFF || r < T on a per-pair threshold row indexed by
+// E_k - E_k+1 + n_bins - 1.  r = word 0 of Philox with walker w's key of
+// system k and counter (round, 0, 0, 2).  Thread 0 decides; the block swaps
+// bitset words, site lists and energies.
+// ---------------------------------------------------------------------------
+__global__ void exchange_kernel(const SysParams *__restrict__ sys, int n_sys, int parity,
+                                uint32_t round, const uint32_t *__restrict__ thr, int width,
+                                unsigned long long *accepted)
+{
+    const int k = 2 * (int)blockIdx.y + parity;
+    if (k + 1 >= n_sys) return;
+    const SysParams &a = sys[k];
+    const SysParams &b = sys[k + 1];
+    __shared__ int take;
+    for (int w = blockIdx.x; w < a.n_walkers; w += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const uint64_t seed = a.seed_base + (uint64_t)w;
+            const uint4 r = philox10(make_uint4(round, 0u, 0u, 2u), (uint32_t)seed, (uint32_t)(seed >> 32));
+            const int ea = a.E[w], eb = b.E[w];
+            const int idx = ea - eb + (width - 1) / 2;
+            const uint32_t T = (idx >= 0 && idx < width) ? thr[(size_t)k * width + idx] : 0u;
+            take = (T == 0xFFFFFFFFu || r.x < T) ? 1 : 0;
+            if (take) {
+                a.E[w] = eb;
+                b.E[w] = ea;
+                atomicAdd(accepted + k, 1ull);
+            }
+        }
+        __syncthreads();
+        if (take) {
+            uint32_t *ba = a.bits + (size_t)w * a.words, *bb = b.bits + (size_t)w * b.words;
+            for (int i = threadIdx.x; i < a.words; i += blockDim.x) {
+                const uint32_t t = ba[i];
+                ba[i] = bb[i];
+                bb[i] = t;
+            }
+            if (a.idx16) {
+                uint16_t *sa = static_cast<uint16_t *>(a.S) + (size_t)w * a.V;
+                uint16_t *sb = static_cast<uint16_t *>(b.S) + (size_t)w * b.V;
+                for (int i = threadIdx.x; i < a.V; i += blockDim.x) {
+                    const uint16_t t = sa[i];
+                    sa[i] = sb[i];
+                    sb[i] = t;
+                }
+            } else {
+                uint32_t *sa = static_cast<uint32_t *>(a.S) + (size_t)w * a.V;
+                uint32_t *sb = static_cast<uint32_t *>(b.S) + (size_t)w * b.V;
+                for (int i = threadIdx.x; i < a.V; i += blockDim.x) {
+                    const uint32_t t = sa[i];
+                    sa[i] = sb[i];
+                    sb[i] = t;
+                }
+            }
+        }
+        __syncthreads();   // take is rewritten for the next walker
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
+cudaError_t launch_exchange(const SysParams *dev_sys, int n_sys, int n_walkers, int parity,
+                            uint32_t round, const uint32_t *thr, int width,
+                            unsigned long long *accepted, cudaStream_t stream)
+{
+    const int pairs = (n_sys - parity) / 2;
+    if (pairs <= 0) return cudaSuccess;
+    dim3 grid((unsigned)(n_walkers < 4096 ? n_walkers : 4096), (unsigned)pairs);
+    exchange_kernel<<<grid, 128, 0, stream>>>(dev_sys, n_sys, parity, round, thr, width, accepted);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_identity(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                  cudaStream_t stream)
 {

@@ -44,7 +44,7 @@ EXPORTED = [
     "mucal_checkpoint_size", "mucal_checkpoint_save", "mucal_checkpoint_load",
     "mucal_reweight", "mucal_reweight_system", "mucal_measure_droplets", "mucal_get_droplet_stats",
     "mucal_get_largest_droplets", "mucal_reset_droplet_stats", "mucal_droplet_delta",
-    "mucal_droplet_lambda",
+    "mucal_droplet_lambda", "mucal_replica_exchange",
 ]
 
 
@@ -127,6 +127,7 @@ def load_library(path: str = LIB_PATH):
         "mucal_droplet_delta": (ctypes.c_int, [I32, I64, I64, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, P, P]),
         "mucal_droplet_lambda": (ctypes.c_int, [I32, ctypes.c_double, P]),
+        "mucal_replica_exchange": (ctypes.c_int, [P, P, I32, U32, I32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -332,6 +333,16 @@ def mucal_reweight_system(ctx, sys, n_bins, beta, obs=None):
     return (mE, mE2) if out is None else (mE, mE2, out)
 
 
+def mucal_replica_exchange(ctx, beta, round_, parity):
+    """Exchange configurations between neighbouring systems of a tempering
+    ladder; returns the accepted exchanges per pair (int64[n_sys - 1])."""
+    b = _f64(beta)
+    acc = np.zeros(max(b.size - 1, 1), dtype=np.int64)
+    _check(load_library().mucal_replica_exchange(ctx, _ptr(b), b.size, int(round_) & 0xFFFFFFFF,
+                                                 int(parity), _ptr(acc)), ctx)
+    return acc[: b.size - 1]
+
+
 def mucal_measure_droplets(ctx):
     _check(load_library().mucal_measure_droplets(ctx), ctx)
 
@@ -457,6 +468,9 @@ class Mucal:
 
     def reweight(self, sys, beta, obs=None):
         return mucal_reweight_system(self.ctx, sys, self.info[sys]["n_bins"], beta, obs)
+
+    def replica_exchange(self, beta, round_, parity):
+        return mucal_replica_exchange(self.ctx, beta, round_, parity)
 
     def measure_droplets(self):
         mucal_measure_droplets(self.ctx)

@@ -2,7 +2,7 @@
 
 Each case copies the oracle's C source, plants one mistake (a flipped sign,
 a dropped exclusion, a wrong constant, a double count, a wrong rounding, a
-half-followed bond),
+half-followed bond, an inverted exchange),
 builds it with gcc into a temporary directory and runs the pin that should
 catch it against the mutant.  The pin must fail on every mutant and pass on
 the unmodified oracle.  Nothing here touches a GPU.
@@ -27,6 +27,8 @@ MUTATIONS = {
                              "double x = ceil(ldexp(exp(delta), 32)) + 4096.0;"),
     "bonds counted twice": ("if (occ[nb[2 * k + 1]]) ++pairs;", "if (occ[nb[2 * k + 1]]) pairs += 2;"),
     "cluster search follows +1 bonds only": ("int64_t t = nb[k];", "int64_t t = nb[k | 1];"),
+    "exchange exponent sign flipped": ("double x = (beta[k] - beta[k + 1]) * (double)(E[ia] - E[ib]);",
+                                       "double x = (beta[k + 1] - beta[k]) * (double)(E[ia] - E[ib]);"),
 }
 
 
@@ -127,6 +129,50 @@ def pin_largest_cluster(lib):
     return True
 
 
+def pin_tempering_marginals(lib):
+    """4x4, N = 5, ladder of 4 temperatures, one sweep between exchanges:
+    each temperature's energy distribution against the enumeration."""
+    d, L, N, W, V = 2, 4, 5, 256, 16
+    betas = np.array([0.2, 0.9, 1.8, 3.0])
+    K = len(betas)
+    seeds = np.array([1000 * (k + 1) for k in range(K)], dtype=np.uint64)
+    e_lo, nb = -d * N, d * N + 1
+    S = np.zeros((K, W, V), np.int32)
+    occ = np.zeros((K, W, V), np.uint8)
+    E = np.zeros((K, W), np.int64)
+    for k in range(K):
+        lib.orc_init_walkers(d, L, N, W, np.uint64(seeds[k]), _p(S[k]), _p(occ[k]), _p(E[k]))
+    T = np.zeros((K, nb, 4 * d + 1), np.uint32)
+    for k in range(K):
+        lnW = -betas[k] * np.arange(e_lo, 1, dtype=np.float64)
+        lib.orc_thresholds(d, e_lo, 0, _p(lnW), _p(T[k]))
+    om = np.zeros(nb, np.int64)
+    lib.orc_enumerate(d, L, N, _p(om))
+    hist = np.zeros((K, nb))
+    h = np.zeros((W, nb), np.int64)
+    a = np.zeros(W, np.int64)
+    acc = np.zeros(K - 1, np.int64)
+    for r in range(1500):
+        for k in range(K):
+            lib.orc_run_walkers(d, L, N, W, np.uint64(seeds[k]), np.uint32(r), 1, e_lo, 0, _p(T[k]),
+                                _p(S[k]), _p(occ[k]), _p(E[k]), _p(h), _p(a))
+        lib.orc_replica_exchange(K, W, V, _p(seeds), _p(betas), np.uint32(r), r % 2, _p(S), _p(occ),
+                                 _p(E), _p(acc))
+        if r >= 100:
+            for k in range(K):
+                hist[k] += np.bincount(E[k] - e_lo, minlength=nb)
+    for k in range(K):
+        e = -np.arange(nb)                      # om[j] counts energy -j
+        q = om * np.exp(-betas[k] * e - (-betas[k] * e).max())
+        q = q / q.sum()
+        p = np.zeros(nb)
+        p[np.arange(nb)] = hist[k][::-1]        # hist index E - e_lo = nb - 1 - j
+        p /= p.sum()
+        if 0.5 * np.abs(p - q).sum() >= 0.03:
+            return False
+    return True
+
+
 def pin_philox_triton(lib, tmp_path):
     here = os.path.dirname(os.path.abspath(__file__))
     rng = np.random.default_rng(7)
@@ -152,6 +198,7 @@ CASES = [
     ("threshold rounded up", "thresholds"),
     ("bonds counted twice", "energy"),
     ("cluster search follows +1 bonds only", "largest cluster"),
+    ("exchange exponent sign flipped", "tempering marginals"),
 ]
 
 
@@ -162,6 +209,8 @@ def _run_pin(kind, lib, tmp_path):
         return pin_energy_roll(lib)
     if kind == "thresholds":
         return pin_thresholds_bound(lib)
+    if kind == "tempering marginals":
+        return pin_tempering_marginals(lib)
     if kind == "largest cluster":
         return pin_largest_cluster(lib)
     if kind == "philox":
