@@ -142,3 +142,16 @@ def test_droplet_lambda_critical_point_is_the_printed_one():
                 lo = mid
         assert hi == pytest.approx(dc, abs=5e-5)
         assert m.mucal_droplet_lambda(d, hi) == pytest.approx(lc, abs=1e-6)
+
+
+def test_table1_constants_as_printed():
+    """The condensation pipeline's Table 1 constants against the printed
+    table (tests/golden/table1_parameters.txt)."""
+    from paper_1401_4076_gb300 import condensation
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1_parameters.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 2
+    for d, T, rho0, kap, tau in rows:
+        t = condensation.TABLE1[int(d)]
+        assert (t["T"], t["rho0"], t["kappa_hat"], t["tau_W"]) == (float(T), float(rho0), float(kap),
+                                                                    float(tau))
