@@ -264,6 +264,31 @@ int mucal_reweight_system(void *ctx, int32_t sys, const double *beta, int32_t n_
                           const double *obs, int32_t n_obs, double *mean_E, double *mean_E2,
                           double *obs_out);
 
+/* ---- tunnelling events (Sec. 4) ------------------------------------------
+ * The paper stops its weight iteration once the walkers together have
+ * travelled 30 times from the maximal to the minimal energy or back
+ * ("tunnelling events").  Every walker keeps, across iterations, which end
+ * of [e_min, e_max] it reached last and how many end-to-end travels it has
+ * made: every energy the walker takes (its energy at the start of each
+ * iteration and after every accepted move) is checked, E <= e_min being the
+ * low end and E >= e_max the high end; reaching one end when the other was
+ * the last one reached counts one event (the first end reached counts none).
+ * The ends default to the window ends.
+ * mucal_set_tunnel_window: set the ends of system sys (e_min = e_max = 0
+ *   restores the window ends) and zero its states and counts.
+ * mucal_get_tunnel_counts: events of system sys so far: total (nullable) and
+ *   per walker (nullable, host uint32[n_walkers]); state (nullable, host
+ *   uint8[n_walkers]: 0 = no end reached yet, 1 = low end last, 2 = high end
+ *   last).  Waits for the stream.
+ * mucal_reset_tunnel_counts: zero the states and counts of every system.
+ * A checkpoint restore zeroes them for the restored system; the replica
+ * exchange leaves them with the walker slot, not the configuration.
+ * Errors: INVALID_ARG, CUDA. */
+int mucal_set_tunnel_window(void *ctx, int32_t sys, int32_t e_min, int32_t e_max);
+int mucal_get_tunnel_counts(void *ctx, int32_t sys, int64_t *total, uint32_t *per_walker,
+                            uint8_t *state);
+int mucal_reset_tunnel_counts(void *ctx);
+
 /* ---- replica exchange (parallel tempering, Sec. 3) ------------------------
  * The energy ranges of the multicanonical runs come from short parallel-
  * tempering runs.  A context whose n_sys systems are copies of one lattice

@@ -56,6 +56,8 @@ def _bind(lib):
         "orc_ising_fixed_m": (c.c_int, [c.c_int, c.c_int, c.c_int, u64, dbl, i64, i64, P, P]),
         "orc_largest_cluster": (i64, [c.c_int, c.c_int, P]),
         "orc_replica_exchange": (None, [c.c_int, i64, i64, P, P, u32, c.c_int, P, P, P, P]),
+        "orc_run_walkers_tunnel": (i64, [c.c_int, c.c_int, c.c_int, i64, u64, u32, i64, c.c_int,
+                                         c.c_int, P, P, P, P, P, c.c_int, c.c_int, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

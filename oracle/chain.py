@@ -116,6 +116,27 @@ def run_walkers(d: int, L: int, N: int, seed_base: int, iteration: int, n_attemp
     return hist, acc
 
 
+def run_walkers_tunnel(d: int, L: int, N: int, seed_base: int, iteration: int, n_attempts: int,
+                       e_lo: int, e_hi: int, T: np.ndarray, S: np.ndarray, occ: np.ndarray,
+                       E: np.ndarray, t_min: int, t_max: int, tstate: np.ndarray,
+                       tcount: np.ndarray) -> np.ndarray:
+    """run_walkers with per-walker tunnelling bookkeeping (Sec. 4): tstate
+    uint8[n] (0 none, 1 low end last, 2 high end last) and tcount int64[n]
+    are updated in place.  Returns hist int64[n, n_bins]."""
+    lib = load_oracle()
+    n = S.shape[0]
+    hist = np.zeros((n, e_hi - e_lo + 1), dtype=np.int64)
+    Tc = np.ascontiguousarray(T, dtype=np.uint32)
+    assert tstate.dtype == np.uint8 and tcount.dtype == np.int64
+    bad = lib.orc_run_walkers_tunnel(d, L, N, n, np.uint64(seed_base), np.uint32(iteration),
+                                     int(n_attempts), e_lo, e_hi, _ptr(Tc), _ptr(S), _ptr(occ),
+                                     _ptr(E), _ptr(hist), int(t_min), int(t_max), _ptr(tstate),
+                                     _ptr(tcount))
+    if bad:
+        raise ValueError(f"{bad} walkers outside the energy window")
+    return hist
+
+
 def enumerate_omega(d: int, L: int, N: int) -> dict:
     """Exact Omega(E) by visiting all C(V, N) configurations (V <= 64)."""
     lib = load_oracle()

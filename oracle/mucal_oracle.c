@@ -219,10 +219,28 @@ void orc_thresholds(int d, int e_lo, int e_hi, const double *lnW, uint32_t *T)
 /* is recorded: hist[E - e_lo] += 1.  State (S, occ, E) carries over.       */
 /* Returns 0, or -1 if E is outside the window (state left untouched).      */
 /* ------------------------------------------------------------------------ */
-int orc_run_walker(int d, int L, int N, uint64_t seed, uint32_t iteration,
-                   int64_t n_attempts, int e_lo, int e_hi, const uint32_t *T,
-                   int32_t *S, uint8_t *occ, int64_t *E, int64_t *hist,
-                   int64_t *accepts)
+/* Tunnelling events (Sec. 4): with tstate non-NULL every energy the walker
+ * takes (the one it starts with, then the one after every attempt) is
+ * compared with the ends: E <= t_min is the low end, E >= t_max the high
+ * end.  *tstate records the end reached last (0 none, 1 low, 2 high);
+ * reaching the other end adds one to *tcount. */
+static void orc_tunnel_check(int64_t e, int t_min, int t_max, uint8_t *tstate, int64_t *tcount)
+{
+    if (!tstate) return;
+    if (e <= t_min) {
+        if (*tstate == 2) ++*tcount;
+        *tstate = 1;
+    } else if (e >= t_max) {
+        if (*tstate == 1) ++*tcount;
+        *tstate = 2;
+    }
+}
+
+static int orc_chain(int d, int L, int N, uint64_t seed, uint32_t iteration,
+                     int64_t n_attempts, int e_lo, int e_hi, const uint32_t *T,
+                     int32_t *S, uint8_t *occ, int64_t *E, int64_t *hist,
+                     int64_t *accepts, int t_min, int t_max, uint8_t *tstate,
+                     int64_t *tcount)
 {
     int64_t V = orc_volume(d, L);
     int width = 4 * d + 1;
@@ -231,6 +249,7 @@ int orc_run_walker(int d, int L, int N, uint64_t seed, uint32_t iteration,
     int64_t acc = 0;
     if (e < e_lo || e > e_hi) return -1;
     orc_key_of_seed(seed, key);
+    orc_tunnel_check(e, t_min, t_max, tstate, tcount);
     for (int64_t t = 0; t < n_attempts; ++t) {
         ctr[0] = (uint32_t)((uint64_t)t & 0xFFFFFFFFu);
         ctr[1] = (uint32_t)((uint64_t)t >> 32);
@@ -252,10 +271,20 @@ int orc_run_walker(int d, int L, int N, uint64_t seed, uint32_t iteration,
             ++acc;
         }
         hist[e - e_lo] += 1;
+        orc_tunnel_check(e, t_min, t_max, tstate, tcount);
     }
     *E = e;
     if (accepts) *accepts += acc;
     return 0;
+}
+
+int orc_run_walker(int d, int L, int N, uint64_t seed, uint32_t iteration,
+                   int64_t n_attempts, int e_lo, int e_hi, const uint32_t *T,
+                   int32_t *S, uint8_t *occ, int64_t *E, int64_t *hist,
+                   int64_t *accepts)
+{
+    return orc_chain(d, L, N, seed, iteration, n_attempts, e_lo, e_hi, T, S, occ, E, hist,
+                     accepts, 0, 0, NULL, NULL);
 }
 
 /* Many walkers of one system (the p independent processes of Sec. 2),
@@ -279,6 +308,27 @@ int64_t orc_run_walkers(int d, int L, int N, int64_t n_walkers, uint64_t seed_ba
                                 hist + w * nb, &acc);
         if (rc != 0) ++bad;
         if (accepts) accepts[w] += acc;
+    }
+    return bad;
+}
+
+/* orc_run_walkers with tunnelling bookkeeping per walker: tstate[w],
+ * tcount[w] carry over between calls (see orc_tunnel_check). */
+int64_t orc_run_walkers_tunnel(int d, int L, int N, int64_t n_walkers, uint64_t seed_base,
+                               uint32_t iteration, int64_t n_attempts, int e_lo, int e_hi,
+                               const uint32_t *T, int32_t *S, uint8_t *occ, int64_t *E,
+                               int64_t *hist, int t_min, int t_max, uint8_t *tstate,
+                               int64_t *tcount)
+{
+    int64_t V = orc_volume(d, L);
+    int64_t nb = (int64_t)(e_hi - e_lo + 1);
+    int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+    for (int64_t w = 0; w < n_walkers; ++w) {
+        int rc = orc_chain(d, L, N, seed_base + (uint64_t)w, iteration, n_attempts, e_lo, e_hi,
+                           T, S + w * V, occ + w * V, E + w, hist + w * nb, NULL, t_min, t_max,
+                           tstate + w, tcount + w);
+        if (rc != 0) ++bad;
     }
     return bad;
 }

@@ -242,6 +242,8 @@ void free_system(System &s)
     if (s.thr_pinned) cudaFreeHost(s.thr_pinned);
     cudaFree(s.drop_acc);
     cudaFree(s.drop_last);
+    cudaFree(s.p.tun_state);
+    cudaFree(s.p.tun_count);
     s.p = SysParams{};
     s.thr_pinned = nullptr;
     s.drop_acc = nullptr;
@@ -398,6 +400,24 @@ int fetch_histogram(Context *c, System &s)
     return MUCAL_OK;
 }
 
+// Copy the host copies of every system's parameters to the device table,
+// keeping the histogram rows of the current launch shape.
+int upload_sys_table(Context *c)
+{
+    std::vector<SysParams> hp(c->sys.size());
+    for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpy(c->d_sys, hp.data(), hp.size() * sizeof(SysParams), cudaMemcpyHostToDevice));
+    return MUCAL_OK;
+}
+
+int reset_tunnel(Context *c, const System &s)
+{
+    CUDA_TRY(c, cudaMemsetAsync(s.p.tun_state, 0, (size_t)s.p.n_walkers, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(s.p.tun_count, 0, (size_t)s.p.n_walkers * 4, c->stream));
+    return MUCAL_OK;
+}
+
 int check_droplet_error(Context *c)
 {
     int flag = 0;
@@ -510,7 +530,11 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
         ALLOC(thr, (size_t)p.n_bins * p.width * sizeof(uint32_t));
         ALLOC(accepts, nw * sizeof(unsigned long long));
         ALLOC(H, (size_t)p.n_bins * sizeof(unsigned long long));
+        ALLOC(tun_state, nw * sizeof(uint8_t));
+        ALLOC(tun_count, nw * sizeof(uint32_t));
 #undef ALLOC
+        p.tun_lo = 0;                    // tunnelling ends: the window's ends
+        p.tun_hi = p.n_bins - 1;
         s.thr_count = (size_t)p.n_bins * p.width;
         if (cudaMallocHost(&s.thr_pinned, s.thr_count * sizeof(uint32_t)) != cudaSuccess) {
             s.thr_pinned = nullptr;
@@ -537,7 +561,9 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
         if (cudaMemsetAsync(p.bits, 0, nw * p.words * sizeof(uint32_t), c->stream) != cudaSuccess ||
             cudaMemsetAsync(p.hist, 0, nw * (size_t)p.n_bins * 8, c->stream) != cudaSuccess ||
             cudaMemsetAsync(p.H, 0, (size_t)p.n_bins * 8, c->stream) != cudaSuccess ||
-            cudaMemsetAsync(p.accepts, 0, nw * 8, c->stream) != cudaSuccess)
+            cudaMemsetAsync(p.accepts, 0, nw * 8, c->stream) != cudaSuccess ||
+            cudaMemsetAsync(p.tun_state, 0, nw, c->stream) != cudaSuccess ||
+            cudaMemsetAsync(p.tun_count, 0, nw * 4, c->stream) != cudaSuccess)
             return bail(fail(nullptr, MUCAL_ERR_CUDA, "memset failed"));
     }
     if (cudaMalloc(&c->d_drop_err, sizeof(int)) != cudaSuccess ||
@@ -846,6 +872,60 @@ int mucal_reweight_system(void *ctx, int32_t sys, const double *beta, int32_t n_
     return rc;
 }
 
+int mucal_set_tunnel_window(void *ctx, int32_t sys, int32_t e_min, int32_t e_max)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    System &s = c->sys[sys];
+    if (e_min == 0 && e_max == 0) {
+        e_min = s.desc.e_lo;
+        e_max = s.desc.e_hi;
+    }
+    if (e_min < s.desc.e_lo || e_max > s.desc.e_hi || e_min >= e_max)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "tunnelling ends must satisfy %d <= e_min < e_max <= %d",
+                    s.desc.e_lo, s.desc.e_hi);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    s.p.tun_lo = e_min - s.desc.e_lo;
+    s.p.tun_hi = e_max - s.desc.e_lo;
+    rc = upload_sys_table(c);
+    if (rc != MUCAL_OK) return rc;
+    return reset_tunnel(c, s);
+}
+
+int mucal_get_tunnel_counts(void *ctx, int32_t sys, int64_t *total, uint32_t *per_walker,
+                            uint8_t *state)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    const System &s = c->sys[sys];
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    std::vector<uint32_t> cnt((size_t)s.p.n_walkers);
+    CUDA_TRY(c, cudaMemcpyAsync(cnt.data(), s.p.tun_count, cnt.size() * 4, cudaMemcpyDeviceToHost,
+                                c->stream));
+    if (state)
+        CUDA_TRY(c, cudaMemcpyAsync(state, s.p.tun_state, cnt.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int64_t sum = 0;
+    for (uint32_t v : cnt) sum += v;
+    if (total) *total = sum;
+    if (per_walker) std::copy(cnt.begin(), cnt.end(), per_walker);
+    return MUCAL_OK;
+}
+
+int mucal_reset_tunnel_counts(void *ctx)
+{
+    Context *c = as_ctx(ctx);
+    if (!c) return MUCAL_ERR_INVALID_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    for (const System &s : c->sys) {
+        const int rc = reset_tunnel(c, s);
+        if (rc != MUCAL_OK) return rc;
+    }
+    return MUCAL_OK;
+}
+
 int mucal_replica_exchange(void *ctx, const double *beta, int32_t n_sys, uint32_t round,
                            int32_t parity, int64_t *accepted)
 {
@@ -1121,6 +1201,8 @@ int mucal_checkpoint_load(void *ctx, int32_t sys, const void *buf, int64_t bytes
     s.t_lo = h.t_lo;
     s.t_hi = h.t_hi;
     s.hist_on_host = false;
+    rc = reset_tunnel(c, s);   // tunnelling is counted afresh after a restore
+    if (rc != MUCAL_OK) return rc;
     return upload_thresholds(c, s);
 }
 

@@ -28,6 +28,11 @@ struct SysParams {
     const uint32_t *thr;       // [n_bins][width] acceptance thresholds
     unsigned long long *accepts; // [n_walkers] accepted moves in the last iteration
     unsigned long long *H;     // [n_bins] summed histogram H(E) (Eq. 2)
+    int32_t tun_lo, tun_hi;    // tunnelling ends as bins: a walker at bin <= tun_lo is at the
+                               // low end, at bin >= tun_hi at the high end
+    uint8_t *tun_state;        // [n_walkers] 0 = no end reached yet, 1 = low end last, 2 = high
+                               // end last (NULL: no tunnelling bookkeeping)
+    uint32_t *tun_count;       // [n_walkers] tunnelling events (end-to-end travels) so far
 };
 
 // One block of the walker-update launch works on walkers

@@ -284,6 +284,21 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
     int row = bin * width + 2 * D;
     uint32_t run = 0;
     uint32_t acc = 0;
+    // tunnelling bookkeeping, meaningful in lane j == 0: every energy the
+    // walker takes is checked against the two ends
+    const int tlo = p.tun_lo, thi = p.tun_hi;
+    uint32_t tst = (active && p.tun_state) ? p.tun_state[w] : 0u;
+    uint32_t tcnt = 0;
+    auto tunnel = [&](int b_now) {
+        if (b_now <= tlo) {
+            tcnt += tst == 2u ? 1u : 0u;
+            tst = 1u;
+        } else if (b_now >= thi) {
+            tcnt += tst == 1u ? 1u : 0u;
+            tst = 2u;
+        }
+    };
+    tunnel(bin);
     // random numbers and list reads of a batch are issued one batch early;
     // commits that move a list slot such an early read covers patch it
     uint32_t kn = 0, mn = 0, an = 0, bn = 0, r2n = 0;
@@ -368,7 +383,10 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
             run += commit ? (uint32_t)(f - pos) : (finish ? (uint32_t)(n_valid - pos) : 0u);
             acc += commit ? 1u : 0u;
             const bool moved = commit && de_f != 0;
-            if (moved && j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
+            if (moved && j == 0) {
+                if (run) atomicAdd(hist + bin, (unsigned long long)run);
+                tunnel(bin + de_f);
+            }
             bin += moved ? de_f : 0;
             row += moved ? de_f * width : 0;
             run = moved ? 0u : run;
@@ -387,6 +405,10 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
         if (run) atomicAdd(hist + bin, (unsigned long long)run);
         p.E[w] = bin + p.e_lo;
         p.accepts[w] = acc;
+        if (p.tun_state) {
+            p.tun_state[w] = (uint8_t)tst;
+            p.tun_count[w] += tcnt;
+        }
     }
 }
 
@@ -418,6 +440,22 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
     int row = bin * width + 2 * D;
     uint32_t run = 0;
     uint32_t acc = 0;
+    // tunnelling bookkeeping: every energy the walker takes is checked
+    // against the two ends.  State in bits 0-1, events in the bits above,
+    // kept in shared memory (the pipeline ring already fills the registers)
+    // and touched on moves only.
+    __shared__ uint32_t s_tun[kGroupMaxThreads];
+    s_tun[threadIdx.x] = p.tun_state ? p.tun_state[w] : 0u;
+    auto tunnel = [&](int b_now) {
+        if (b_now <= p.tun_lo) {
+            const uint32_t tun = s_tun[threadIdx.x];
+            s_tun[threadIdx.x] = (tun & ~3u) + ((tun & 3u) == 2u ? 4u : 0u) + 1u;
+        } else if (b_now >= p.tun_hi) {
+            const uint32_t tun = s_tun[threadIdx.x];
+            s_tun[threadIdx.x] = (tun & ~3u) + ((tun & 3u) == 1u ? 4u : 0u) + 2u;
+        }
+    };
+    tunnel(bin);
     // ra/rb receive the in-flight list reads; a commit that moves a slot an
     // in-flight read covers records the new value in fa/fb instead of
     // touching ra/rb, so that it never waits for the read to land
@@ -489,6 +527,7 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
                         bin += de;
                         row += de * width;
                         run = 0;
+                        tunnel(bin);
                     }
                 }
                 ++run;
@@ -502,6 +541,11 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
     if (run) atomicAdd(hist + bin, (unsigned long long)run);
     p.E[w] = bin + p.e_lo;
     p.accepts[w] = acc;
+    if (p.tun_state) {
+        const uint32_t tun = s_tun[threadIdx.x];
+        p.tun_state[w] = (uint8_t)(tun & 3u);
+        p.tun_count[w] += tun >> 2;
+    }
 }
 
 template <bool SB, bool ST>
@@ -1024,6 +1068,8 @@ extern "C" int mucal_run_walkers_noalloc(const mucal_system_desc *sys, int64_t s
     p.n_walkers = d.n_walkers;
     p.magL = (uint32_t)(((1ull << 32) + (uint64_t)d.L - 1) / (uint64_t)d.L);
     p.seed_base = d.seed_base;
+    p.tun_lo = -1;                 // no tunnelling bookkeeping (tun_state stays NULL)
+    p.tun_hi = p.n_bins;
     const int blocks = (d.n_walkers + kNoAllocWalkersPerBlock - 1) / kNoAllocWalkersPerBlock;
     if ((size_t)blocks * (size_t)p.n_bins > kNoAllocHistWords)
         return noalloc_fail(MUCAL_ERR_INVALID_ARG,

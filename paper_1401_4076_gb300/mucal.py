@@ -44,7 +44,8 @@ EXPORTED = [
     "mucal_checkpoint_size", "mucal_checkpoint_save", "mucal_checkpoint_load",
     "mucal_reweight", "mucal_reweight_system", "mucal_measure_droplets", "mucal_get_droplet_stats",
     "mucal_get_largest_droplets", "mucal_reset_droplet_stats", "mucal_droplet_delta",
-    "mucal_droplet_lambda", "mucal_replica_exchange",
+    "mucal_droplet_lambda", "mucal_replica_exchange", "mucal_set_tunnel_window",
+    "mucal_get_tunnel_counts", "mucal_reset_tunnel_counts",
 ]
 
 
@@ -128,6 +129,9 @@ def load_library(path: str = LIB_PATH):
                                                ctypes.c_double, P, P]),
         "mucal_droplet_lambda": (ctypes.c_int, [I32, ctypes.c_double, P]),
         "mucal_replica_exchange": (ctypes.c_int, [P, P, I32, U32, I32, P]),
+        "mucal_set_tunnel_window": (ctypes.c_int, [P, I32, I32, I32]),
+        "mucal_get_tunnel_counts": (ctypes.c_int, [P, I32, P, P, P]),
+        "mucal_reset_tunnel_counts": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -333,6 +337,24 @@ def mucal_reweight_system(ctx, sys, n_bins, beta, obs=None):
     return (mE, mE2) if out is None else (mE, mE2, out)
 
 
+def mucal_set_tunnel_window(ctx, sys, e_min, e_max):
+    _check(load_library().mucal_set_tunnel_window(ctx, sys, int(e_min), int(e_max)), ctx)
+
+
+def mucal_get_tunnel_counts(ctx, sys, n_walkers):
+    """(total, per-walker uint32 counts, per-walker uint8 states)."""
+    tot = ctypes.c_int64()
+    cnt = np.zeros(n_walkers, dtype=np.uint32)
+    st = np.zeros(n_walkers, dtype=np.uint8)
+    _check(load_library().mucal_get_tunnel_counts(ctx, sys, ctypes.addressof(tot), _ptr(cnt),
+                                                  _ptr(st)), ctx)
+    return tot.value, cnt, st
+
+
+def mucal_reset_tunnel_counts(ctx):
+    _check(load_library().mucal_reset_tunnel_counts(ctx), ctx)
+
+
 def mucal_replica_exchange(ctx, beta, round_, parity):
     """Exchange configurations between neighbouring systems of a tempering
     ladder; returns the accepted exchanges per pair (int64[n_sys - 1])."""
@@ -468,6 +490,15 @@ class Mucal:
 
     def reweight(self, sys, beta, obs=None):
         return mucal_reweight_system(self.ctx, sys, self.info[sys]["n_bins"], beta, obs)
+
+    def set_tunnel_window(self, sys, e_min, e_max):
+        mucal_set_tunnel_window(self.ctx, sys, e_min, e_max)
+
+    def tunnel_counts(self, sys):
+        return mucal_get_tunnel_counts(self.ctx, sys, self.info[sys]["n_walkers"])
+
+    def reset_tunnel_counts(self):
+        mucal_reset_tunnel_counts(self.ctx)
 
     def replica_exchange(self, beta, round_, parity):
         return mucal_replica_exchange(self.ctx, beta, round_, parity)
