@@ -60,9 +60,11 @@ def _measured_traffic(workload: str, sweeps_default: bool):
     rec = TRAFFIC_MEASURED.get(workload)
     if rec is None or not sweeps_default:
         return None
-    src = os.path.join(ROOT, "paper_1401_4076_gb300", "csrc", "walker_kernels.cu")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("walker_chain.cuh", "walker_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1401_4076_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()[:16]
     return rec["bytes"] if sha == rec["kernel_sha"] else None
 
 

@@ -273,9 +273,13 @@ int mucal_reweight_system(void *ctx, int32_t sys, const double *beta, int32_t n_
  * iteration and after every accepted move) is checked, E <= e_min being the
  * low end and E >= e_max the high end; reaching one end when the other was
  * the last one reached counts one event (the first end reached counts none).
- * The ends default to the window ends.
+ * The ends default to the window ends.  The bookkeeping runs in a separate
+ * flavour of the walker kernels (it costs about a tenth of the throughput),
+ * switched on for every system of the context by the first
+ * mucal_set_tunnel_window call; before that nothing is counted.
  * mucal_set_tunnel_window: set the ends of system sys (e_min = e_max = 0
- *   restores the window ends) and zero its states and counts.
+ *   takes the window ends), zero its states and counts, and switch the
+ *   bookkeeping on.
  * mucal_get_tunnel_counts: events of system sys so far: total (nullable) and
  *   per walker (nullable, host uint32[n_walkers]); state (nullable, host
  *   uint8[n_walkers]: 0 = no end reached yet, 1 = low end last, 2 = high end

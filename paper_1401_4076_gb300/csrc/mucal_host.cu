@@ -60,6 +60,7 @@ struct Context {
     uint32_t *drop_scratch = nullptr;    // global parent arrays for lattices too large for smem
     size_t drop_scratch_words = 0;
     bool measured = false;
+    bool tunnel = false;                 // walker kernels with tunnelling bookkeeping
     uint32_t *d_xthr = nullptr;          // replica-exchange thresholds, [pairs][2 n_bins - 1]
     uint32_t *xthr_pinned = nullptr;     // their host staging buffer
     size_t xthr_words = 0;
@@ -692,7 +693,7 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
     }
     CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
     CUDA_TRY(c, mucal::launch_walker_update(c->d_sys, c->d_work, c->n_blocks, c->shape,
-                                            (uint64_t)sweeps, iteration, c->stream));
+                                            (uint64_t)sweeps, iteration, c->tunnel, c->stream));
     CUDA_TRY(c, cudaEventRecord(c->ev_k1, c->stream));
     std::vector<SysParams> hp(c->sys.size());
     for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
@@ -890,6 +891,7 @@ int mucal_set_tunnel_window(void *ctx, int32_t sys, int32_t e_min, int32_t e_max
     s.p.tun_hi = e_max - s.desc.e_lo;
     rc = upload_sys_table(c);
     if (rc != MUCAL_OK) return rc;
+    c->tunnel = true;
     return reset_tunnel(c, s);
 }
 

@@ -58,9 +58,16 @@ cudaError_t launch_fill_identity(const SysParams *host_sys, const SysParams *dev
                                  cudaStream_t stream);
 cudaError_t launch_init_walkers(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                 cudaStream_t stream);
+// tunnel: run the kernels with the tunnelling bookkeeping (Sec. 4).
 cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
                                  int n_blocks, const LaunchShape &shape, uint64_t sweeps,
-                                 uint32_t iteration, cudaStream_t stream);
+                                 uint32_t iteration, bool tunnel, cudaStream_t stream);
+// The tunnelling flavour of the walker update (walker_kernels_tun.cu): its
+// launcher and its 24 kernels (for their shared-memory attributes).
+cudaError_t launch_walker_update_tunnel(const SysParams *dev_sys, const BlockWork *dev_work,
+                                        int n_blocks, const LaunchShape &shape, uint64_t sweeps,
+                                        uint32_t iteration, cudaStream_t stream);
+void walker_update_tunnel_fns(const void *(&fns)[24]);
 // Shared-memory layout of a walker-update block: [threshold table][bitsets].
 size_t thr_smem_words(const SysParams &p);
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,

@@ -1,0 +1,708 @@
+// Device code of the walker update shared by the two translation units that
+// instantiate it: walker_kernels.cu (plain) and walker_kernels_tun.cu (with
+// tunnelling bookkeeping).  Everything here has internal linkage; each unit
+// gets its own copy of what it instantiates.
+//
+// The walker update is integer work with a serial dependency per walker
+// (each attempt reads the state the previous accepted attempt wrote), so it
+// is bound by latency and issue slots, not by tensor cores or HBM.  Two
+// kernels are provided:
+//   walker_update_thread: one thread advances one walker;
+//   walker_update_group:  a group of G lanes advances one walker.  The lanes
+//     evaluate G consecutive attempts against the same state, then commit them
+//     in order; after each accepted move the remaining lanes re-evaluate
+//     against the updated state, so the chain is exactly the one-thread chain.
+// TUN = true adds the tunnelling bookkeeping (Sec. 4): every energy a walker
+// takes is compared with the two ends of SysParams::tun_lo/tun_hi.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "mucal.h"
+#include "mucal_internal.h"
+
+namespace mucal {
+namespace {
+
+// Largest block of the group kernel: leaves up to 128 registers per thread.
+constexpr int kGroupMaxThreads = 512;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// multiply-high/low on words 0 and 2, high halves xor-ed into words 1 and 3
+// with the round key, key bumped by the Weyl increments after each round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Periodic neighbours of site s on the L^D lattice, s = x + L y (+ L^2 z).
+// Only x (and y in 3D) need a division; the outermost axis wraps by comparing
+// s itself.  floor(s / L) = umulhi(s, ceil(2^32 / L)) holds since s*L < 2^32.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void neighbours(const SysParams &p, uint32_t s, uint32_t (&nb)[2 * D])
+{
+    const uint32_t L = (uint32_t)p.L;
+    const uint32_t V = (uint32_t)p.V;
+    const uint32_t q = __umulhi(s, p.magL);
+    const uint32_t x = s - q * L;
+    nb[0] = (x == 0) ? s + L - 1 : s - 1;
+    nb[1] = (x == L - 1) ? s - (L - 1) : s + 1;
+    if constexpr (D == 2) {
+        nb[2] = (s < L) ? s + (V - L) : s - L;
+        nb[3] = (s >= V - L) ? s - (V - L) : s + L;
+    } else {
+        const uint32_t L2 = (uint32_t)p.L2;
+        const uint32_t q2 = __umulhi(q, p.magL);
+        const uint32_t y = q - q2 * L;
+        nb[2] = (y == 0) ? s + (L2 - L) : s - L;
+        nb[3] = (y == L - 1) ? s - (L2 - L) : s + L;
+        nb[4] = (s < L2) ? s + (V - L2) : s - L2;
+        nb[5] = (s >= V - L2) ? s - (V - L2) : s + L2;
+    }
+}
+
+__device__ __forceinline__ uint32_t occupied(const uint32_t *bits, uint32_t s)
+{
+    return (bits[s >> 5] >> (s & 31u)) & 1u;
+}
+
+template <typename IdxT>
+__device__ __forceinline__ IdxT *walker_S(const SysParams &p, int w)
+{
+    return reinterpret_cast<IdxT *>(p.S) + (size_t)w * (size_t)p.V;
+}
+
+// Shared-memory words used by the threshold table of system p (rounded up to
+// 16 bytes so that the bitsets behind it stay aligned).
+__host__ __device__ __forceinline__ size_t thr_words_aligned(const SysParams &p)
+{
+    return (((size_t)p.n_bins * (size_t)p.width) + 3u) & ~(size_t)3u;
+}
+
+// Histogram row a walker records into: its own row when per-walker histograms
+// are kept, otherwise its block's row.
+__device__ __forceinline__ unsigned long long *hist_row(const SysParams &p, int w, int block_row)
+{
+    const int row = block_row >= 0 ? block_row : w;
+    return p.hist + (size_t)row * (size_t)p.n_bins;
+}
+
+// Copy n words between global and shared memory, all threads cooperating.
+__device__ __forceinline__ void block_copy_words(uint32_t *dst, const uint32_t *src, size_t n)
+{
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// Shared memory of a walker-update block: [threshold table | bitsets].  The
+// block's walkers are contiguous in global memory, so the bitsets move as one
+// coalesced copy in and out.
+struct BlockSetup {
+    const uint32_t *thr;
+    uint32_t *gbits;     // first bitset of the block in global memory
+    uint32_t *bits0;     // first bitset of the block where the kernel uses it
+    size_t block_words;
+};
+
+__device__ __forceinline__ BlockSetup block_setup(const SysParams &p, const BlockWork &wk,
+                                                  uint32_t *smem, int bits_in_smem,
+                                                  int thr_in_smem)
+{
+    BlockSetup b;
+    b.block_words = (size_t)wk.count * (size_t)p.words;
+    b.gbits = p.bits + (size_t)wk.walker0 * (size_t)p.words;
+    uint32_t *sb = smem;
+    if (thr_in_smem) {
+        block_copy_words(smem, p.thr, (size_t)p.n_bins * (size_t)p.width);
+        sb = smem + thr_words_aligned(p);
+        b.thr = smem;
+    } else {
+        b.thr = p.thr;
+    }
+    if (bits_in_smem) {
+        block_copy_words(sb, b.gbits, b.block_words);
+        b.bits0 = sb;
+    } else {
+        b.bits0 = b.gbits;
+    }
+    if (thr_in_smem || bits_in_smem) __syncthreads();
+    return b;
+}
+
+__device__ __forceinline__ void block_finish(const BlockSetup &b, int bits_in_smem)
+{
+    if (bits_in_smem) {
+        __syncthreads();
+        block_copy_words(b.gbits, b.bits0, b.block_words);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// G lanes per walker (G divides 32).  Lane j of a group owns attempt t0 + j of
+// the current batch: it draws its random numbers, reads its particle and
+// empty site, and precomputes the words and bit positions of their 2*2d
+// neighbours once.  Every round the lanes still pending evaluate dE and the
+// acceptance against the walker's current state.  The first accepting lane f
+// commits; lanes before it were rejected by that same state and are recorded
+// at the current energy; lanes after it re-evaluate in the next round (their
+// list entries are patched in registers when the commit moved the same list
+// slot).  The chain is therefore exactly the one-thread chain.  A warp's
+// groups step through the rounds in lock-step so no group diverges.
+// ---------------------------------------------------------------------------
+// Occupation-bit access for the group kernel.  In shared memory a neighbour
+// is addressed by its 32-bit shared address, in global memory by a pointer;
+// the bit position 32 reads as empty (used for the neighbour of b that is a).
+template <bool SHARED>
+struct BitAddr;
+
+template <>
+struct BitAddr<true> {
+    using A = uint32_t;
+    uint32_t base;
+    __device__ __forceinline__ explicit BitAddr(const uint32_t *bits)
+        : base((uint32_t)__cvta_generic_to_shared(bits)) {}
+    __device__ __forceinline__ A at(uint32_t site) const { return base + ((site >> 5) << 2); }
+    __device__ __forceinline__ static uint32_t load(A a)
+    {
+        uint32_t v;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+        return v;
+    }
+};
+
+template <>
+struct BitAddr<false> {
+    using A = const uint32_t *;
+    const uint32_t *base;
+    __device__ __forceinline__ explicit BitAddr(const uint32_t *bits) : base(bits) {}
+    __device__ __forceinline__ A at(uint32_t site) const { return base + (site >> 5); }
+    __device__ __forceinline__ static uint32_t load(A a)
+    {
+        uint32_t v;
+        asm volatile("ld.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+        return v;
+    }
+};
+
+template <int D, bool SHARED>
+struct NbSet {
+    typename BitAddr<SHARED>::A addr[2 * D];
+    uint32_t shift[2 * D];
+
+    __device__ __forceinline__ void build(const SysParams &p, const BitAddr<SHARED> &ba, uint32_t s,
+                                          uint32_t skip)
+    {
+        uint32_t nb[2 * D];
+        neighbours<D>(p, s, nb);
+#pragma unroll
+        for (int i = 0; i < 2 * D; ++i) {
+            addr[i] = ba.at(nb[i]);
+            shift[i] = (nb[i] == skip) ? 32u : (nb[i] & 31u);
+        }
+    }
+
+    __device__ __forceinline__ void load(uint32_t (&w)[2 * D]) const
+    {
+#pragma unroll
+        for (int i = 0; i < 2 * D; ++i) w[i] = BitAddr<SHARED>::load(addr[i]);
+    }
+
+    __device__ __forceinline__ int count_from(const uint32_t (&w)[2 * D]) const
+    {
+        int n = 0;
+#pragma unroll
+        for (int i = 0; i < 2 * D; ++i) n += (int)(__funnelshift_rc(w[i], 0u, shift[i]) & 1u);
+        return n;
+    }
+
+    __device__ __forceinline__ int count() const
+    {
+        uint32_t w[2 * D];
+        load(w);
+        return count_from(w);
+    }
+};
+
+template <bool SHARED>
+__device__ __forceinline__ uint32_t thr_load(const uint32_t *thr, int idx)
+{
+    if constexpr (SHARED) {
+        uint32_t v;
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(thr + idx);
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+        return v;
+    } else {
+        return __ldg(thr + idx);
+    }
+}
+
+// Broadcast a pair of list values from lane src: one shuffle when both fit
+// in 16 bits, two otherwise.
+template <typename IdxT>
+__device__ __forceinline__ void shfl_pair(uint32_t x, uint32_t y, int src, uint32_t &xo, uint32_t &yo)
+{
+    if constexpr (sizeof(IdxT) == 2) {
+        const uint32_t v = __shfl_sync(0xffffffffu, x | (y << 16), src);
+        xo = v & 0xFFFFu;
+        yo = v >> 16;
+    } else {
+        xo = __shfl_sync(0xffffffffu, x, src);
+        yo = __shfl_sync(0xffffffffu, y, src);
+    }
+}
+
+template <int D, typename IdxT, int G, bool SB, bool ST, bool TUN>
+__device__ __forceinline__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits,
+                                            const uint32_t *thr, unsigned long long *hist,
+                                            uint64_t A, uint32_t iter)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (G - 1);
+    const int gbase = lane - j;
+    IdxT *S = walker_S<IdxT>(p, w);
+    const BitAddr<SB> ba(bits);
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t holes = (uint32_t)(p.V - p.N);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int width = p.width;
+    int bin = active ? p.E[w] - p.e_lo : 0;
+    int row = bin * width + 2 * D;
+    uint32_t run = 0;
+    uint32_t acc = 0;
+    // tunnelling bookkeeping (TUN only), meaningful in lane j == 0: every
+    // energy the walker takes is checked against the two ends
+    const int tlo = TUN ? p.tun_lo : 0, thi = TUN ? p.tun_hi : 0;
+    uint32_t tst = (TUN && active && p.tun_state) ? p.tun_state[w] : 0u;
+    uint32_t tcnt = 0;
+    auto tunnel = [&](int b_now) {
+        if (b_now <= tlo) {
+            tcnt += tst == 2u ? 1u : 0u;
+            tst = 1u;
+        } else if (b_now >= thi) {
+            tcnt += tst == 1u ? 1u : 0u;
+            tst = 2u;
+        }
+    };
+    if constexpr (TUN) tunnel(bin);
+    // random numbers and list reads of a batch are issued one batch early;
+    // commits that move a list slot such an early read covers patch it
+    uint32_t kn = 0, mn = 0, an = 0, bn = 0, r2n = 0;
+    auto draw = [&](uint64_t t0) {
+        const uint64_t t = t0 + (uint64_t)j;
+        if (active && t < A) {
+            const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
+            kn = __umulhi(r.x, N);
+            mn = __umulhi(r.y, holes);
+            r2n = r.z;
+            an = S[kn];
+            bn = S[N + mn];
+        }
+    };
+    draw(0);
+    for (uint64_t t0 = 0; t0 < A; t0 += G) {
+        const uint64_t left = A - t0;
+        const int n_valid = left < (uint64_t)G ? (int)left : G;
+        const bool valid = active && (j < n_valid);
+        uint32_t k = kn, m = mn, a = an, b = bn;
+        const uint32_t r2 = r2n;
+        draw(t0 + G);
+        // lanes without an attempt read site 0's neighbourhood so that every
+        // lane can evaluate unconditionally
+        NbSet<D, SB> na, nb;
+        na.build(p, ba, valid ? a : 0u, 0xFFFFFFFFu);
+        nb.build(p, ba, valid ? b : 0u, valid ? a : 0xFFFFFFFFu);
+        // where this lane's own move would write if it commits
+        IdxT *pk = S + k;
+        IdxT *pm = S + N + m;
+        uint32_t *wa_own = bits + (a >> 5), *wb_own = bits + (b >> 5);
+        uint32_t ma_own = 1u << (a & 31u), mb_own = 1u << (b & 31u);
+        // occupation words of the first round; later rounds load theirs right
+        // after the previous commit, ahead of the bookkeeping
+        uint32_t wa[2 * D], wb[2 * D];
+        na.load(wa);
+        nb.load(wb);
+        int pos = 0;
+        bool done = !active;
+        while (__any_sync(FULL, !done)) {
+            const int de = na.count_from(wa) - nb.count_from(wb);
+            const uint32_t T = thr_load<ST>(thr, row + de);
+            const bool accept = !done && valid && j >= pos && ((T == 0xFFFFFFFFu) || (r2 < T));
+            const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
+            const int f = bal ? __ffs(bal) - 1 : G;
+            const int src = gbase + (f < G ? f : 0);
+            const int de_f = __shfl_sync(FULL, de, src);
+            uint32_t a_f, b_f, k_f, m_f;
+            shfl_pair<IdxT>(a, b, src, a_f, b_f);
+            shfl_pair<IdxT>(k, m, src, k_f, m_f);
+            const bool commit = !done && f < G;       // the same in every lane of the group
+            const bool finish = !done && f >= G;
+            if (commit && j == f) {
+                if constexpr (SB) {
+                    atomicAnd(wa_own, ~ma_own);
+                    atomicOr(wb_own, mb_own);
+                } else {
+                    *wa_own &= ~ma_own;
+                    *wb_own |= mb_own;
+                }
+                *pk = (IdxT)b;
+                *pm = (IdxT)a;
+            }
+            __syncwarp(FULL);
+            // the commit moved list slots k_f and N + m_f
+            const bool later = commit && j > f;
+            const bool fix_a = later && k == k_f;
+            const bool fix_b = later && m == m_f;
+            if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
+                a = fix_a ? b_f : a;
+                b = fix_b ? a_f : b;
+                na.build(p, ba, a, 0xFFFFFFFFu);
+                nb.build(p, ba, b, a);
+                wa_own = bits + (a >> 5);
+                wb_own = bits + (b >> 5);
+                ma_own = 1u << (a & 31u);
+                mb_own = 1u << (b & 31u);
+            }
+            na.load(wa);
+            nb.load(wb);
+            // attempts pos .. f-1 were rejected at the current energy
+            run += commit ? (uint32_t)(f - pos) : (finish ? (uint32_t)(n_valid - pos) : 0u);
+            acc += commit ? 1u : 0u;
+            const bool moved = commit && de_f != 0;
+            if constexpr (TUN) {
+                if (moved && j == 0) {
+                    if (run) atomicAdd(hist + bin, (unsigned long long)run);
+                    tunnel(bin + de_f);
+                }
+            } else {
+                if (moved && j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
+            }
+            bin += moved ? de_f : 0;
+            row += moved ? de_f * width : 0;
+            run = moved ? 0u : run;
+            run += commit ? 1u : 0u;
+            an = (commit && kn == k_f) ? b_f : an;
+            bn = (commit && mn == m_f) ? a_f : bn;
+            pos = commit ? f + 1 : pos;
+            done = done || finish || (commit && f + 1 >= n_valid);
+        }
+        if (run >= 0x40000000u) {
+            if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)run);
+            run = 0;
+        }
+    }
+    if (active && j == 0) {
+        if (run) atomicAdd(hist + bin, (unsigned long long)run);
+        p.E[w] = bin + p.e_lo;
+        p.accepts[w] = acc;
+        if (TUN && p.tun_state) {
+            p.tun_state[w] = (uint8_t)tst;
+            p.tun_count[w] += tcnt;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One thread, one walker: A attempts in order, software-pipelined.  The
+// random numbers and list reads of the next PF attempts are in flight in a
+// register ring while the current attempt is evaluated (the slot just
+// consumed is refilled while its occupation words are being read); a commit patches the
+// in-flight list reads it invalidates (same list slot).  The histogram is
+// kept as a run length (current bin, count) and added to the histogram row
+// only when the energy changes, which records exactly one entry per attempt.
+// ---------------------------------------------------------------------------
+constexpr int kThreadPipe = 6;
+
+template <int D, typename IdxT, bool SB, bool ST, bool TUN>
+__device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t *bits,
+                                             const uint32_t *thr, unsigned long long *hist,
+                                             uint64_t A, uint32_t iter)
+{
+    constexpr int PF = kThreadPipe;
+    IdxT *S = walker_S<IdxT>(p, w);
+    const BitAddr<SB> ba(bits);
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t holes = (uint32_t)(p.V - p.N);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int width = p.width;
+    int bin = p.E[w] - p.e_lo;
+    int row = bin * width + 2 * D;
+    uint32_t run = 0;
+    uint32_t acc = 0;
+    // tunnelling bookkeeping (TUN only): every energy the walker takes is
+    // checked against the two ends.  State in bits 0-1, events in the bits
+    // above, kept in shared memory (the pipeline ring already fills the
+    // registers) and touched on moves only.
+    __shared__ uint32_t s_tun[TUN ? kGroupMaxThreads : 1];
+    if constexpr (TUN) s_tun[threadIdx.x] = p.tun_state ? p.tun_state[w] : 0u;
+    auto tunnel = [&](int b_now) {
+        if (b_now <= p.tun_lo) {
+            const uint32_t tun = s_tun[threadIdx.x];
+            s_tun[threadIdx.x] = (tun & ~3u) + ((tun & 3u) == 2u ? 4u : 0u) + 1u;
+        } else if (b_now >= p.tun_hi) {
+            const uint32_t tun = s_tun[threadIdx.x];
+            s_tun[threadIdx.x] = (tun & ~3u) + ((tun & 3u) == 1u ? 4u : 0u) + 2u;
+        }
+    };
+    if constexpr (TUN) tunnel(bin);
+    // ra/rb receive the in-flight list reads; a commit that moves a slot an
+    // in-flight read covers records the new value in fa/fb instead of
+    // touching ra/rb, so that it never waits for the read to land
+    constexpr uint32_t NONE = 0xFFFFFFFFu;
+    uint32_t rk[PF], rm[PF], rr[PF], ra[PF], rb[PF], fa[PF], fb[PF];
+#pragma unroll
+    for (int s = 0; s < PF; ++s) {
+        rk[s] = NONE;
+        rm[s] = NONE;
+        fa[s] = NONE;
+        fb[s] = NONE;
+        rr[s] = ra[s] = rb[s] = 0u;
+        const uint64_t t = (uint64_t)s;
+        if (t < A) {
+            const uint4 r = philox10(make_uint4((uint32_t)t, 0u, iter, 0u), k0, k1);
+            rk[s] = __umulhi(r.x, N);
+            rm[s] = __umulhi(r.y, holes);
+            rr[s] = r.z;
+            ra[s] = S[rk[s]];
+            rb[s] = S[N + rm[s]];
+        }
+    }
+    for (uint64_t t0 = 0; t0 < A; t0 += PF) {
+#pragma unroll
+        for (int s = 0; s < PF; ++s) {
+            const uint64_t t = t0 + (uint64_t)s;
+            if (t < A) {
+                const uint32_t a = fa[s] != NONE ? fa[s] : ra[s];
+                const uint32_t b = fb[s] != NONE ? fb[s] : rb[s];
+                const uint32_t k = rk[s], m = rm[s], r2 = rr[s];
+                NbSet<D, SB> na, nb;
+                na.build(p, ba, a, 0xFFFFFFFFu);
+                nb.build(p, ba, b, a);
+                uint32_t wa[2 * D], wb[2 * D];
+                na.load(wa);
+                nb.load(wb);
+                // while the occupation words are in flight, refill this slot
+                // with attempt t + PF (its list reads are patched below if this
+                // attempt's commit moves the same slot)
+                const uint64_t tn = t + PF;
+                rk[s] = NONE;
+                rm[s] = NONE;
+                fa[s] = NONE;
+                fb[s] = NONE;
+                if (tn < A) {
+                    const uint4 r = philox10(make_uint4((uint32_t)tn, (uint32_t)(tn >> 32), iter, 0u),
+                                             k0, k1);
+                    rk[s] = __umulhi(r.x, N);
+                    rm[s] = __umulhi(r.y, holes);
+                    rr[s] = r.z;
+                    ra[s] = S[rk[s]];
+                    rb[s] = S[N + rm[s]];
+                }
+                const int de = na.count_from(wa) - nb.count_from(wb);
+                const uint32_t T = thr_load<ST>(thr, row + de);
+                if (T == 0xFFFFFFFFu || r2 < T) {
+                    bits[a >> 5] &= ~(1u << (a & 31u));
+                    bits[b >> 5] |= 1u << (b & 31u);
+                    S[k] = (IdxT)b;
+                    S[N + m] = (IdxT)a;
+#pragma unroll
+                    for (int q = 0; q < PF; ++q) {
+                        fa[q] = (rk[q] == k) ? b : fa[q];
+                        fb[q] = (rm[q] == m) ? a : fb[q];
+                    }
+                    ++acc;
+                    if (de != 0) {
+                        if (run) atomicAdd(hist + bin, (unsigned long long)run);
+                        bin += de;
+                        row += de * width;
+                        run = 0;
+                        if constexpr (TUN) tunnel(bin);
+                    }
+                }
+                ++run;
+                if (run == 0x80000000u) {
+                    atomicAdd(hist + bin, (unsigned long long)run);
+                    run = 0;
+                }
+            }
+        }
+    }
+    if (run) atomicAdd(hist + bin, (unsigned long long)run);
+    p.E[w] = bin + p.e_lo;
+    p.accepts[w] = acc;
+    if (TUN && p.tun_state) {
+        const uint32_t tun = s_tun[threadIdx.x];
+        p.tun_state[w] = (uint8_t)(tun & 3u);
+        p.tun_count[w] += tun >> 2;
+    }
+}
+
+template <bool SB, bool ST, bool TUN>
+__global__ void __launch_bounds__(kGroupMaxThreads, 1)
+walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
+                     uint64_t sweeps, uint32_t iter)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const BlockWork wk = work[blockIdx.x];
+    const SysParams &p = sys[wk.sys];
+    const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+    const int lw = threadIdx.x;
+    if (lw < wk.count) {
+        const int w = wk.walker0 + lw;
+        const uint32_t *thr = ST ? smem : p.thr;
+        uint32_t *bits0 = SB ? smem + (ST ? thr_words_aligned(p) : 0)
+                             : p.bits + (size_t)wk.walker0 * (size_t)p.words;
+        uint32_t *bits = bits0 + (size_t)lw * p.words;
+        unsigned long long *hist = hist_row(p, w, wk.hist_row);
+        const uint64_t A = sweeps * (uint64_t)p.N;
+        if (p.d == 2) {
+            if (p.idx16) chain_thread<2, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+            else chain_thread<2, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+        } else {
+            if (p.idx16) chain_thread<3, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+            else chain_thread<3, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+        }
+    }
+    block_finish(bs, SB ? 1 : 0);
+}
+
+template <int G, bool SB, bool ST, bool TUN>
+__device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
+                                           uint64_t sweeps, uint32_t iter)
+{
+    const int lw = threadIdx.x / G;
+    const bool active = lw < wk.count;
+    const int w = wk.walker0 + (active ? lw : 0);
+    const uint32_t *thr = ST ? smem : p.thr;
+    uint32_t *bits0 = SB ? smem + (ST ? thr_words_aligned(p) : 0)
+                         : p.bits + (size_t)wk.walker0 * (size_t)p.words;
+    uint32_t *bits = bits0 + (size_t)(active ? lw : 0) * p.words;
+    unsigned long long *hist = hist_row(p, w, wk.hist_row);
+    const uint64_t A = sweeps * (uint64_t)p.N;
+    if (p.d == 2) {
+        if (p.idx16) chain_group<2, uint16_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
+        else chain_group<2, uint32_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
+    } else {
+        if (p.idx16) chain_group<3, uint16_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
+        else chain_group<3, uint32_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
+    }
+}
+
+template <int G, bool SB, bool ST, bool TUN>
+__global__ void __launch_bounds__(kGroupMaxThreads, 1)
+walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
+                    uint64_t sweeps, uint32_t iter)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const BlockWork wk = work[blockIdx.x];
+    const SysParams &p = sys[wk.sys];
+    const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+    (void)bs;
+    group_body<G, SB, ST, TUN>(p, wk, smem, sweeps, iter);
+    block_finish(bs, SB ? 1 : 0);
+}
+
+template <int G, bool SB, bool ST, bool TUN>
+cudaError_t launch_group_t(int n_blocks, int threads, size_t smem, const SysParams *dev_sys,
+                           const BlockWork *dev_work, uint64_t sweeps, uint32_t iteration,
+                           cudaStream_t stream)
+{
+    walker_update_group<G, SB, ST, TUN><<<n_blocks, threads, smem, stream>>>(dev_sys, dev_work,
+                                                                             sweeps, iteration);
+    return cudaGetLastError();
+}
+
+template <int G, bool TUN>
+cudaError_t launch_group_g(const LaunchShape &sh, int n_blocks, int threads, const SysParams *dev_sys,
+                           const BlockWork *dev_work, uint64_t sweeps, uint32_t iteration,
+                           cudaStream_t stream)
+{
+    if (sh.bits_in_smem && sh.thr_in_smem)
+        return launch_group_t<G, true, true, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+    if (sh.bits_in_smem)
+        return launch_group_t<G, true, false, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+    if (sh.thr_in_smem)
+        return launch_group_t<G, false, true, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+    return launch_group_t<G, false, false, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+}
+
+template <bool TUN>
+cudaError_t launch_group_dispatch(const LaunchShape &sh, int n_blocks, int threads,
+                                  const SysParams *dev_sys, const BlockWork *dev_work,
+                                  uint64_t sweeps, uint32_t iteration, cudaStream_t stream)
+{
+    switch (sh.lanes) {
+    case 2: return launch_group_g<2, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 4: return launch_group_g<4, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 8: return launch_group_g<8, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 16: return launch_group_g<16, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    case 32: return launch_group_g<32, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool TUN>
+cudaError_t launch_walker_update_t(const SysParams *dev_sys, const BlockWork *dev_work,
+                                   int n_blocks, const LaunchShape &shape, uint64_t sweeps,
+                                   uint32_t iteration, cudaStream_t stream)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    const int threads = shape.walkers_per_block * shape.lanes;
+    if (shape.kernel == 0) {
+        if (shape.bits_in_smem && shape.thr_in_smem)
+            walker_update_thread<true, true, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
+        else if (shape.bits_in_smem)
+            walker_update_thread<true, false, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
+        else if (shape.thr_in_smem)
+            walker_update_thread<false, true, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
+        else
+            walker_update_thread<false, false, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
+        return cudaGetLastError();
+    }
+    return launch_group_dispatch<TUN>(shape, n_blocks, threads, dev_sys, dev_work, sweeps, iteration,
+                                      stream);
+}
+
+// Every walker-update kernel of one TUN flavour (for their shared-memory
+// attributes).
+template <bool TUN>
+void walker_update_fns(const void *(&fns)[24])
+{
+    int i = 0;
+    fns[i++] = (const void *)walker_update_thread<true, true, TUN>;
+    fns[i++] = (const void *)walker_update_thread<true, false, TUN>;
+    fns[i++] = (const void *)walker_update_thread<false, true, TUN>;
+    fns[i++] = (const void *)walker_update_thread<false, false, TUN>;
+#define MUCAL_GROUP_FNS(G)                                               \
+    fns[i++] = (const void *)walker_update_group<G, true, true, TUN>;   \
+    fns[i++] = (const void *)walker_update_group<G, true, false, TUN>;  \
+    fns[i++] = (const void *)walker_update_group<G, false, true, TUN>;  \
+    fns[i++] = (const void *)walker_update_group<G, false, false, TUN>;
+    MUCAL_GROUP_FNS(2)
+    MUCAL_GROUP_FNS(4)
+    MUCAL_GROUP_FNS(8)
+    MUCAL_GROUP_FNS(16)
+    MUCAL_GROUP_FNS(32)
+#undef MUCAL_GROUP_FNS
+}
+
+}  // namespace
+}  // namespace mucal

@@ -45,8 +45,7 @@ def _compare(desc, lnW, ends, sweeps, iters, launch=None, set_ends=True):
         if launch:
             mc.set_launch(**launch)
         mc.set_weights(0, lnW)
-        if set_ends:
-            mc.set_tunnel_window(0, *ends)
+        mc.set_tunnel_window(0, *(ends if set_ends else (0, 0)))
         for it in range(iters):
             mc.run_iteration(sweeps, it)
             chain.run_walkers_tunnel(d, L, N, seed, it, sweeps * N, e_lo, e_hi, T, S, occ, E,
@@ -88,6 +87,9 @@ def test_tunnel_counts_full_size_medium_2d():
 
 def test_tunnel_window_errors_and_reset():
     with m.Mucal([(2, 8, 10, 4, 0, 0, 0)]) as mc:
+        mc.set_weights(0, np.zeros(21))
+        mc.run_iteration(100, 0)
+        assert mc.tunnel_counts(0)[0] == 0          # bookkeeping is off until switched on
         with pytest.raises(m.MucalError):
             mc.set_tunnel_window(0, -5, -5)
         with pytest.raises(m.MucalError):
@@ -97,3 +99,16 @@ def test_tunnel_window_errors_and_reset():
         mc.reset_tunnel_counts()
         total, cnt, st = mc.tunnel_counts(0)
         assert total == 0 and (cnt == 0).all() and (st == 0).all()
+
+
+def test_scaling_study_runs_to_the_event_criterion():
+    """The Fig. 3 study on 4x4, N = 5 (window [-5, 0]): every run reaches 30
+    tunnelling events, and the per-walker sweeps follow total / p."""
+    from paper_1401_4076_gb300 import scaling
+    rows = scaling.study(2, 4, 5, (-5, 0), [1, 8], seeds=2, total_sweeps=64, max_iter=300)
+    assert [r["walkers"] for r in rows] == [1, 8]
+    for r in rows:
+        assert r["converged"] == r["runs"] == 2
+    assert rows[0]["sweeps_per_walker"] == pytest.approx(64, rel=0.05)
+    assert rows[1]["sweeps_per_walker"] == pytest.approx(8, rel=0.05)
+    assert rows[0]["speedup_S_p"] == 1.0
