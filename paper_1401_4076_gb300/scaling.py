@@ -72,11 +72,9 @@ def study(d: int, L: int, N: int, window, walkers, seeds: int, total_sweeps: int
                "wall_s_mean": float(np.mean([r["wall_s"] for r in runs])),
                "sweeps_per_walker": runs[0]["sweeps_per_walker"]}
         rows.append(row)
-    t1 = rows[0]["wall_s_mean"]
-    i1 = rows[0]["iterations_mean"]
-    for row in rows:
-        row["speedup_S_p"] = t1 / row["wall_s_mean"]     # relative to the first walker count
-        row["iteration_ratio"] = i1 / row["iterations_mean"]
+        # speed-up relative to the first walker count
+        row["speedup_S_p"] = rows[0]["wall_s_mean"] / row["wall_s_mean"]
+        row["iteration_ratio"] = rows[0]["iterations_mean"] / row["iterations_mean"]
         if log:
             log(row)
     return rows
