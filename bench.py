@@ -253,6 +253,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the learned-vs-plain convergence comparison (run after the timing)")
+    ap.add_argument("--no-aux", action="store_true",
+                    help="skip the timings of the analysis kernels (run after the timing)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -377,18 +379,155 @@ def main(argv=None):
         line["e2e"] = e2e_measure(wl, args, systems, stream, device, world)
     if rank == 0 and world == 1 and not args.no_convergence:
         line["convergence"] = convergence_measure(stream)
+    if rank == 0 and world == 1 and not args.no_aux:
+        line["aux_kernels"] = aux_measure(stream, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle.build import build_oracle
         build_oracle()
         r, cores, sample = cpu_oracle_rate(wl, args.cpu_budget)
         line["cpu_baseline"] = {"value": r, "unit": "attempts/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
+        if not args.no_aux:
+            line["cpu_baseline"]["aux_kernels"] = aux_oracle_rates()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+AUX_SYSTEM = (2, 64, 410, 4096, 0, 0, 0)   # the 2D L=64, N=410, 4096-walker system
+
+
+def _events_ms(stream, fn, reps):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def aux_measure(stream, device):
+    """Device times of the analysis kernels on the 2D L=64, N=410 system with
+    4096 walkers, each against the HBM roofline of its algorithmic bytes:
+    droplet labelling (reads every walker's particle list and bitset, writes
+    V_D), replica exchange on an 8-copy ladder at equal temperatures (every
+    proposal accepted: both configurations read and written), and the cost of
+    the tunnelling flavour of the walker kernel."""
+    from paper_1401_4076_gb300 import mucal as m
+    out = {}
+    peaks, kind = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    d, L, N, W, _, _, _ = AUX_SYSTEM
+    V = L ** d
+    try:
+        with m.Mucal([AUX_SYSTEM], cuda_stream=stream.cuda_stream) as mc:
+            mc.set_weights(0, -1.2 * np.arange(d * N + 1, dtype=np.float64))
+            mc.run_iteration(20, 0)                 # bonds favoured: droplets form
+            ms = _events_ms(stream, mc.measure_droplets, 20)
+            bytes_ = W * (N * 2 + V // 8 + 4 + 4)
+            vd = mc.largest_droplets(0)
+            out["droplet_labelling"] = {
+                "ms_per_measurement": ms, "walkers_per_s": W / (ms / 1e3),
+                "mean_V_D": float(vd.mean()),
+                "roofline": {"bound": "hbm", "alg_bytes": bytes_,
+                             "achieved": bytes_ / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": bytes_ / (ms / 1e3) / 1e9 / hbm,
+                             "peak_source": f"{kind} hbm_gbs"}}
+            mc.run_iteration(100, 1)
+            k_plain = mc.stats(0)["kernel_ms"]
+            mc.set_tunnel_window(0, 0, 0)
+            mc.run_iteration(100, 2)
+            k_tun = mc.stats(0)["kernel_ms"]
+            out["tunnelling_flavour"] = {"walker_kernel_ms_plain": k_plain,
+                                         "walker_kernel_ms_tunnel": k_tun,
+                                         "cost": k_tun / k_plain - 1.0,
+                                         "sweeps": 100}
+    except Exception as exc:
+        out["droplet_error"] = repr(exc)[:200]
+    try:
+        K = 8
+        ladder = [(d, L, N, W, 0, 0, 10 ** 7 + k * W) for k in range(K)]
+        with m.Mucal(ladder, cuda_stream=stream.cuda_stream) as mc:
+            betas = [1.0] * K
+            r = [0]
+
+            def ex():
+                mc.replica_exchange(betas, r[0], 0)
+                r[0] += 1
+            ms = _events_ms(stream, ex, 20)
+            pairs = K // 2
+            bytes_ = pairs * W * 2 * 2 * (V * 2 + V // 8 + 4)
+            out["replica_exchange"] = {
+                "ms_per_call": ms, "ladder": f"{K} copies, parity 0 ({pairs} pairs), all accepted",
+                "note": "each call also uploads the threshold rows and reads back the counts",
+                "roofline": {"bound": "hbm", "alg_bytes": bytes_,
+                             "achieved": bytes_ / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": bytes_ / (ms / 1e3) / 1e9 / hbm,
+                             "peak_source": f"{kind} hbm_gbs"}}
+    except Exception as exc:
+        out["exchange_error"] = repr(exc)[:200]
+    try:
+        rng = np.random.default_rng(0)
+        H = rng.integers(1, 10 ** 6, d * N + 1)
+        lnW = np.cumsum(rng.normal(size=d * N + 1))
+        betas = np.linspace(0.1, 3.0, 1000)
+        t0 = time.perf_counter()
+        m.mucal_reweight(H, lnW, -d * N, betas)
+        out["reweighting"] = {"betas": 1000, "bins": d * N + 1,
+                              "host_ms": (time.perf_counter() - t0) * 1e3}
+    except Exception as exc:
+        out["reweight_error"] = repr(exc)[:200]
+    return out
+
+
+def aux_oracle_rates():
+    """The oracle beside the analysis kernels: breadth-first largest droplet
+    per walker (one thread) on the oracle's own placements of the same
+    system, the replica exchange on a 64-walker 8-copy ladder, and the
+    reweighting of 1000 temperatures."""
+    from oracle import chain, muca
+    out = {}
+    d, L, N, W, _, _, seed = AUX_SYSTEM
+    nw = 64
+    S, occ, E = chain.init_walkers(d, L, N, nw, seed)
+    t0 = time.perf_counter()
+    for w in range(nw):
+        chain.largest_droplet(d, L, occ[w])
+    dt = time.perf_counter() - t0
+    out["droplet_labelling"] = {"walkers_per_s": nw / dt, "cores": 1,
+                                "sample": f"{nw} random placements of 64x64, N=410"}
+    K = 8
+    V = L ** d
+    seeds = np.array([10 ** 7 + k * W for k in range(K)], dtype=np.uint64)
+    SS = np.zeros((K, nw, V), np.int32)
+    OO = np.zeros((K, nw, V), np.uint8)
+    EE = np.zeros((K, nw), np.int64)
+    for k in range(K):
+        SS[k], OO[k], EE[k] = chain.init_walkers(d, L, N, nw, int(seeds[k]))
+    t0 = time.perf_counter()
+    for r in range(5):
+        chain.replica_exchange([1.0] * K, seeds, r, 0, SS, OO, EE)
+    dt = (time.perf_counter() - t0) / 5
+    out["replica_exchange"] = {"ms_per_call": dt * 1e3, "cores": 1,
+                               "sample": f"{K} copies x {nw} walkers (the GPU line: x 4096)"}
+    rng = np.random.default_rng(0)
+    H = rng.integers(1, 10 ** 6, d * N + 1)
+    lnW = np.cumsum(rng.normal(size=d * N + 1))
+    t0 = time.perf_counter()
+    for b in np.linspace(0.1, 3.0, 100):
+        muca.reweight_moments(lnW, H, -d * N, b)
+    out["reweighting"] = {"ms_per_1000_betas": (time.perf_counter() - t0) * 1e4, "cores": 1,
+                          "sample": "100 betas, scaled to 1000"}
+    return out
 
 
 def convergence_measure(stream):
