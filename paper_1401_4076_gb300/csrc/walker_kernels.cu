@@ -105,6 +105,29 @@ __global__ void hist_reduce_kernel(SysParams p)
 // system k and counter (round, 0, 0, 2).  Thread 0 decides; the block swaps
 // bitset words, site lists and energies.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void block_swap_t(T *x, T *y, size_t n)
+{
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const T t = x[i];
+        x[i] = y[i];
+        y[i] = t;
+    }
+}
+
+// Swap two byte ranges of even length with the widest accesses their
+// alignment allows (16 bytes for the site lists and bitsets of most lattices).
+__device__ __forceinline__ void block_swap(void *x, void *y, size_t bytes)
+{
+    const uintptr_t al = (uintptr_t)x | (uintptr_t)y | (uintptr_t)bytes;
+    if ((al & 15) == 0)
+        block_swap_t(static_cast<uint4 *>(x), static_cast<uint4 *>(y), bytes / 16);
+    else if ((al & 3) == 0)
+        block_swap_t(static_cast<uint32_t *>(x), static_cast<uint32_t *>(y), bytes / 4);
+    else
+        block_swap_t(static_cast<uint16_t *>(x), static_cast<uint16_t *>(y), bytes / 2);
+}
+
 __global__ void exchange_kernel(const SysParams *__restrict__ sys, int n_sys, int parity,
                                 uint32_t round, const uint32_t *__restrict__ thr, int width,
                                 unsigned long long *accepted)
@@ -130,29 +153,11 @@ __global__ void exchange_kernel(const SysParams *__restrict__ sys, int n_sys, in
         }
         __syncthreads();
         if (take) {
-            uint32_t *ba = a.bits + (size_t)w * a.words, *bb = b.bits + (size_t)w * b.words;
-            for (int i = threadIdx.x; i < a.words; i += blockDim.x) {
-                const uint32_t t = ba[i];
-                ba[i] = bb[i];
-                bb[i] = t;
-            }
-            if (a.idx16) {
-                uint16_t *sa = static_cast<uint16_t *>(a.S) + (size_t)w * a.V;
-                uint16_t *sb = static_cast<uint16_t *>(b.S) + (size_t)w * b.V;
-                for (int i = threadIdx.x; i < a.V; i += blockDim.x) {
-                    const uint16_t t = sa[i];
-                    sa[i] = sb[i];
-                    sb[i] = t;
-                }
-            } else {
-                uint32_t *sa = static_cast<uint32_t *>(a.S) + (size_t)w * a.V;
-                uint32_t *sb = static_cast<uint32_t *>(b.S) + (size_t)w * b.V;
-                for (int i = threadIdx.x; i < a.V; i += blockDim.x) {
-                    const uint32_t t = sa[i];
-                    sa[i] = sb[i];
-                    sb[i] = t;
-                }
-            }
+            const size_t ib = a.idx16 ? 2 : 4;
+            block_swap(a.bits + (size_t)w * a.words, b.bits + (size_t)w * b.words,
+                       (size_t)a.words * 4);
+            block_swap(static_cast<char *>(a.S) + (size_t)w * a.V * ib,
+                       static_cast<char *>(b.S) + (size_t)w * b.V * ib, (size_t)a.V * ib);
         }
         __syncthreads();   // take is rewritten for the next walker
     }
