@@ -105,6 +105,10 @@ typedef struct mucal_launch_config {
                                   a multiple of 32 for GROUP */
     int32_t bits_in_smem;      /* 1: stage each walker's occupation bitset in shared
                                   memory for the launch; 0: use it in global memory */
+    int32_t persistent;        /* 1: launch only the blocks that fit on the device at
+                                  once; each pulls the next block of walkers from a
+                                  counter when it finishes one.  0: one block per block
+                                  of walkers, scheduled by the hardware */
 } mucal_launch_config;
 
 typedef struct mucal_system_info {
@@ -160,6 +164,15 @@ int mucal_get_thresholds(void *ctx, int32_t sys, uint32_t *T, int64_t n);
  * memory than a block can have for some system). */
 int mucal_set_launch_config(void *ctx, const mucal_launch_config *cfg);
 int mucal_get_launch_config(void *ctx, mucal_launch_config *cfg);
+
+/* CUDA-graph mode (enable = 1): mucal_run_iteration then launches its device
+ * work (histogram clears, walker update, histogram sums, timing events) as
+ * one CUDA graph, captured on the context's stream the first time and again
+ * whenever sweeps, the launch shape or the kernel flavour changes; between
+ * launches only the iteration number of the walker-update node is updated.
+ * Results are identical to the direct launches.  Waits for the stream.
+ * Errors: INVALID_ARG, CUDA. */
+int mucal_set_graph_mode(void *ctx, int32_t enable);
 
 /* One iteration of Sec. 2 for every system of the context, asynchronous on
  * the context's stream: zero the histograms, let every walker perform

@@ -1,8 +1,9 @@
 """Launch-shape autotuner for the walker update.
 
 For a set of systems it times every candidate launch shape: kernel (one
-thread per walker, or G lanes per walker), walkers per block, and whether the
-occupation bitsets are staged in shared memory.  All candidates compute the
+thread per walker, or G lanes per walker), walkers per block, whether the
+occupation bitsets are staged in shared memory, and (for the finalists)
+whether the launch is persistent.  All candidates compute the
 identical chain (the group kernel commits attempts in order), so only speed
 differs.  Timing runs on a scratch context whose walkers use other seeds, so
 the caller's chains are not advanced.  The acceptance rate changes which
@@ -73,9 +74,15 @@ def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 3, cuda_stream=
         first.sort(key=lambda x: x[1])
         table = []
         for cfg, _ in first[:finalists]:
-            ms, it = _time(mc, cfg, sweeps, repeats, it)
-            table.append((cfg, ms))
-            if log:
-                log(json.dumps({"launch": cfg, "kernel_ms": ms}))
+            # each finalist also as a persistent launch (resident blocks that
+            # pull the next block of walkers from a counter)
+            for c in (cfg, dict(cfg, persistent=1)):
+                try:
+                    ms, it = _time(mc, c, sweeps, repeats, it)
+                except m.MucalError:
+                    continue
+                table.append((c, ms))
+                if log:
+                    log(json.dumps({"launch": c, "kernel_ms": ms}))
     table.sort(key=lambda x: x[1])
     return table[0][0], table + first[finalists:]

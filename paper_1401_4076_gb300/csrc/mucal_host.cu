@@ -61,6 +61,17 @@ struct Context {
     size_t drop_scratch_words = 0;
     bool measured = false;
     bool tunnel = false;                 // walker kernels with tunnelling bookkeeping
+    int *d_next_item = nullptr;          // work-item counter of persistent launches
+    // CUDA-graph mode: one graph per (sweeps, launch shape, flavour, grid)
+    bool graph_mode = false;
+    cudaGraph_t graph = nullptr;         // kept: its nodes address the executable's
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphNode_t graph_walker = nullptr;  // the walker-update node (iteration changes)
+    cudaKernelNodeParams graph_kp{};
+    uint64_t graph_sweeps = 0;
+    LaunchShape graph_shape{};
+    bool graph_tunnel = false;
+    int graph_grid = 0;
     uint32_t *d_xthr = nullptr;          // replica-exchange thresholds, [pairs][2 n_bins - 1]
     uint32_t *xthr_pinned = nullptr;     // their host staging buffer
     size_t xthr_words = 0;
@@ -264,6 +275,9 @@ void destroy_context(Context *c)
     cudaFree(c->d_xthr);
     cudaFree(c->d_xacc);
     if (c->xthr_pinned) cudaFreeHost(c->xthr_pinned);
+    cudaFree(c->d_next_item);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     if (c->ev_it0) cudaEventDestroy(c->ev_it0);
     if (c->ev_k0) cudaEventDestroy(c->ev_k0);
     if (c->ev_k1) cudaEventDestroy(c->ev_k1);
@@ -345,6 +359,7 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     sh.lanes = cfg.lanes_per_walker;
     sh.walkers_per_block = cfg.walkers_per_block;
     sh.bits_in_smem = cfg.bits_in_smem ? 1 : 0;
+    sh.persistent = cfg.persistent ? 1 : 0;
     if (sh.kernel == MUCAL_KERNEL_THREAD) {
         if (sh.lanes != 1)
             return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
@@ -416,6 +431,83 @@ int reset_tunnel(Context *c, const System &s)
 {
     CUDA_TRY(c, cudaMemsetAsync(s.p.tun_state, 0, (size_t)s.p.n_walkers, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(s.p.tun_count, 0, (size_t)s.p.n_walkers * 4, c->stream));
+    return MUCAL_OK;
+}
+
+// The device work of one iteration, asynchronous on the context's stream:
+// clear the histograms, the walker update, the histogram sums, with the
+// timing events around them.
+int enqueue_iteration(Context *c, uint64_t sweeps, uint32_t iteration, int grid)
+{
+    CUDA_TRY(c, cudaEventRecord(c->ev_it0, c->stream));
+    for (auto &s : c->sys) {
+        CUDA_TRY(c, cudaMemsetAsync(s.p.hist, 0, (size_t)s.p.hist_rows * (size_t)s.p.n_bins * 8,
+                                    c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(s.p.H, 0, (size_t)s.p.n_bins * 8, c->stream));
+    }
+    if (c->shape.persistent) CUDA_TRY(c, cudaMemsetAsync(c->d_next_item, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
+    CUDA_TRY(c, mucal::launch_walker_update(c->d_sys, c->d_work, c->n_blocks, c->shape, sweeps,
+                                            iteration, c->tunnel, grid, c->d_next_item, c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->ev_k1, c->stream));
+    std::vector<SysParams> hp(c->sys.size());
+    for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
+    CUDA_TRY(c, mucal::launch_hist_reduce(hp.data(), c->d_sys, (int)hp.size(), c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->ev_it1, c->stream));
+    return MUCAL_OK;
+}
+
+// Capture enqueue_iteration into a CUDA graph on the context's stream,
+// instantiate it and remember its walker-update node.
+void drop_graph(Context *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_walker = nullptr;
+}
+
+int capture_iteration(Context *c, uint64_t sweeps, uint32_t iteration, int grid)
+{
+    drop_graph(c);
+    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_iteration(c, sweeps, iteration, grid);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
+    if (rc != MUCAL_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    CUDA_TRY(c, end);
+    const void *fn = mucal::walker_update_fn(c->shape, c->tunnel);
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(graph, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n && !c->graph_walker; ++i) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[i], &t);
+        if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+        if (e == cudaSuccess && kp.func == fn) {
+            c->graph_walker = nodes[i];
+            c->graph_kp = kp;
+        }
+    }
+    if (e == cudaSuccess && !c->graph_walker) e = cudaErrorInvalidValue;
+    c->graph = graph;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    if (e != cudaSuccess) {
+        c->graph_exec = nullptr;
+        drop_graph(c);
+        return fail(c, MUCAL_ERR_CUDA, "iteration graph capture failed: %s", cudaGetErrorString(e));
+    }
+    c->graph_sweeps = sweeps;
+    c->graph_shape = c->shape;
+    c->graph_tunnel = c->tunnel;
+    c->graph_grid = grid;
     return MUCAL_OK;
 }
 
@@ -567,6 +659,8 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
             cudaMemsetAsync(p.tun_count, 0, nw * 4, c->stream) != cudaSuccess)
             return bail(fail(nullptr, MUCAL_ERR_CUDA, "memset failed"));
     }
+    if (cudaMalloc(&c->d_next_item, sizeof(int)) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of the work-item counter failed"));
     if (cudaMalloc(&c->d_drop_err, sizeof(int)) != cudaSuccess ||
         cudaMemsetAsync(c->d_drop_err, 0, sizeof(int), c->stream) != cudaSuccess)
         return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of the droplet error flag failed"));
@@ -599,9 +693,9 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
                                  "system %d: initial energy %d outside window [%d, %d]", i, v,
                                  s.desc.e_lo, s.desc.e_hi));
     }
-    mucal_launch_config def{MUCAL_KERNEL_GROUP, 8, 16, 1};
+    mucal_launch_config def{MUCAL_KERNEL_GROUP, 8, 16, 1, 0};
     for (auto &s : c->sys)
-        if (smem_for(LaunchShape{MUCAL_KERNEL_GROUP, 8, 16, 1, 0, 0}, s.p) > (size_t)c->max_smem)
+        if (smem_for(LaunchShape{MUCAL_KERNEL_GROUP, 8, 16, 1, 0, 0, 0}, s.p) > (size_t)c->max_smem)
             def.bits_in_smem = 0;
     rc = apply_launch_config(c, def);
     if (rc != MUCAL_OK) return bail(rc);
@@ -669,6 +763,18 @@ int mucal_get_launch_config(void *ctx, mucal_launch_config *cfg)
     cfg->lanes_per_walker = c->shape.lanes;
     cfg->walkers_per_block = c->shape.walkers_per_block;
     cfg->bits_in_smem = c->shape.bits_in_smem;
+    cfg->persistent = c->shape.persistent;
+    return MUCAL_OK;
+}
+
+int mucal_set_graph_mode(void *ctx, int32_t enable)
+{
+    Context *c = as_ctx(ctx);
+    if (!c) return MUCAL_ERR_INVALID_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->graph_mode = enable != 0;
+    drop_graph(c);
     return MUCAL_OK;
 }
 
@@ -681,24 +787,42 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
         if ((uint64_t)sweeps * (uint64_t)s.p.N >= (1ull << 40))
             return fail(c, MUCAL_ERR_INVALID_ARG, "sweeps * N must be below 2^40");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    CUDA_TRY(c, cudaEventRecord(c->ev_it0, c->stream));
+    int grid = 0;
+    CUDA_TRY(c, mucal::walker_update_grid(c->shape, c->tunnel, c->n_blocks, &grid));
+    if (!c->graph_mode) {
+        int rc = enqueue_iteration(c, (uint64_t)sweeps, iteration, grid);
+        if (rc != MUCAL_OK) return rc;
+    } else {
+        const LaunchShape &a = c->shape, &b = c->graph_shape;
+        const bool same = c->graph_exec && c->graph_sweeps == (uint64_t)sweeps &&
+                          c->graph_tunnel == c->tunnel && c->graph_grid == grid &&
+                          a.kernel == b.kernel && a.lanes == b.lanes &&
+                          a.walkers_per_block == b.walkers_per_block &&
+                          a.bits_in_smem == b.bits_in_smem && a.thr_in_smem == b.thr_in_smem &&
+                          a.smem_bytes == b.smem_bytes && a.persistent == b.persistent;
+        if (!same) {
+            int rc = capture_iteration(c, (uint64_t)sweeps, iteration, grid);
+            if (rc != MUCAL_OK) return rc;
+        }
+        // only the iteration number (the Philox counter word) changes
+        uint64_t sw = (uint64_t)sweeps;
+        int n_items = c->n_blocks;
+        int *counter = c->shape.persistent ? c->d_next_item : nullptr;
+        const SysParams *dsys = c->d_sys;
+        const BlockWork *dwork = c->d_work;
+        void *args[] = {(void *)&dsys, (void *)&dwork, (void *)&sw, (void *)&iteration,
+                        (void *)&n_items, (void *)&counter};
+        cudaKernelNodeParams kp = c->graph_kp;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        CUDA_TRY(c, cudaGraphExecKernelNodeSetParams(c->graph_exec, c->graph_walker, &kp));
+        CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    }
     for (auto &s : c->sys) {
-        const size_t nw = (size_t)s.p.n_walkers;
-        CUDA_TRY(c, cudaMemsetAsync(s.p.hist, 0, (size_t)s.p.hist_rows * (size_t)s.p.n_bins * 8,
-                                    c->stream));
-        CUDA_TRY(c, cudaMemsetAsync(s.p.H, 0, (size_t)s.p.n_bins * 8, c->stream));
         s.hist_on_host = false;
-        s.last_attempts = (uint64_t)sweeps * (uint64_t)s.p.N * nw;
+        s.last_attempts = (uint64_t)sweeps * (uint64_t)s.p.N * (uint64_t)s.p.n_walkers;
         s.lnW_run = s.lnW;
     }
-    CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
-    CUDA_TRY(c, mucal::launch_walker_update(c->d_sys, c->d_work, c->n_blocks, c->shape,
-                                            (uint64_t)sweeps, iteration, c->tunnel, c->stream));
-    CUDA_TRY(c, cudaEventRecord(c->ev_k1, c->stream));
-    std::vector<SysParams> hp(c->sys.size());
-    for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
-    CUDA_TRY(c, mucal::launch_hist_reduce(hp.data(), c->d_sys, (int)hp.size(), c->stream));
-    CUDA_TRY(c, cudaEventRecord(c->ev_it1, c->stream));
     c->ran = true;
     c->sweeps_last = (uint64_t)sweeps;
     c->launches += 1;

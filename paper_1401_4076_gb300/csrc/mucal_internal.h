@@ -51,6 +51,7 @@ struct LaunchShape {
     int bits_in_smem;
     int thr_in_smem;        // stage the system's threshold table in shared memory
     size_t smem_bytes;      // dynamic shared memory per block
+    int persistent;         // resident blocks pull work items from a counter
 };
 
 // Kernel launchers (walker_kernels.cu).  All are asynchronous on `stream`.
@@ -58,15 +59,22 @@ cudaError_t launch_fill_identity(const SysParams *host_sys, const SysParams *dev
                                  cudaStream_t stream);
 cudaError_t launch_init_walkers(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                 cudaStream_t stream);
-// tunnel: run the kernels with the tunnelling bookkeeping (Sec. 4).
-cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
-                                 int n_blocks, const LaunchShape &shape, uint64_t sweeps,
-                                 uint32_t iteration, bool tunnel, cudaStream_t stream);
-// The tunnelling flavour of the walker update (walker_kernels_tun.cu): its
-// launcher and its 24 kernels (for their shared-memory attributes).
-cudaError_t launch_walker_update_tunnel(const SysParams *dev_sys, const BlockWork *dev_work,
-                                        int n_blocks, const LaunchShape &shape, uint64_t sweeps,
-                                        uint32_t iteration, cudaStream_t stream);
+// The walker-update kernel of a launch shape; tunnel selects the flavour with
+// the tunnelling bookkeeping (Sec. 4).  Its arguments are (const SysParams *,
+// const BlockWork *, uint64_t sweeps, uint32_t iteration, int n_items,
+// int *next_item).
+const void *walker_update_fn(const LaunchShape &shape, bool tunnel);
+// Blocks of a launch over n_items work items: n_items, or for a persistent
+// shape the blocks that fit on the device at once (at most n_items).
+cudaError_t walker_update_grid(const LaunchShape &shape, bool tunnel, int n_items, int *grid);
+// Launch it on `grid` blocks; next_item: a device counter that is 0 at the
+// start of the launch (used only by persistent shapes).
+cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work, int n_items,
+                                 const LaunchShape &shape, uint64_t sweeps, uint32_t iteration,
+                                 bool tunnel, int grid, int *next_item, cudaStream_t stream);
+// The tunnelling flavour (walker_kernels_tun.cu): its kernel of a launch
+// shape and all its 24 kernels (for their shared-memory attributes).
+const void *walker_update_fn_tunnel(const LaunchShape &shape);
 void walker_update_tunnel_fns(const void *(&fns)[24]);
 // Shared-memory layout of a walker-update block: [threshold table][bitsets].
 size_t thr_smem_words(const SysParams &p);

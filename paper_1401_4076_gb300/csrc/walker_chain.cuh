@@ -555,33 +555,49 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
     }
 }
 
+// Work items of a launch: block b takes item b; with next_item non-NULL the
+// launch is persistent (fewer blocks than items) and a block that finishes
+// an item takes the next one from the counter (which starts at 0).
+__device__ __forceinline__ int next_work_item(int *next_item, int *s_item)
+{
+    __syncthreads();   // the item's shared memory and *s_item are reused
+    if (threadIdx.x == 0) *s_item = (int)gridDim.x + atomicAdd(next_item, 1);
+    __syncthreads();
+    return *s_item;
+}
+
 template <bool SB, bool ST, bool TUN>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
-                     uint64_t sweeps, uint32_t iter)
+                     uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    const BlockWork wk = work[blockIdx.x];
-    const SysParams &p = sys[wk.sys];
-    const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
-    const int lw = threadIdx.x;
-    if (lw < wk.count) {
-        const int w = wk.walker0 + lw;
-        const uint32_t *thr = ST ? smem : p.thr;
-        uint32_t *bits0 = SB ? smem + (ST ? thr_words_aligned(p) : 0)
-                             : p.bits + (size_t)wk.walker0 * (size_t)p.words;
-        uint32_t *bits = bits0 + (size_t)lw * p.words;
-        unsigned long long *hist = hist_row(p, w, wk.hist_row);
-        const uint64_t A = sweeps * (uint64_t)p.N;
-        if (p.d == 2) {
-            if (p.idx16) chain_thread<2, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
-            else chain_thread<2, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
-        } else {
-            if (p.idx16) chain_thread<3, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
-            else chain_thread<3, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+    __shared__ int s_item;
+    for (int item = blockIdx.x; item < n_items;) {
+        const BlockWork wk = work[item];
+        const SysParams &p = sys[wk.sys];
+        const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+        const int lw = threadIdx.x;
+        if (lw < wk.count) {
+            const int w = wk.walker0 + lw;
+            const uint32_t *thr = ST ? smem : p.thr;
+            uint32_t *bits0 = SB ? smem + (ST ? thr_words_aligned(p) : 0)
+                                 : p.bits + (size_t)wk.walker0 * (size_t)p.words;
+            uint32_t *bits = bits0 + (size_t)lw * p.words;
+            unsigned long long *hist = hist_row(p, w, wk.hist_row);
+            const uint64_t A = sweeps * (uint64_t)p.N;
+            if (p.d == 2) {
+                if (p.idx16) chain_thread<2, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+                else chain_thread<2, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+            } else {
+                if (p.idx16) chain_thread<3, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+                else chain_thread<3, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+            }
         }
+        block_finish(bs, SB ? 1 : 0);
+        if (!next_item) break;
+        item = next_work_item(next_item, &s_item);
     }
-    block_finish(bs, SB ? 1 : 0);
 }
 
 template <int G, bool SB, bool ST, bool TUN>
@@ -609,76 +625,48 @@ __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &
 template <int G, bool SB, bool ST, bool TUN>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
-                    uint64_t sweeps, uint32_t iter)
+                    uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    const BlockWork wk = work[blockIdx.x];
-    const SysParams &p = sys[wk.sys];
-    const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
-    (void)bs;
-    group_body<G, SB, ST, TUN>(p, wk, smem, sweeps, iter);
-    block_finish(bs, SB ? 1 : 0);
+    __shared__ int s_item;
+    for (int item = blockIdx.x; item < n_items;) {
+        const BlockWork wk = work[item];
+        const SysParams &p = sys[wk.sys];
+        const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+        group_body<G, SB, ST, TUN>(p, wk, smem, sweeps, iter);
+        block_finish(bs, SB ? 1 : 0);
+        if (!next_item) break;
+        item = next_work_item(next_item, &s_item);
+    }
 }
 
-template <int G, bool SB, bool ST, bool TUN>
-cudaError_t launch_group_t(int n_blocks, int threads, size_t smem, const SysParams *dev_sys,
-                           const BlockWork *dev_work, uint64_t sweeps, uint32_t iteration,
-                           cudaStream_t stream)
-{
-    walker_update_group<G, SB, ST, TUN><<<n_blocks, threads, smem, stream>>>(dev_sys, dev_work,
-                                                                             sweeps, iteration);
-    return cudaGetLastError();
-}
-
+// The walker-update kernel of a launch shape (one TUN flavour).
 template <int G, bool TUN>
-cudaError_t launch_group_g(const LaunchShape &sh, int n_blocks, int threads, const SysParams *dev_sys,
-                           const BlockWork *dev_work, uint64_t sweeps, uint32_t iteration,
-                           cudaStream_t stream)
+const void *group_fn(const LaunchShape &sh)
 {
-    if (sh.bits_in_smem && sh.thr_in_smem)
-        return launch_group_t<G, true, true, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
-    if (sh.bits_in_smem)
-        return launch_group_t<G, true, false, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
-    if (sh.thr_in_smem)
-        return launch_group_t<G, false, true, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
-    return launch_group_t<G, false, false, TUN>(n_blocks, threads, sh.smem_bytes, dev_sys, dev_work, sweeps, iteration, stream);
+    if (sh.bits_in_smem && sh.thr_in_smem) return (const void *)walker_update_group<G, true, true, TUN>;
+    if (sh.bits_in_smem) return (const void *)walker_update_group<G, true, false, TUN>;
+    if (sh.thr_in_smem) return (const void *)walker_update_group<G, false, true, TUN>;
+    return (const void *)walker_update_group<G, false, false, TUN>;
 }
 
 template <bool TUN>
-cudaError_t launch_group_dispatch(const LaunchShape &sh, int n_blocks, int threads,
-                                  const SysParams *dev_sys, const BlockWork *dev_work,
-                                  uint64_t sweeps, uint32_t iteration, cudaStream_t stream)
+const void *walker_update_fn_t(const LaunchShape &sh)
 {
+    if (sh.kernel == 0) {
+        if (sh.bits_in_smem && sh.thr_in_smem) return (const void *)walker_update_thread<true, true, TUN>;
+        if (sh.bits_in_smem) return (const void *)walker_update_thread<true, false, TUN>;
+        if (sh.thr_in_smem) return (const void *)walker_update_thread<false, true, TUN>;
+        return (const void *)walker_update_thread<false, false, TUN>;
+    }
     switch (sh.lanes) {
-    case 2: return launch_group_g<2, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
-    case 4: return launch_group_g<4, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
-    case 8: return launch_group_g<8, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
-    case 16: return launch_group_g<16, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
-    case 32: return launch_group_g<32, TUN>(sh, n_blocks, threads, dev_sys, dev_work, sweeps, iteration, stream);
-    default: return cudaErrorInvalidValue;
+    case 2: return group_fn<2, TUN>(sh);
+    case 4: return group_fn<4, TUN>(sh);
+    case 8: return group_fn<8, TUN>(sh);
+    case 16: return group_fn<16, TUN>(sh);
+    case 32: return group_fn<32, TUN>(sh);
+    default: return nullptr;
     }
-}
-
-template <bool TUN>
-cudaError_t launch_walker_update_t(const SysParams *dev_sys, const BlockWork *dev_work,
-                                   int n_blocks, const LaunchShape &shape, uint64_t sweeps,
-                                   uint32_t iteration, cudaStream_t stream)
-{
-    if (n_blocks <= 0) return cudaSuccess;
-    const int threads = shape.walkers_per_block * shape.lanes;
-    if (shape.kernel == 0) {
-        if (shape.bits_in_smem && shape.thr_in_smem)
-            walker_update_thread<true, true, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
-        else if (shape.bits_in_smem)
-            walker_update_thread<true, false, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
-        else if (shape.thr_in_smem)
-            walker_update_thread<false, true, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
-        else
-            walker_update_thread<false, false, TUN><<<n_blocks, threads, shape.smem_bytes, stream>>>(dev_sys, dev_work, sweeps, iteration);
-        return cudaGetLastError();
-    }
-    return launch_group_dispatch<TUN>(shape, n_blocks, threads, dev_sys, dev_work, sweeps, iteration,
-                                      stream);
 }
 
 // Every walker-update kernel of one TUN flavour (for their shared-memory

@@ -244,15 +244,42 @@ cudaError_t walker_update_max_smem(int *bytes)
     return cudaSuccess;
 }
 
-cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work,
-                                 int n_blocks, const LaunchShape &shape, uint64_t sweeps,
-                                 uint32_t iteration, bool tunnel, cudaStream_t stream)
+const void *walker_update_fn(const LaunchShape &shape, bool tunnel)
 {
-    if (tunnel)
-        return launch_walker_update_tunnel(dev_sys, dev_work, n_blocks, shape, sweeps, iteration,
-                                           stream);
-    return launch_walker_update_t<false>(dev_sys, dev_work, n_blocks, shape, sweeps, iteration,
-                                         stream);
+    return tunnel ? walker_update_fn_tunnel(shape) : walker_update_fn_t<false>(shape);
+}
+
+cudaError_t walker_update_grid(const LaunchShape &shape, bool tunnel, int n_items, int *grid)
+{
+    *grid = n_items;
+    if (!shape.persistent || n_items <= 0) return cudaSuccess;
+    const void *fn = walker_update_fn(shape, tunnel);
+    if (!fn) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn,
+                                                          shape.walkers_per_block * shape.lanes,
+                                                          shape.smem_bytes);
+    if (e != cudaSuccess) return e;
+    const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    *grid = (int)(resident < n_items ? resident : n_items);
+    return cudaSuccess;
+}
+
+cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work, int n_items,
+                                 const LaunchShape &shape, uint64_t sweeps, uint32_t iteration,
+                                 bool tunnel, int grid, int *next_item, cudaStream_t stream)
+{
+    if (n_items <= 0) return cudaSuccess;
+    const void *fn = walker_update_fn(shape, tunnel);
+    if (!fn) return cudaErrorInvalidValue;
+    int *counter = shape.persistent ? next_item : nullptr;
+    void *args[] = {(void *)&dev_sys, (void *)&dev_work, (void *)&sweeps, (void *)&iteration,
+                    (void *)&n_items, (void *)&counter};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)(shape.walkers_per_block * shape.lanes)),
+                            args, shape.smem_bytes, stream);
 }
 
 size_t thr_smem_words(const SysParams &p) { return thr_words_aligned(p); }

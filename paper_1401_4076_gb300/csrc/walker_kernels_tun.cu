@@ -5,12 +5,9 @@
 
 namespace mucal {
 
-cudaError_t launch_walker_update_tunnel(const SysParams *dev_sys, const BlockWork *dev_work,
-                                        int n_blocks, const LaunchShape &shape, uint64_t sweeps,
-                                        uint32_t iteration, cudaStream_t stream)
+const void *walker_update_fn_tunnel(const LaunchShape &shape)
 {
-    return launch_walker_update_t<true>(dev_sys, dev_work, n_blocks, shape, sweeps, iteration,
-                                        stream);
+    return walker_update_fn_t<true>(shape);
 }
 
 void walker_update_tunnel_fns(const void *(&fns)[24]) { walker_update_fns<true>(fns); }

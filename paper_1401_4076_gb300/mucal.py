@@ -45,7 +45,7 @@ EXPORTED = [
     "mucal_reweight", "mucal_reweight_system", "mucal_measure_droplets", "mucal_get_droplet_stats",
     "mucal_get_largest_droplets", "mucal_reset_droplet_stats", "mucal_droplet_delta",
     "mucal_droplet_lambda", "mucal_replica_exchange", "mucal_set_tunnel_window",
-    "mucal_get_tunnel_counts", "mucal_reset_tunnel_counts",
+    "mucal_get_tunnel_counts", "mucal_reset_tunnel_counts", "mucal_set_graph_mode",
 ]
 
 
@@ -57,7 +57,8 @@ class mucal_system_desc(ctypes.Structure):
 
 class mucal_launch_config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
-                ("walkers_per_block", ctypes.c_int32), ("bits_in_smem", ctypes.c_int32)]
+                ("walkers_per_block", ctypes.c_int32), ("bits_in_smem", ctypes.c_int32),
+                ("persistent", ctypes.c_int32)]
 
 
 class mucal_system_info(ctypes.Structure):
@@ -132,6 +133,7 @@ def load_library(path: str = LIB_PATH):
         "mucal_set_tunnel_window": (ctypes.c_int, [P, I32, I32, I32]),
         "mucal_get_tunnel_counts": (ctypes.c_int, [P, I32, P, P, P]),
         "mucal_reset_tunnel_counts": (ctypes.c_int, [P]),
+        "mucal_set_graph_mode": (ctypes.c_int, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -203,8 +205,9 @@ def mucal_get_thresholds(ctx, sys, n_bins, width):
 
 
 def mucal_set_launch_config(ctx, kernel=MUCAL_KERNEL_THREAD, lanes_per_walker=1,
-                            walkers_per_block=32, bits_in_smem=1):
-    cfg = mucal_launch_config(kernel, lanes_per_walker, walkers_per_block, bits_in_smem)
+                            walkers_per_block=32, bits_in_smem=1, persistent=0):
+    cfg = mucal_launch_config(kernel, lanes_per_walker, walkers_per_block, bits_in_smem,
+                              int(persistent))
     _check(load_library().mucal_set_launch_config(ctx, ctypes.byref(cfg)), ctx)
 
 
@@ -212,7 +215,12 @@ def mucal_get_launch_config(ctx):
     cfg = mucal_launch_config()
     _check(load_library().mucal_get_launch_config(ctx, ctypes.byref(cfg)), ctx)
     return {"kernel": cfg.kernel, "lanes_per_walker": cfg.lanes_per_walker,
-            "walkers_per_block": cfg.walkers_per_block, "bits_in_smem": cfg.bits_in_smem}
+            "walkers_per_block": cfg.walkers_per_block, "bits_in_smem": cfg.bits_in_smem,
+            "persistent": cfg.persistent}
+
+
+def mucal_set_graph_mode(ctx, enable):
+    _check(load_library().mucal_set_graph_mode(ctx, 1 if enable else 0), ctx)
 
 
 def mucal_run_iteration(ctx, sweeps, iteration):
@@ -490,6 +498,9 @@ class Mucal:
 
     def reweight(self, sys, beta, obs=None):
         return mucal_reweight_system(self.ctx, sys, self.info[sys]["n_bins"], beta, obs)
+
+    def set_graph_mode(self, enable=True):
+        mucal_set_graph_mode(self.ctx, enable)
 
     def set_tunnel_window(self, sys, e_min, e_max):
         mucal_set_tunnel_window(self.ctx, sys, e_min, e_max)
