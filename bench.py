@@ -225,7 +225,8 @@ def _config(wl, args):
             "weights": "recursive update from lnW=0; timed steps are iterations P+W..P+W+K-1",
             "prerun_iterations": getattr(args, "prerun", 0),
             "l2": "flushed (512 MB write) before every timed step",
-            "launch": getattr(args, "launch_desc", None)}
+            "launch": getattr(args, "launch_desc", None),
+            "cuda_graph": bool(getattr(args, "graph", False))}
 
 
 def main(argv=None):
@@ -251,6 +252,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the learned-vs-plain convergence comparison (run after the timing)")
+    ap.add_argument("--graph", action="store_true",
+                    help="run every iteration's device work as one CUDA graph launch")
+    ap.add_argument("--persistent", type=int, default=-1,
+                    help="1: persistent walker-update launch, 0: one block per work item")
     ap.add_argument("--no-aux", action="store_true",
                     help="skip the timings of the analysis kernels (run after the timing)")
     args = ap.parse_args(argv)
@@ -286,13 +291,16 @@ def main(argv=None):
     attempts_per_step = sweeps * sum(s[2] * s[3] for s in systems)
 
     mc = m.Mucal(systems, cuda_stream=stream.cuda_stream)
-    if args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0:
+    if args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0:
         cur = mc.launch()
         cfg = dict(kernel=args.kernel if args.kernel >= 0 else cur["kernel"],
                    lanes_per_walker=args.lanes or cur["lanes_per_walker"],
                    walkers_per_block=args.wpb or cur["walkers_per_block"],
-                   bits_in_smem=args.smem if args.smem >= 0 else cur["bits_in_smem"])
+                   bits_in_smem=args.smem if args.smem >= 0 else cur["bits_in_smem"],
+                   persistent=args.persistent if args.persistent >= 0 else cur["persistent"])
         mc.set_launch(**cfg)
+    if args.graph:
+        mc.set_graph_mode(True)
     args.launch_desc = mc.launch()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
 
@@ -306,7 +314,7 @@ def main(argv=None):
     for it in range(args.prerun, args.prerun + args.warmup):
         step(it)
     torch.cuda.synchronize(device)
-    explicit = args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0
+    explicit = args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0
     if not args.no_autotune and not explicit:
         from paper_1401_4076_gb300.autotune import autotune
         lnWs = [mc.weights(s) for s in range(len(systems))]
@@ -576,6 +584,8 @@ def e2e_measure(wl, args, systems, stream, device, world):
     mc = m.Mucal(systems, cuda_stream=stream.cuda_stream)
     if args.launch_desc:
         mc.set_launch(**args.launch_desc)
+    if args.graph:
+        mc.set_graph_mode(True)
     h2d = d2h = 0
     for it in range(args.steps):
         mc.run_iteration(sweeps, it)

@@ -170,7 +170,8 @@ int mucal_get_launch_config(void *ctx, mucal_launch_config *cfg);
  * one CUDA graph, captured on the context's stream the first time and again
  * whenever sweeps, the launch shape or the kernel flavour changes; between
  * launches only the iteration number of the walker-update node is updated.
- * Results are identical to the direct launches.  Waits for the stream.
+ * Results are identical to the direct launches; mucal_stats.kernel_ms then
+ * times the whole graph (clears and sums included).  Waits for the stream.
  * Errors: INVALID_ARG, CUDA. */
 int mucal_set_graph_mode(void *ctx, int32_t enable);
 

@@ -436,24 +436,25 @@ int reset_tunnel(Context *c, const System &s)
 
 // The device work of one iteration, asynchronous on the context's stream:
 // clear the histograms, the walker update, the histogram sums, with the
-// timing events around them.
-int enqueue_iteration(Context *c, uint64_t sweeps, uint32_t iteration, int grid)
+// timing events around them unless it is being captured into a graph (the
+// graph launch is timed from outside instead).
+int enqueue_iteration(Context *c, uint64_t sweeps, uint32_t iteration, int grid, bool events)
 {
-    CUDA_TRY(c, cudaEventRecord(c->ev_it0, c->stream));
+    if (events) CUDA_TRY(c, cudaEventRecord(c->ev_it0, c->stream));
     for (auto &s : c->sys) {
         CUDA_TRY(c, cudaMemsetAsync(s.p.hist, 0, (size_t)s.p.hist_rows * (size_t)s.p.n_bins * 8,
                                     c->stream));
         CUDA_TRY(c, cudaMemsetAsync(s.p.H, 0, (size_t)s.p.n_bins * 8, c->stream));
     }
     if (c->shape.persistent) CUDA_TRY(c, cudaMemsetAsync(c->d_next_item, 0, sizeof(int), c->stream));
-    CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
+    if (events) CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
     CUDA_TRY(c, mucal::launch_walker_update(c->d_sys, c->d_work, c->n_blocks, c->shape, sweeps,
                                             iteration, c->tunnel, grid, c->d_next_item, c->stream));
-    CUDA_TRY(c, cudaEventRecord(c->ev_k1, c->stream));
+    if (events) CUDA_TRY(c, cudaEventRecord(c->ev_k1, c->stream));
     std::vector<SysParams> hp(c->sys.size());
     for (size_t i = 0; i < c->sys.size(); ++i) hp[i] = c->sys[i].p;
     CUDA_TRY(c, mucal::launch_hist_reduce(hp.data(), c->d_sys, (int)hp.size(), c->stream));
-    CUDA_TRY(c, cudaEventRecord(c->ev_it1, c->stream));
+    if (events) CUDA_TRY(c, cudaEventRecord(c->ev_it1, c->stream));
     return MUCAL_OK;
 }
 
@@ -472,7 +473,7 @@ int capture_iteration(Context *c, uint64_t sweeps, uint32_t iteration, int grid)
 {
     drop_graph(c);
     CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue_iteration(c, sweeps, iteration, grid);
+    const int rc = enqueue_iteration(c, sweeps, iteration, grid, false);
     cudaGraph_t graph = nullptr;
     const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
     if (rc != MUCAL_OK) {
@@ -790,7 +791,7 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
     int grid = 0;
     CUDA_TRY(c, mucal::walker_update_grid(c->shape, c->tunnel, c->n_blocks, &grid));
     if (!c->graph_mode) {
-        int rc = enqueue_iteration(c, (uint64_t)sweeps, iteration, grid);
+        int rc = enqueue_iteration(c, (uint64_t)sweeps, iteration, grid, true);
         if (rc != MUCAL_OK) return rc;
     } else {
         const LaunchShape &a = c->shape, &b = c->graph_shape;
@@ -816,7 +817,12 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
         kp.kernelParams = args;
         kp.extra = nullptr;
         CUDA_TRY(c, cudaGraphExecKernelNodeSetParams(c->graph_exec, c->graph_walker, &kp));
+        // the whole graph is timed: kernel_ms then includes the clears and sums
+        CUDA_TRY(c, cudaEventRecord(c->ev_it0, c->stream));
+        CUDA_TRY(c, cudaEventRecord(c->ev_k0, c->stream));
         CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
+        CUDA_TRY(c, cudaEventRecord(c->ev_k1, c->stream));
+        CUDA_TRY(c, cudaEventRecord(c->ev_it1, c->stream));
     }
     for (auto &s : c->sys) {
         s.hist_on_host = false;
