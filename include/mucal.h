@@ -443,6 +443,12 @@ int mucal_mlp_get_params(void *mlp, float *params, int64_t n, int32_t rounded);
 /* y[B] = network(X[B][4]). */
 int mucal_mlp_forward(void *mlp, const float *X, int64_t B, float *y);
 
+/* y[B] = network(X[B][4]) with the 128x128 layer on the fifth-generation
+ * tensor cores (tcgen05.mma, accumulator in tensor memory; 128 rows per CTA).
+ * Same numerics as mucal_mlp_forward up to the order of fp32 sums.  Errors:
+ * INVALID_ARG, OOM, CUDA, STATE (a tensor-core wait ran out). */
+int mucal_mlp_forward_tcgen05(void *mlp, const float *X, int64_t B, float *y);
+
 /* One forward and backward pass of the mean squared error against t[B]:
  * loss (nullable) and the gradient with respect to all 17281 parameters
  * (grad nullable, host fp32[17281]).  Parameters are not changed. */

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "mucal.h"
+#include "mucal_internal.h"
 
 namespace {
 
@@ -419,6 +420,7 @@ struct Mlp {
     int64_t cap = 0;           // rows of the batch buffers (multiple of 256)
     float *X = nullptr, *t = nullptr, *y = nullptr;
     __nv_bfloat16 *h1T = nullptr, *dz2T = nullptr;
+    int *d_err = nullptr;      // error flag of the tcgen05 forward kernel
     int64_t step = 0;
     std::string err;
 };
@@ -556,6 +558,7 @@ void mucal_mlp_destroy(void *mlp)
     cudaFree(m->w); cudaFree(m->grad); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->wq);
     cudaFree(m->loss); cudaFree(m->X); cudaFree(m->t); cudaFree(m->y); cudaFree(m->h1T);
     cudaFree(m->dz2T);
+    cudaFree(m->d_err);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -595,6 +598,24 @@ int mucal_mlp_forward(void *mlp, const float *X, int64_t B, float *y)
     MLP_TRY(m, cudaGetLastError());
     MLP_TRY(m, cudaMemcpyAsync(y, m->y, B * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
     MLP_TRY(m, cudaStreamSynchronize(m->stream));
+    return MUCAL_OK;
+}
+
+int mucal_mlp_forward_tcgen05(void *mlp, const float *X, int64_t B, float *y)
+{
+    Mlp *m = static_cast<Mlp *>(mlp);
+    if (!m || !X || !y || B <= 0) return mfail(m, MUCAL_ERR_INVALID_ARG, "bad forward arguments");
+    MLP_TRY(m, cudaSetDevice(m->device));
+    int rc = upload_batch(m, X, nullptr, B);
+    if (rc != MUCAL_OK) return rc;
+    if (!m->d_err) MLP_TRY(m, cudaMalloc(&m->d_err, sizeof(int)));
+    MLP_TRY(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+    MLP_TRY(m, mucal::mlp_forward_tcgen05(m->wq, m->X, m->y, B, m->d_err, m->stream));
+    int flag = 0;
+    MLP_TRY(m, cudaMemcpyAsync(y, m->y, B * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    MLP_TRY(m, cudaMemcpyAsync(&flag, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MLP_TRY(m, cudaStreamSynchronize(m->stream));
+    if (flag) return mfail(m, MUCAL_ERR_STATE, "tcgen05 forward: the tensor-core wait ran out");
     return MUCAL_OK;
 }
 

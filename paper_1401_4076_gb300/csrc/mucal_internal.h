@@ -104,6 +104,12 @@ cudaError_t droplet_plan(const SysParams &p, DropletPlan *plan);
 cudaError_t launch_droplets(const SysParams &p, const DropletOut &o, const DropletPlan &plan,
                             uint32_t *scratch, cudaStream_t stream);
 
+// Forward pass of the seeding network with the 128x128 layer on tcgen05
+// (mlp_tcgen05.cu): wq the bf16 parameter vector, X [B][4], y [B]; err is set
+// non-zero if a tensor-core wait ran out.
+cudaError_t mlp_forward_tcgen05(const void *wq, const float *X, float *y, int64_t B, int *err,
+                                cudaStream_t stream);
+
 // Error message of calls that have no context (mucal_host.cu).
 void set_init_error(const char *msg);
 

@@ -46,6 +46,7 @@ EXPORTED = [
     "mucal_get_largest_droplets", "mucal_reset_droplet_stats", "mucal_droplet_delta",
     "mucal_droplet_lambda", "mucal_replica_exchange", "mucal_set_tunnel_window",
     "mucal_get_tunnel_counts", "mucal_reset_tunnel_counts", "mucal_set_graph_mode",
+    "mucal_mlp_forward_tcgen05",
 ]
 
 
@@ -134,6 +135,7 @@ def load_library(path: str = LIB_PATH):
         "mucal_get_tunnel_counts": (ctypes.c_int, [P, I32, P, P, P]),
         "mucal_reset_tunnel_counts": (ctypes.c_int, [P]),
         "mucal_set_graph_mode": (ctypes.c_int, [P, I32]),
+        "mucal_mlp_forward_tcgen05": (ctypes.c_int, [P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -565,6 +567,13 @@ def mucal_mlp_forward(mlp, X):
     return y
 
 
+def mucal_mlp_forward_tcgen05(mlp, X):
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 4)
+    y = np.zeros(X.shape[0], dtype=np.float32)
+    _mlp_check(load_library().mucal_mlp_forward_tcgen05(mlp, _ptr(X), X.shape[0], _ptr(y)), mlp)
+    return y
+
+
 def mucal_mlp_gradients(mlp, X, t):
     X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 4)
     t = np.ascontiguousarray(t, dtype=np.float32)
@@ -631,6 +640,9 @@ class Mlp:
 
     def forward(self, X):
         return mucal_mlp_forward(self.h, X)
+
+    def forward_tcgen05(self, X):
+        return mucal_mlp_forward_tcgen05(self.h, X)
 
     def gradients(self, X, t):
         return mucal_mlp_gradients(self.h, X, t)
