@@ -485,6 +485,33 @@ def aux_measure(stream, device):
     except Exception as exc:
         out["exchange_error"] = repr(exc)[:200]
     try:
+        from paper_1401_4076_gb300 import workloads as wls
+        params = wls.mlp_initial_params(0)
+        X, t = wls.mlp_test_batch(8192, 1)
+        res = {}
+        for name, tc in (("tcgen05", True), ("mma_sync", False)):
+            with m.Mlp(params, cuda_stream=stream.cuda_stream) as net:
+                net.use_tcgen05(tc)
+                net.train(X, t, steps=20, lr=1e-3)
+                t0 = time.perf_counter()
+                net.train(X, t, steps=200, lr=1e-3)
+                step_ms = (time.perf_counter() - t0) / 200 * 1e3
+                net.forward(X)
+                t0 = time.perf_counter()
+                for _ in range(20):
+                    net.forward(X)
+                fwd_ms = (time.perf_counter() - t0) / 20 * 1e3
+            # flops of the three 128x128 contractions per row (forward with
+            # hi + lo: 2 x 2 H^2; backward: dH1 and dW2: 2 x 2 H^2)
+            flops = 8192 * 8 * 128 * 128
+            res[name] = {"train_step_ms": step_ms, "forward_ms_with_copies": fwd_ms,
+                         "train_tflops_effective": flops / (step_ms / 1e3) / 1e12}
+        out["seeding_network"] = dict(res, batch=8192,
+                                      note="train step = gradient kernels + Adam, host loop; "
+                                           "forward includes the host-device copies")
+    except Exception as exc:
+        out["mlp_error"] = repr(exc)[:200]
+    try:
         rng = np.random.default_rng(0)
         H = rng.integers(1, 10 ** 6, d * N + 1)
         lnW = np.cumsum(rng.normal(size=d * N + 1))

@@ -449,6 +449,13 @@ int mucal_mlp_forward(void *mlp, const float *X, int64_t B, float *y);
  * INVALID_ARG, OOM, CUDA, STATE (a tensor-core wait ran out). */
 int mucal_mlp_forward_tcgen05(void *mlp, const float *X, int64_t B, float *y);
 
+/* Select the tensor-core path of mucal_mlp_forward, mucal_mlp_gradients and
+ * mucal_mlp_train: enable = 1 runs every 128x128 contraction (Z2 = H1 W2^T,
+ * dH1 = dZ2 W2 and dW2 = dZ2^T H1 over each 128-row tile) with tcgen05.mma
+ * on tensor memory (the default); 0 uses mma.sync.  The numerics are the
+ * same (bf16 operands, fp32 accumulation) up to the order of fp32 sums. */
+int mucal_mlp_use_tcgen05(void *mlp, int32_t enable);
+
 /* One forward and backward pass of the mean squared error against t[B]:
  * loss (nullable) and the gradient with respect to all 17281 parameters
  * (grad nullable, host fp32[17281]).  Parameters are not changed. */

@@ -420,7 +420,8 @@ struct Mlp {
     int64_t cap = 0;           // rows of the batch buffers (multiple of 256)
     float *X = nullptr, *t = nullptr, *y = nullptr;
     __nv_bfloat16 *h1T = nullptr, *dz2T = nullptr;
-    int *d_err = nullptr;      // error flag of the tcgen05 forward kernel
+    int *d_err = nullptr;      // error flag of the tcgen05 kernels
+    bool use_tc = true;        // forward, gradients and training on tcgen05 (else mma.sync)
     int64_t step = 0;
     std::string err;
 };
@@ -476,10 +477,40 @@ int upload_batch(Mlp *m, const float *X, const float *t, int64_t B)
 
 size_t rows_smem() { return sizeof(MlpShared); }
 
+int ensure_err(Mlp *m)
+{
+    if (!m->d_err) {
+        MLP_TRY(m, cudaMalloc(&m->d_err, sizeof(int)));
+        MLP_TRY(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+    }
+    return MUCAL_OK;
+}
+
+// Read and clear the tcgen05 error flag (waits for the stream).
+int check_tc(Mlp *m)
+{
+    if (!m->d_err) return MUCAL_OK;
+    int flag = 0;
+    MLP_TRY(m, cudaMemcpyAsync(&flag, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MLP_TRY(m, cudaStreamSynchronize(m->stream));
+    if (flag) {
+        MLP_TRY(m, cudaMemset(m->d_err, 0, sizeof(int)));
+        return mfail(m, MUCAL_ERR_STATE, "tcgen05 kernel: a tensor-core wait ran out");
+    }
+    return MUCAL_OK;
+}
+
 int enqueue_grad(Mlp *m, int64_t B)
 {
     const int blocks = (int)((B + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
     MLP_TRY(m, cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream));
+    if (m->use_tc) {
+        int rc = ensure_err(m);
+        if (rc != MUCAL_OK) return rc;
+        MLP_TRY(m, mucal::mlp_train_tcgen05(m->wq, m->X, m->t, B, m->grad, m->loss, m->d_err,
+                                            m->stream));
+        return MUCAL_OK;
+    }
     mlp_rows_kernel<true><<<blocks, WARPS * 32, rows_smem(), m->stream>>>(
         m->wq, m->X, m->t, m->y, B, 1.0f / (float)B, m->h1T, m->dz2T, m->cap, m->grad, m->loss);
     MLP_TRY(m, cudaGetLastError());
@@ -585,9 +616,18 @@ int mucal_mlp_get_params(void *mlp, float *params, int64_t n, int32_t rounded)
     return MUCAL_OK;
 }
 
+int mucal_mlp_use_tcgen05(void *mlp, int32_t enable)
+{
+    Mlp *m = static_cast<Mlp *>(mlp);
+    if (!m) return mfail(m, MUCAL_ERR_INVALID_ARG, "mlp is NULL");
+    m->use_tc = enable != 0;
+    return MUCAL_OK;
+}
+
 int mucal_mlp_forward(void *mlp, const float *X, int64_t B, float *y)
 {
     Mlp *m = static_cast<Mlp *>(mlp);
+    if (m && m->use_tc) return mucal_mlp_forward_tcgen05(mlp, X, B, y);
     if (!m || !X || !y || B <= 0) return mfail(m, MUCAL_ERR_INVALID_ARG, "bad forward arguments");
     MLP_TRY(m, cudaSetDevice(m->device));
     int rc = upload_batch(m, X, nullptr, B);
@@ -608,15 +648,11 @@ int mucal_mlp_forward_tcgen05(void *mlp, const float *X, int64_t B, float *y)
     MLP_TRY(m, cudaSetDevice(m->device));
     int rc = upload_batch(m, X, nullptr, B);
     if (rc != MUCAL_OK) return rc;
-    if (!m->d_err) MLP_TRY(m, cudaMalloc(&m->d_err, sizeof(int)));
-    MLP_TRY(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+    rc = ensure_err(m);
+    if (rc != MUCAL_OK) return rc;
     MLP_TRY(m, mucal::mlp_forward_tcgen05(m->wq, m->X, m->y, B, m->d_err, m->stream));
-    int flag = 0;
     MLP_TRY(m, cudaMemcpyAsync(y, m->y, B * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
-    MLP_TRY(m, cudaMemcpyAsync(&flag, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
-    MLP_TRY(m, cudaStreamSynchronize(m->stream));
-    if (flag) return mfail(m, MUCAL_ERR_STATE, "tcgen05 forward: the tensor-core wait ran out");
-    return MUCAL_OK;
+    return check_tc(m);
 }
 
 int mucal_mlp_gradients(void *mlp, const float *X, const float *t, int64_t B, float *loss, float *grad)
@@ -633,7 +669,7 @@ int mucal_mlp_gradients(void *mlp, const float *X, const float *t, int64_t B, fl
     if (loss) MLP_TRY(m, cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
     MLP_TRY(m, cudaMemsetAsync(m->grad, 0, NPARAM * 4, m->stream));
     MLP_TRY(m, cudaStreamSynchronize(m->stream));
-    return MUCAL_OK;
+    return check_tc(m);
 }
 
 int mucal_mlp_train(void *mlp, const float *X, const float *t, int64_t B, int32_t steps, float lr,
@@ -659,7 +695,7 @@ int mucal_mlp_train(void *mlp, const float *X, const float *t, int64_t B, int32_
     }
     if (loss_out) MLP_TRY(m, cudaMemcpyAsync(loss_out, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
     MLP_TRY(m, cudaStreamSynchronize(m->stream));
-    return MUCAL_OK;
+    return check_tc(m);
 }
 
 }  // extern "C"

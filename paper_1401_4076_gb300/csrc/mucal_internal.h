@@ -109,6 +109,10 @@ cudaError_t launch_droplets(const SysParams &p, const DropletOut &o, const Dropl
 // non-zero if a tensor-core wait ran out.
 cudaError_t mlp_forward_tcgen05(const void *wq, const float *X, float *y, int64_t B, int *err,
                                 cudaStream_t stream);
+// Gradients of the mean squared error against target[B] added to grad
+// (fp32[17281]) and the loss added to *loss, every contraction on tcgen05.
+cudaError_t mlp_train_tcgen05(const void *wq, const float *X, const float *target, int64_t B,
+                              float *grad, float *loss, int *err, cudaStream_t stream);
 
 // Error message of calls that have no context (mucal_host.cu).
 void set_init_error(const char *msg);

@@ -46,7 +46,7 @@ EXPORTED = [
     "mucal_get_largest_droplets", "mucal_reset_droplet_stats", "mucal_droplet_delta",
     "mucal_droplet_lambda", "mucal_replica_exchange", "mucal_set_tunnel_window",
     "mucal_get_tunnel_counts", "mucal_reset_tunnel_counts", "mucal_set_graph_mode",
-    "mucal_mlp_forward_tcgen05",
+    "mucal_mlp_forward_tcgen05", "mucal_mlp_use_tcgen05",
 ]
 
 
@@ -136,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "mucal_reset_tunnel_counts": (ctypes.c_int, [P]),
         "mucal_set_graph_mode": (ctypes.c_int, [P, I32]),
         "mucal_mlp_forward_tcgen05": (ctypes.c_int, [P, P, I64, P]),
+        "mucal_mlp_use_tcgen05": (ctypes.c_int, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -643,6 +644,9 @@ class Mlp:
 
     def forward_tcgen05(self, X):
         return mucal_mlp_forward_tcgen05(self.h, X)
+
+    def use_tcgen05(self, enable=True):
+        _mlp_check(load_library().mucal_mlp_use_tcgen05(self.h, 1 if enable else 0), self.h)
 
     def gradients(self, X, t):
         return mucal_mlp_gradients(self.h, X, t)

@@ -1,6 +1,6 @@
-"""The tcgen05 forward pass of the seeding network against the mma.sync one
-and the float64 oracle (same bf16-rounded parameters).  The two GPU paths
-differ only in the order of their fp32 sums."""
+"""The tcgen05 passes of the seeding network (the default) against the
+mma.sync ones and the float64 oracle (same bf16-rounded parameters).  The
+two GPU paths differ only in the order of their fp32 sums."""
 import numpy as np
 import pytest
 
@@ -29,6 +29,7 @@ def test_tcgen05_forward_matches_mma_and_oracle(B):
         net.train(X, t, steps=200, lr=2e-3)       # weights away from their start
         Xb = X[:B]
         y_tc = net.forward_tcgen05(Xb)
+        net.use_tcgen05(False)
         y_mma = net.forward(Xb)
         q = net.params(rounded=True)
     po = {k: np.asarray(v, dtype=np.float64) for k, v in m.mlp_unflatten(q).items()}
@@ -36,3 +37,48 @@ def test_tcgen05_forward_matches_mma_and_oracle(B):
     scale = max(1.0, float(np.abs(yo).max()))
     assert np.abs(y_tc - y_mma).max() <= 1e-5 * scale
     assert np.abs(y_tc - yo).max() <= 1e-2 * scale
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12))
+
+
+@pytest.mark.parametrize("B", [50, 128, 1000, 3001])
+def test_tcgen05_gradients_match_mma_and_oracle(B):
+    params = workloads.mlp_initial_params(7)
+    X, t = workloads.mlp_test_batch(B, 8)
+    with m.Mlp(params) as net:
+        net.use_tcgen05(False)
+        loss_m, g_m = net.gradients(X, t)
+        net.use_tcgen05(True)
+        loss_t, g_t = net.gradients(X, t)
+        q = net.params(rounded=True)
+    po = {k: np.asarray(v, dtype=np.float64) for k, v in m.mlp_unflatten(q).items()}
+    lo = omlp.loss(po, X.astype(np.float64), t.astype(np.float64))
+    go = omlp.backward(po, X.astype(np.float64), t.astype(np.float64))
+    assert loss_t == pytest.approx(loss_m, rel=1e-4)
+    assert abs(loss_t - lo) <= 1e-2 * max(lo, 1e-6)
+    gt, gm = m.mlp_unflatten(g_t), m.mlp_unflatten(g_m)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a = np.asarray(gt[name], dtype=np.float64).reshape(-1)
+        b = np.asarray(gm[name], dtype=np.float64).reshape(-1)
+        o = go[name].reshape(-1)
+        assert _rel(a, b) <= 1e-2, (name, _rel(a, b))
+        assert _rel(a, o) <= 2e-2, (name, _rel(a, o))
+        cos = float(a @ o / max(np.linalg.norm(a) * np.linalg.norm(o), 1e-30))
+        assert cos >= 0.999, (name, cos)
+
+
+def test_tcgen05_training_lowers_the_loss_like_mma():
+    params = workloads.mlp_initial_params(9)
+    X, t = workloads.mlp_test_batch(2000, 10)
+    losses = {}
+    for tc in (False, True):
+        with m.Mlp(params) as net:
+            net.use_tcgen05(tc)
+            first, _ = net.gradients(X, t)
+            last = net.train(X, t, steps=300, lr=2e-3)
+            losses[tc] = (first, last)
+    for tc, (first, last) in losses.items():
+        assert last < 0.5 * first, (tc, first, last)
+    assert losses[True][1] == pytest.approx(losses[False][1], rel=0.2)
