@@ -4,9 +4,13 @@
 // weights W = 1/Omega_pred for the iteration of Sec. 2, which then runs
 // unchanged and decides convergence as before.
 //
+// This file holds the host side, the Adam update and the mma.sync kernels,
+// which are the reference path; the default path runs the contractions with
+// tcgen05 (mlp_tcgen05.cu).
+//
 // Numerics: parameters kept in fp32 (master copy, Adam state) and used in
 // bf16; the 128x128 contractions run on the tensor cores as bf16 x bf16 with
-// fp32 accumulation (mma.sync m16n8k16); the K=4 input layer, the N=1 output
+// fp32 accumulation (here mma.sync m16n8k16); the K=4 input layer, the N=1 output
 // layer, GELU and all reductions are fp32.  In the forward pass the layer-1
 // activations enter the tensor cores split into two bf16 terms (hi + lo),
 // which keeps the network's output smooth in its inputs to about 1e-5
