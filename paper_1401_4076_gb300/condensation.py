@@ -60,10 +60,15 @@ def sizes_for_deltas(d: int, N: int, deltas, L_max: int = 512):
 
 def run(d: int, N: int, Ls, walkers: int = 1024, sweeps: int = 500, max_iter: int = 1000,
         goal: float = 0.5, prod_rounds: int = 40, prod_sweeps: int = 500, thermal_rounds: int = 5,
-        seed: int = 0, windows=None, cuda_stream=None, log=None):
+        seed: int = 0, windows=None, T=None, keep_rounds=False, cuda_stream=None, log=None):
     """Iterate every system to flatness, then measure; returns one record per L.
-    windows: one (e_lo, e_hi) per L, or None to take them from tempering runs."""
-    t = TABLE1[d]
+    windows: one (e_lo, e_hi) per L, or None to take them from tempering runs.
+    T: the temperature to reweight to (default: Table 1's for d; Delta and
+    lambda always use Table 1's constants).  keep_rounds: also return every
+    production round's histogram and droplet sums (for error estimates)."""
+    t = dict(TABLE1[d])
+    if T is not None:
+        t["T"] = float(T)
     beta = 1.0 / t["T"]
     t0 = time.perf_counter()
     ranges = []
@@ -104,6 +109,8 @@ def run(d: int, N: int, Ls, walkers: int = 1024, sweeps: int = 500, max_iter: in
         # production with frozen weights
         lnW = [mc.weights(i) for i in range(n)]
         H = [np.zeros(len(w), dtype=np.int64) for w in lnW]
+        rounds = [[] for _ in range(n)]
+        prev = [None] * n
         base = max_iter + 1
         for r in range(thermal_rounds + prod_rounds):
             mc.run_iteration(prod_sweeps, base + r)
@@ -113,6 +120,12 @@ def run(d: int, N: int, Ls, walkers: int = 1024, sweeps: int = 500, max_iter: in
                 for i in range(n):
                     H[i] += mc.histogram(i)
             mc.measure_droplets()
+            if keep_rounds and r >= thermal_rounds:
+                for i in range(n):
+                    st = np.stack(mc.droplet_stats(i))
+                    d_st = st if prev[i] is None else st - prev[i]
+                    prev[i] = st
+                    rounds[i].append((mc.histogram(i), d_st))
         records = []
         stats = []
         for i, L in enumerate(Ls):
@@ -148,7 +161,8 @@ def run(d: int, N: int, Ls, walkers: int = 1024, sweeps: int = 500, max_iter: in
         r["wall_s"] = round(wall, 3)
         r["iteration_wall_s"] = round(t_iter - t_range, 3)
         r["tempering_wall_s"] = round(t_range, 3)
-    return records, {"H": H, "lnW": lnW, "droplet_stats": stats, "windows": windows}
+    return records, {"H": H, "lnW": lnW, "droplet_stats": stats, "windows": windows,
+                     "rounds": rounds if keep_rounds else None}
 
 
 def main(argv=None):

@@ -68,3 +68,20 @@ def test_condensation_with_tempering_windows():
         assert -d * N < lo < r["tempering"]["target_range"][0] and hi == 0
     a, b = sorted(recs, key=lambda r: r["Delta"])
     assert b["lambda"] > a["lambda"]
+
+
+def test_reweighted_muca_agrees_with_canonical():
+    """Fig. 2's check on a small lattice: the multicanonical pipeline
+    reweighted to T against direct canonical Metropolis at T (the fixed-N
+    lattice gas is the micromagnetic Ising model, Eq. 5): <E> and <V_D>
+    agree within five combined standard errors."""
+    from paper_1401_4076_gb300 import compare
+    d, L, N, T = 2, 12, 20, 0.8
+    recs, aux = cond.run(d, N, [L], walkers=256, sweeps=200, max_iter=400, prod_rounds=20,
+                         prod_sweeps=200, T=T, seed=21, keep_rounds=True)
+    r = recs[0]
+    assert r["converged"]
+    eE, eV = compare.muca_jackknife(aux, d, N, T)
+    c = compare.canonical(d, L, N, T, walkers=1024, sweeps=20, thermal=50, measure=100, seed=99)
+    assert abs(r["mean_E"] - c["mean_E"]) < 5 * math.hypot(eE, c["err_E"]), (r["mean_E"], c, eE)
+    assert abs(r["mean_V_D"] - c["mean_V_D"]) < 5 * math.hypot(eV, c["err_V_D"]), (r, c, eV)
