@@ -270,6 +270,29 @@ int mucal_reweight(const int64_t *H, const double *lnW, int32_t n_bins, int32_t 
                    const double *beta, int32_t n_beta, const double *obs, int32_t n_obs,
                    double *mean_E, double *mean_E2, double *obs_out);
 
+/* Multi-histogram estimate of ln Omega(E) from K histograms H[k][n_bins]
+ * sampled with log-weights lnW[k][n_bins] (for instance several iterations of
+ * Sec. 2, or several production runs): the self-consistent combination
+ *   Omega(E) = sum_k H_k(E) / sum_k N_k exp(lnW_k(E) - f_k),
+ *   exp(f_k) = sum_E Omega(E) exp(lnW_k(E)),   N_k = sum_E H_k(E),
+ * iterated from f_k = 0 (f_0 fixed to 0) until max_k |f_k change| < tol or
+ * max_iter passes.  ln_omega (host float64[n_bins]) receives ln Omega shifted
+ * to maximum 0, NaN where no histogram visited; iterations (nullable) the
+ * passes made (max_iter means the tolerance was not reached).  With K = 1 it
+ * is ln H(E) - lnW(E).  A run restricted to an energy window has weight 0
+ * outside it: pass lnW = -inf there.  Errors: INVALID_ARG (NULL arrays, sizes < 1,
+ * max_iter < 1, tol <= 0, a negative H, non-finite lnW where H > 0, all
+ * histograms empty).  Message: mucal_last_error(NULL). */
+int mucal_multi_histogram(const int64_t *H, const double *lnW, int32_t K, int32_t n_bins,
+                          int32_t max_iter, double tol, double *ln_omega, int32_t *iterations);
+
+/* The constant of Eq. 5: with s_i = 2 n_i - 1 the lattice-gas energy is
+ * H_gas = H_Ising / 4 + c(N), c(N) = J d (V/4 - N), so an energy E of the
+ * gas is E_Ising = 4 (E - c(N)) at fixed magnetisation M = 2N - V, and the
+ * Ising temperature is 4T.  Errors: INVALID_ARG (d outside {2,3}, V < 1,
+ * N outside [0, V], NULL c_N). */
+int mucal_ising_constant(int32_t d, int64_t V, int64_t N, double J, double *c_N);
+
 /* mucal_reweight of system sys's last summed histogram with the weights it
  * was sampled with (those in force at the last mucal_run_iteration, not the
  * ones a later mucal_update_weights or mucal_set_weights installed).  Waits

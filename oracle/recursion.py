@@ -115,3 +115,39 @@ def ln_omega(lnW: np.ndarray, H: np.ndarray, V: int, N: int) -> np.ndarray:
     ln_total = math.lgamma(V + 1) - math.lgamma(N + 1) - math.lgamma(V - N + 1)
     out[vis] += ln_total - lse
     return out
+
+
+def multi_histogram(H, lnW, max_iter=10000, tol=1e-12):
+    """ln Omega from several histograms H_k sampled with weights lnW_k, the
+    self-consistent multi-histogram combination: Omega(E) = sum_k H_k(E) /
+    sum_k N_k W_k(E) exp(-f_k), exp(f_k) = sum_E Omega(E) W_k(E), f_0 = 0.
+    Plain loops; returns (ln Omega shifted to max 0 with NaN where no
+    histogram visits, passes)."""
+    H = np.asarray(H, dtype=np.float64)
+    lnW = np.asarray(lnW, dtype=np.float64)
+    K, nb = H.shape
+    Nk = H.sum(axis=1)
+    num = H.sum(axis=0)
+    f = np.zeros(K)
+    lo = np.full(nb, np.nan)
+    passes = 0
+    for passes in range(1, max_iter + 1):
+        for b in range(nb):
+            if num[b] <= 0:
+                continue
+            terms = [math.log(Nk[k]) + lnW[k, b] - f[k] for k in range(K) if Nk[k] > 0]
+            mx = max(terms)
+            lo[b] = math.log(num[b]) - (mx + math.log(sum(math.exp(t - mx) for t in terms)))
+        fn = np.zeros(K)
+        for k in range(K):
+            terms = [lo[b] + lnW[k, b] for b in range(nb) if num[b] > 0]
+            mx = max(terms)
+            fn[k] = mx + math.log(sum(math.exp(t - mx) for t in terms))
+        fn -= fn[0]
+        change = np.abs(fn - f).max()
+        f = fn
+        if change < tol:
+            break
+    vis = num > 0
+    lo[vis] -= lo[vis].max()
+    return lo, passes

@@ -1,12 +1,15 @@
 // Host-side analysis of multicanonical data (Sec. 3): reweighting to
-// canonical temperatures and the infinite-volume droplet fraction of Biskup
-// et al. as the paper states it (Eqs. 8-10).  Double precision, no device
-// work: the inputs are a few hundred bins.
+// canonical temperatures, the multi-histogram combination of several
+// iterations' histograms into one ln Omega, the Ising map of Eq. 5 and the
+// infinite-volume droplet fraction of Biskup et al. as the paper states it
+// (Eqs. 8-10).  Double precision, no device work: the inputs are a few
+// hundred bins.
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <limits>
+#include <vector>
 
 #include "mucal.h"
 #include "mucal_internal.h"
@@ -85,6 +88,84 @@ int mucal_reweight(const int64_t *H, const double *lnW, int32_t n_bins, int32_t 
             obs_out[(size_t)i * n_obs + k] = zk > 0.0 ? sk / zk : nan;
         }
     }
+    return MUCAL_OK;
+}
+
+int mucal_multi_histogram(const int64_t *H, const double *lnW, int32_t K, int32_t n_bins,
+                          int32_t max_iter, double tol, double *ln_omega, int32_t *iterations)
+{
+    if (!H || !lnW || !ln_omega) return bad("H, lnW and ln_omega must not be NULL");
+    if (K < 1 || n_bins < 1) return bad("need K >= 1 and n_bins >= 1");
+    if (max_iter < 1 || !(tol > 0.0)) return bad("need max_iter >= 1 and tol > 0");
+    std::vector<double> lnN((size_t)K, -INFINITY), f((size_t)K, 0.0), fn((size_t)K, 0.0);
+    std::vector<double> num((size_t)n_bins, 0.0);
+    bool any = false;
+    for (int k = 0; k < K; ++k) {
+        double tot = 0.0;
+        for (int b = 0; b < n_bins; ++b) {
+            const int64_t h = H[(size_t)k * n_bins + b];
+            if (h < 0) return bad("H[%d][%d] is negative", k, b);
+            if (h > 0 && !std::isfinite(lnW[(size_t)k * n_bins + b]))
+                return bad("lnW[%d][%d] is not finite", k, b);
+            tot += (double)h;
+            num[b] += (double)h;
+        }
+        if (tot > 0.0) lnN[k] = std::log(tot);
+        any = any || tot > 0.0;
+    }
+    if (!any) return bad("every histogram is empty");
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    int it = 0;
+    for (it = 1; it <= max_iter; ++it) {
+        // ln Omega(E) = ln sum_k H_k(E) - ln sum_k N_k exp(lnW_k(E) - f_k)
+        for (int b = 0; b < n_bins; ++b) {
+            if (num[b] <= 0.0) {
+                ln_omega[b] = nan;
+                continue;
+            }
+            double mx = -INFINITY;
+            for (int k = 0; k < K; ++k)
+                if (std::isfinite(lnN[k])) mx = std::max(mx, lnN[k] + lnW[(size_t)k * n_bins + b] - f[k]);
+            double sden = 0.0;
+            for (int k = 0; k < K; ++k)
+                if (std::isfinite(lnN[k])) sden += std::exp(lnN[k] + lnW[(size_t)k * n_bins + b] - f[k] - mx);
+            ln_omega[b] = std::log(num[b]) - (mx + std::log(sden));
+        }
+        // f_k = ln sum_E Omega(E) exp(lnW_k(E)), shifted so that f_0 = 0
+        for (int k = 0; k < K; ++k) {
+            double mx = -INFINITY;
+            for (int b = 0; b < n_bins; ++b)
+                if (num[b] > 0.0) mx = std::max(mx, ln_omega[b] + lnW[(size_t)k * n_bins + b]);
+            double sz = 0.0;
+            for (int b = 0; b < n_bins; ++b)
+                if (num[b] > 0.0) sz += std::exp(ln_omega[b] + lnW[(size_t)k * n_bins + b] - mx);
+            fn[k] = mx + std::log(sz);
+        }
+        double delta = 0.0;
+        const double f0 = fn[0];
+        for (int k = 0; k < K; ++k) {
+            fn[k] -= f0;
+            delta = std::max(delta, std::fabs(fn[k] - f[k]));
+            f[k] = fn[k];
+        }
+        if (delta < tol) break;
+    }
+    // shift ln Omega to maximum 0
+    double mx = -INFINITY;
+    for (int b = 0; b < n_bins; ++b)
+        if (num[b] > 0.0) mx = std::max(mx, ln_omega[b]);
+    for (int b = 0; b < n_bins; ++b)
+        if (num[b] > 0.0) ln_omega[b] -= mx;
+    if (iterations) *iterations = std::min(it, max_iter);
+    return MUCAL_OK;
+}
+
+int mucal_ising_constant(int32_t d, int64_t V, int64_t N, double J, double *c_N)
+{
+    if (d != 2 && d != 3) return bad("d must be 2 or 3");
+    if (V < 1 || N < 0 || N > V) return bad("need V >= 1 and 0 <= N <= V");
+    if (!c_N) return bad("c_N is NULL");
+    *c_N = J * (double)d * ((double)V / 4.0 - (double)N);
     return MUCAL_OK;
 }
 

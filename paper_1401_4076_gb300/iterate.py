@@ -50,9 +50,24 @@ class RunResult:
     extra: dict = field(default_factory=dict)
 
 
+def ln_omega_multi(history, V: int, N: int) -> np.ndarray:
+    """ln Omega(E) from several iterations' histograms and the weights they
+    were sampled with (the multi-histogram combination of the library),
+    shifted so that the visited bins carry all C(V, N) states."""
+    H = np.stack([h for h, _ in history])
+    W = np.stack([w for _, w in history])
+    lo, _ = m.mucal_multi_histogram(H, W)
+    vis = ~np.isnan(lo)
+    mx = lo[vis].max()
+    lse = mx + math.log(np.exp(lo[vis] - mx).sum())
+    lo[vis] += ln_binomial(V, N) - lse
+    return lo
+
+
 def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None, goal=0.5,
                     scheme=m.MUCAL_SCHEME_RECURSIVE, cuda_stream=None, launch=None,
-                    final_sweeps: int = 0, relax_iters: int = 0, relax_tol: float = 0.0):
+                    final_sweeps: int = 0, relax_iters: int = 0, relax_tol: float = 0.0,
+                    history: int = 0):
     """Run the weight iteration of Sec. 2 for several systems in one context
     (one launch per iteration) until each reaches flatness >= goal inside its
     target window (t_lo, t_hi) or max_iter iterations.  A system that has
@@ -68,6 +83,10 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
     a cap and the relaxation of a system ends early once the mean energy of
     its histogram moves by less than relax_tol times the window width from
     one iteration to the next.
+
+    history: keep the histograms of the last `history` updating iterations of
+    each system with the weights they were sampled with, in
+    RunResult.extra["history"] (for ``ln_omega_multi``).
     """
     n = len(systems)
     t0 = time.perf_counter()
@@ -88,6 +107,7 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
         relaxing = [relax_iters > 0] * n
         relaxed = [0] * n
         last_mean = [None] * n
+        hist_keep = [[] for _ in range(n)]
         for it in range(max_iter):
             mc.run_iteration(sweeps, it)
             for i in range(n):
@@ -109,6 +129,9 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
                         relaxing[i] = False
                     continue
                 H = mc.histogram(i)
+                if history:
+                    hist_keep[i].append((H, mc.weights(i)))
+                    del hist_keep[i][:-history]
                 lnW, f = mc.update_weights(i, scheme)
                 flat[i].append(f)
                 Hs[i] = H
@@ -133,7 +156,7 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
         for i in range(n):
             results.append(RunResult(tuple(systems[i]), iters[i], flat[i], done[i], walls[i],
                                      lnWs[i], final_H[i] if final_sweeps else Hs[i],
-                                     attempts[i]))
+                                     attempts[i], {"history": hist_keep[i]} if history else {}))
     return results
 
 

@@ -46,7 +46,8 @@ EXPORTED = [
     "mucal_get_largest_droplets", "mucal_reset_droplet_stats", "mucal_droplet_delta",
     "mucal_droplet_lambda", "mucal_replica_exchange", "mucal_set_tunnel_window",
     "mucal_get_tunnel_counts", "mucal_reset_tunnel_counts", "mucal_set_graph_mode",
-    "mucal_mlp_forward_tcgen05", "mucal_mlp_use_tcgen05",
+    "mucal_mlp_forward_tcgen05", "mucal_mlp_use_tcgen05", "mucal_multi_histogram",
+    "mucal_ising_constant",
 ]
 
 
@@ -137,6 +138,8 @@ def load_library(path: str = LIB_PATH):
         "mucal_set_graph_mode": (ctypes.c_int, [P, I32]),
         "mucal_mlp_forward_tcgen05": (ctypes.c_int, [P, P, I64, P]),
         "mucal_mlp_use_tcgen05": (ctypes.c_int, [P, I32]),
+        "mucal_multi_histogram": (ctypes.c_int, [P, P, I32, I32, I32, ctypes.c_double, P, P]),
+        "mucal_ising_constant": (ctypes.c_int, [I32, I64, I64, ctypes.c_double, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -339,6 +342,28 @@ def mucal_reweight(H, lnW, e_lo, beta, obs=None):
     _check(load_library().mucal_reweight(_ptr(h), _ptr(w), h.size, int(e_lo), _ptr(b), b.size,
                                          _ptr(o), n_obs, _ptr(mE), _ptr(mE2), _ptr(out)), None)
     return (mE, mE2) if out is None else (mE, mE2, out)
+
+
+def mucal_multi_histogram(H, lnW, max_iter=10000, tol=1e-12):
+    """ln Omega (max 0, NaN where unvisited) from histograms H[K][n_bins]
+    sampled with lnW[K][n_bins]; returns (ln_omega, passes)."""
+    h = np.ascontiguousarray(np.atleast_2d(H), dtype=np.int64)
+    w = np.ascontiguousarray(np.atleast_2d(lnW), dtype=np.float64)
+    if h.shape != w.shape:
+        raise ValueError("H and lnW differ in shape")
+    out = np.zeros(h.shape[1])
+    it = ctypes.c_int32()
+    _check(load_library().mucal_multi_histogram(_ptr(h), _ptr(w), h.shape[0], h.shape[1],
+                                                int(max_iter), float(tol), _ptr(out),
+                                                ctypes.addressof(it)), None)
+    return out, it.value
+
+
+def mucal_ising_constant(d, V, N, J=1.0):
+    c = ctypes.c_double()
+    _check(load_library().mucal_ising_constant(int(d), int(V), int(N), float(J),
+                                               ctypes.addressof(c)), None)
+    return c.value
 
 
 def mucal_reweight_system(ctx, sys, n_bins, beta, obs=None):

@@ -155,3 +155,35 @@ def test_table1_constants_as_printed():
         t = condensation.TABLE1[int(d)]
         assert (t["T"], t["rho0"], t["kappa_hat"], t["tau_W"]) == (float(T), float(rho0), float(kap),
                                                                     float(tau))
+
+
+def test_multi_histogram_matches_oracle():
+    from oracle.recursion import multi_histogram
+    rng = np.random.default_rng(21)
+    for K, nb in ((1, 30), (3, 60), (4, 90)):
+        H = rng.integers(0, 10 ** 6, (K, nb))
+        lnW = rng.normal(scale=5.0, size=(K, nb))
+        for k in range(K):                     # each run sees a window of its own
+            lo = int(rng.integers(0, nb // 2))
+            hi = int(rng.integers(nb // 2, nb))
+            H[k, :lo] = 0
+            H[k, hi:] = 0
+            lnW[k, :lo] = -np.inf
+            lnW[k, hi:] = -np.inf
+        H[:, 7] = 0                            # a bin no run visits
+        got, passes = m.mucal_multi_histogram(H, lnW, max_iter=5000, tol=1e-13)
+        ref, ref_passes = multi_histogram(H, lnW, max_iter=5000, tol=1e-13)
+        assert np.isnan(got[7]) and np.isnan(ref[7])
+        ok = ~np.isnan(ref)
+        np.testing.assert_allclose(got[ok], ref[ok], rtol=0, atol=1e-9)
+        assert passes == ref_passes
+    with pytest.raises(m.MucalError):
+        m.mucal_multi_histogram(np.zeros((2, 5), np.int64), np.zeros((2, 5)))
+
+
+def test_ising_constant_matches_oracle():
+    for d, L, N in ((2, 4, 8), (3, 5, 40), (2, 64, 410)):
+        V = L ** d
+        assert m.mucal_ising_constant(d, V, N) == pytest.approx(muca.ising_constant(d, L, N), rel=1e-15)
+    with pytest.raises(m.MucalError):
+        m.mucal_ising_constant(4, 10, 1)

@@ -173,3 +173,31 @@ def test_reweighting_exact_from_exact_histogram():
     # infinite temperature: the plain average over all C(16, 8) states
     mean = sum(c * e for e, c in OM.items()) / math.comb(16, 8)
     assert muca.exact_moments(OM, 0.0)[0] == pytest.approx(mean, rel=1e-12)
+
+
+def test_multi_histogram_joins_windows_exactly():
+    """Two exact histograms of the 4x4, N = 8 lattice sampled with different
+    weights, each seeing only part of the energy range (as from two windows)
+    and with different total counts: the combination recovers ln Omega over
+    the union, which needs the free energies f_k to be right."""
+    from oracle.recursion import multi_histogram
+    rng = np.random.default_rng(12)
+    lnW1, lnW2 = rng.normal(size=NB), rng.normal(scale=2.0, size=NB)
+    H1 = _exact_hist(OM, lnW1, E_LO, total=1e9)
+    H2 = _exact_hist(OM, lnW2, E_LO, total=3e7)
+    H1[: -8 - E_LO] = 0.0                      # window E >= -8
+    H2[-5 - E_LO:] = 0.0                       # window E <= -6
+    # outside its window a run has weight 0: lnW = -inf there
+    w1, w2 = lnW1.copy(), lnW2.copy()
+    w1[: -8 - E_LO] = -np.inf
+    w2[-5 - E_LO:] = -np.inf
+    lo, passes = multi_histogram(np.stack([H1, H2]), np.stack([w1, w2]))
+    ideal = np.array([math.log(OM[E_LO + b]) if (E_LO + b) in OM else np.nan for b in range(NB)])
+    mask = ~np.isnan(ideal)
+    _agree_up_to_constant(lo, ideal, mask, 1e-8)
+    assert np.isnan(lo[-11 - E_LO])
+    # one histogram alone: ln H - lnW
+    lo1, _ = multi_histogram(H1[None, :], lnW1[None, :])
+    vis = H1 > 0
+    ref = np.log(H1[vis]) - lnW1[vis]
+    np.testing.assert_allclose(lo1[vis], ref - ref.max(), atol=1e-12)
