@@ -145,6 +145,9 @@ def run(d: int, N: int, Ls, walkers: int = 1024, sweeps: int = 500, max_iter: in
                    "lambda": vd / vl if vl > 0 else None,
                    "lambda_theory": m.mucal_droplet_lambda(d, D),
                    "mean_E": float(mE[0]),
+                   # the same state in Ising variables (Eq. 5): T_I = 4T, M = 2N - V
+                   "T_ising": 4.0 * t["T"], "M_ising": 2 * N - V,
+                   "mean_E_ising": 4.0 * (float(mE[0]) - m.mucal_ising_constant(d, V, N)),
                    "specific_heat_per_site": float(beta ** 2 * (mE2[0] - mE[0] ** 2) / V),
                    "window": [e_lo, e_lo + len(lnW[i]) - 1],
                    "iterations": iters[i], "converged": done[i], "flatness": flat[i],

@@ -85,3 +85,20 @@ def test_reweighted_muca_agrees_with_canonical():
     c = compare.canonical(d, L, N, T, walkers=1024, sweeps=20, thermal=50, measure=100, seed=99)
     assert abs(r["mean_E"] - c["mean_E"]) < 5 * math.hypot(eE, c["err_E"]), (r["mean_E"], c, eE)
     assert abs(r["mean_V_D"] - c["mean_V_D"]) < 5 * math.hypot(eV, c["err_V_D"]), (r, c, eV)
+
+
+def test_ising_equivalent_energy_matches_the_enumeration():
+    """4x4, N = 8 through the pipeline at T = 0.6775 (Ising beta 0.369):
+    the reported Ising energy 4 (<E> - c(N)) equals the canonical Ising
+    energy of the enumerated lattice at fixed magnetisation (Eq. 5) within
+    0.05."""
+    from oracle import chain as ochain
+    d, L, N, T = 2, 4, 8, 1.0 / (4 * 0.369)
+    recs, _ = cond.run(d, N, [L], walkers=512, sweeps=400, max_iter=300, prod_rounds=10,
+                       prod_sweeps=2000, T=T, seed=5, windows=[(-16, 0)])
+    r = recs[0]
+    assert r["converged"] and r["M_ising"] == 0 and r["T_ising"] == pytest.approx(1 / 0.369)
+    omega = ochain.enumerate_omega(d, L, N)
+    exact_gas = muca.exact_moments(omega, 1.0 / T)[0]
+    exact_ising = 4.0 * (exact_gas - muca.ising_constant(d, L, N))
+    assert r["mean_E_ising"] == pytest.approx(exact_ising, abs=0.05)
