@@ -201,3 +201,30 @@ def test_multi_histogram_joins_windows_exactly():
     vis = H1 > 0
     ref = np.log(H1[vis]) - lnW1[vis]
     np.testing.assert_allclose(lo1[vis], ref - ref.max(), atol=1e-12)
+
+
+def test_reweight_observable_is_canonical_enumeration():
+    """An exact multicanonical histogram with the microcanonical mean of the
+    largest droplet per energy, reweighted (Sec. 3), equals the canonical
+    average of the largest droplet over all C(16, 8) configurations."""
+    from itertools import combinations
+    d, L, N, V = 2, 4, 8, 16
+    per_e = {}
+    configs = []
+    for combo in combinations(range(V), N):
+        occ = np.zeros(V, np.uint8)
+        occ[list(combo)] = 1
+        e = chain.energy(d, L, occ)
+        vd = chain.largest_droplet(d, L, occ)
+        configs.append((e, vd))
+        per_e.setdefault(e, []).append(vd)
+    rng = np.random.default_rng(6)
+    lnW = rng.normal(size=NB)
+    H = _exact_hist(OM, lnW, E_LO)
+    obs = np.full(NB, np.nan)
+    for e, v in per_e.items():
+        obs[e - E_LO] = sum(v) / len(v)
+    for beta in (0.0, 1.0, 2.5):
+        w = np.array([math.exp(-beta * e) for e, _ in configs])
+        ref = float((w * np.array([v for _, v in configs])).sum() / w.sum())
+        assert muca.reweight_observable(lnW, H, E_LO, beta, obs) == pytest.approx(ref, rel=1e-10)
