@@ -243,7 +243,7 @@ def main(argv=None):
     ap.add_argument("--smem", type=int, default=-1)
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run after the warm-up steps)")
-    ap.add_argument("--tune-sweeps", type=int, default=10)
+    ap.add_argument("--tune-sweeps", type=int, default=20)
     ap.add_argument("--prerun", type=int, default=0,
                     help="untimed iterations of the recursion before the warm-up (to measure "
                          "a later stage of the weight iteration; 0 = start at lnW = 0)")
@@ -318,7 +318,7 @@ def main(argv=None):
     if not args.no_autotune and not explicit:
         from paper_1401_4076_gb300.autotune import autotune
         lnWs = [mc.weights(s) for s in range(len(systems))]
-        best, table = autotune(systems, lnW=lnWs, sweeps=args.tune_sweeps,
+        best, table = autotune(systems, lnW=lnWs, sweeps=args.tune_sweeps, repeats=5,
                                cuda_stream=stream.cuda_stream)
         mc.set_launch(**best)
         args.launch_desc = mc.launch()
