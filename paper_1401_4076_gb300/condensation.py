@@ -4,8 +4,9 @@ For a fixed particle number N the density is varied through the lattice size
 L.  Each system's energy window comes from a short parallel-tempering run
 around the Table 1 temperature (``tempering.energy_range``) unless given;
 every system runs the multicanonical iteration of Sec. 2 over its window
-until its histogram is flat over the energies the tempering replica at that
-temperature visited, then a production phase with the
+until its histogram is flat from the low end of the coldest tempering
+replicas to the top of the energies the replica at that temperature visited,
+then a production phase with the
 weights frozen: after every production iteration the device labels the
 clusters of every walker (the largest droplet V_D) and accumulates V_D per
 energy.  The histograms and the microcanonical means <V_D>(E) are reweighted
@@ -84,11 +85,12 @@ def run(d: int, N: int, Ls, walkers: int = 1024, sweeps: int = 500, max_iter: in
                for i, L in enumerate(Ls)]
     n = len(systems)
     with m.Mucal(systems, cuda_stream=cuda_stream) as mc:
-        # flatness is judged on the range the tempering replica at T visited,
-        # so a system is not declared converged before its walkers reach the
-        # condensed side of that range
+        # flatness is judged from the energy below which the coldest tempering
+        # replicas spent 1 % of their time up to the top of the range the
+        # replica at T visited, so a system is not declared converged before
+        # its walkers sample the condensed states that matter at T
         for i, info in enumerate(ranges):
-            mc.set_target_window(i, info["target_min"], info["target_max"])
+            mc.set_target_window(i, min(info["target_min"], info["cold_q01"]), info["target_max"])
         done = [False] * n
         iters = [max_iter] * n
         flat = [-1.0] * n

@@ -56,7 +56,11 @@ def energy_range(d: int, L: int, N: int, T: float, walkers: int = 256, n_temps: 
     tv = np.nonzero(H[j])[0]
     pad = max(2, int(round(margin * d * N)))
     lo = max(e_lo_full, cold_min - pad)
+    # the energy below which the coldest replicas spent 1 % of their time
+    cdf = np.cumsum(H[0]) / max(1, H[0].sum())
+    cold_q01 = e_lo_full + int(np.searchsorted(cdf, 0.01))
     info = {"betas": betas.tolist(), "accepted_exchanges": acc.tolist(),
+            "cold_q01": cold_q01,
             "exchange_proposals_per_pair": (rounds // 2) * walkers,
             "cold_min": cold_min, "target_min": e_lo_full + int(tv.min()),
             "target_max": e_lo_full + int(tv.max())}
