@@ -61,6 +61,7 @@ def energy_range(d: int, L: int, N: int, T: float, walkers: int = 256, n_temps: 
     cold_q01 = e_lo_full + int(np.searchsorted(cdf, 0.01))
     info = {"betas": betas.tolist(), "accepted_exchanges": acc.tolist(),
             "cold_q01": cold_q01,
+            "hot_max": e_lo_full + int(np.nonzero(H[-1])[0].max()),
             "exchange_proposals_per_pair": (rounds // 2) * walkers,
             "cold_min": cold_min, "target_min": e_lo_full + int(tv.min()),
             "target_max": e_lo_full + int(tv.max())}

@@ -176,3 +176,33 @@ def test_multi_histogram_ln_omega_from_iterations():
     lo = iterate.ln_omega_multi(res.extra["history"], 16, 8)
     for e, c in omega.items():
         assert abs(lo[e + 16] - math.log(c)) < 0.02, (e, lo[e + 16], math.log(c))
+
+
+def test_production_curve_against_enumeration():
+    """4x4, N = 8: flat weights, production with droplet measurements, then
+    <E>, the specific heat and <V_D> reweighted to a grid of temperatures,
+    against the canonical sums over all C(16, 8) configurations."""
+    import math
+    from itertools import combinations
+    from paper_1401_4076_gb300 import production
+    d, L, N, V = 2, 4, 8, 16
+    temps = [0.4, 0.7, 1.0, 2.0]
+    res = production.run((d, L, N, 512, 0, 0, 17), temps, sweeps=400, max_iter=100,
+                         prod_rounds=20, prod_sweeps=1000, target=(-12, 0))
+    assert res["converged"]
+    cfg = []
+    for combo in combinations(range(V), N):
+        occ = np.zeros(V, np.uint8)
+        occ[list(combo)] = 1
+        cfg.append((chain.energy(d, L, occ), chain.largest_droplet(d, L, occ)))
+    E = np.array([e for e, _ in cfg], float)
+    D = np.array([v for _, v in cfg], float)
+    for row in res["curve"]:
+        w = np.exp(-(E - E.min()) / row["T"])
+        e1 = (w * E).sum() / w.sum()
+        e2 = (w * E * E).sum() / w.sum()
+        cv = (e2 - e1 * e1) / (row["T"] ** 2 * V)
+        assert row["mean_E"] == pytest.approx(e1, abs=0.03), row
+        assert row["specific_heat_per_site"] == pytest.approx(cv, rel=0.05, abs=2e-3), row
+        assert row["mean_V_D"] == pytest.approx((w * D).sum() / w.sum(), abs=0.05), row
+        assert row["mean_E_ising"] == pytest.approx(4 * (row["mean_E"] - muca.ising_constant(d, L, N)))
