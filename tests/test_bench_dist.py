@@ -7,7 +7,6 @@ maximum over ranks, and the CPU reference arm runs on rank 0 only.
 import os
 import socket
 
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 

@@ -9,7 +9,6 @@ enumerated lattice (Eq. 1).  A wrong sign or a wrong pairing breaks that.
 import math
 
 import numpy as np
-import pytest
 
 from oracle import chain
 
