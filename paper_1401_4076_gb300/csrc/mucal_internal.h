@@ -72,10 +72,16 @@ cudaError_t walker_update_grid(const LaunchShape &shape, bool tunnel, int n_item
 cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_work, int n_items,
                                  const LaunchShape &shape, uint64_t sweeps, uint32_t iteration,
                                  bool tunnel, int grid, int *next_item, cudaStream_t stream);
-// The tunnelling flavour (walker_kernels_tun.cu): its kernel of a launch
-// shape and all its 24 kernels (for their shared-memory attributes).
+// The other three flavours of the walker update, one translation unit each
+// (walker_kernels_tun.cu, walker_kernels_persist.cu,
+// walker_kernels_persist_tun.cu): the kernel of a launch shape and all 24
+// kernels of the flavour (for their shared-memory attributes).
 const void *walker_update_fn_tunnel(const LaunchShape &shape);
 void walker_update_tunnel_fns(const void *(&fns)[24]);
+const void *walker_update_fn_persist(const LaunchShape &shape);
+void walker_update_persist_fns(const void *(&fns)[24]);
+const void *walker_update_fn_persist_tun(const LaunchShape &shape);
+void walker_update_persist_tun_fns(const void *(&fns)[24]);
 // Shared-memory layout of a walker-update block: [threshold table][bitsets].
 size_t thr_smem_words(const SysParams &p);
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,

@@ -1,6 +1,7 @@
-// Device code of the walker update shared by the two translation units that
-// instantiate it: walker_kernels.cu (plain) and walker_kernels_tun.cu (with
-// tunnelling bookkeeping).  Everything here has internal linkage; each unit
+// Device code of the walker update shared by the translation units that
+// instantiate it: walker_kernels.cu (plain), walker_kernels_tun.cu (with
+// tunnelling bookkeeping), walker_kernels_persist.cu and
+// walker_kernels_persist_tun.cu (persistent launches).  Everything here has internal linkage; each unit
 // gets its own copy of what it instantiates.
 //
 // The walker update is integer work with a serial dependency per walker
@@ -14,6 +15,9 @@
 //     against the updated state, so the chain is exactly the one-thread chain.
 // TUN = true adds the tunnelling bookkeeping (Sec. 4): every energy a walker
 // takes is compared with the two ends of SysParams::tun_lo/tun_hi.
+// PERSIST = true makes the launch persistent (see next_work_item).  Each of
+// the four (TUN, PERSIST) flavours is instantiated in a translation unit of
+// its own so that they compile in parallel.
 #pragma once
 
 #include <cstdint>
@@ -273,6 +277,13 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    // A later lane whose slot the commit moved is found either by comparing
+    // slot indices (k, m against the committing lane's, one more shuffle) or
+    // by comparing sites (a, b, no extra shuffle).  Both find the same lanes;
+    // which is faster depends on the code the compiler makes of the loop:
+    // measured on GB300, the slot compare for G = 8, the site compare for
+    // G = 4 and G = 16.
+    constexpr bool kFixBySlot = (G == 8);
     const int lane = threadIdx.x & 31;
     const int j = lane & (G - 1);
     const int gbase = lane - j;
@@ -349,9 +360,9 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
             const int f = bal ? __ffs(bal) - 1 : G;
             const int src = gbase + (f < G ? f : 0);
             const int de_f = __shfl_sync(FULL, de, src);
-            uint32_t a_f, b_f, k_f, m_f;
+            uint32_t a_f, b_f, k_f = 0, m_f = 0;
             shfl_pair<IdxT>(a, b, src, a_f, b_f);
-            shfl_pair<IdxT>(k, m, src, k_f, m_f);
+            if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
             const bool commit = !done && f < G;       // the same in every lane of the group
             const bool finish = !done && f >= G;
             if (commit && j == f) {
@@ -366,10 +377,12 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
                 *pm = (IdxT)a;
             }
             __syncwarp(FULL);
-            // the commit moved list slots k_f and N + m_f
+            // the commit moved list slots k_f and N + m_f: slot k_f held a_f and
+            // slot N + m_f held b_f, and every site sits in exactly one slot,
+            // so a lane's slot k is k_f exactly when its (current) a is a_f
             const bool later = commit && j > f;
-            const bool fix_a = later && k == k_f;
-            const bool fix_b = later && m == m_f;
+            const bool fix_a = later && (kFixBySlot ? k == k_f : a == a_f);
+            const bool fix_b = later && (kFixBySlot ? m == m_f : b == b_f);
             if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
                 a = fix_a ? b_f : a;
                 b = fix_b ? a_f : b;
@@ -398,8 +411,8 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
             row += moved ? de_f * width : 0;
             run = moved ? 0u : run;
             run += commit ? 1u : 0u;
-            an = (commit && kn == k_f) ? b_f : an;
-            bn = (commit && mn == m_f) ? a_f : bn;
+            an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
+            bn = (commit && (kFixBySlot ? mn == m_f : bn == b_f)) ? a_f : bn;
             pos = commit ? f + 1 : pos;
             done = done || finish || (commit && f + 1 >= n_valid);
         }
@@ -433,7 +446,7 @@ constexpr int kThreadPipe = 6;
 template <int D, typename IdxT, bool SB, bool ST, bool TUN>
 __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t *bits,
                                              const uint32_t *thr, unsigned long long *hist,
-                                             uint64_t A, uint32_t iter)
+                                             uint64_t A, uint32_t iter, uint32_t *s_tun)
 {
     constexpr int PF = kThreadPipe;
     IdxT *S = walker_S<IdxT>(p, w);
@@ -449,9 +462,8 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
     uint32_t acc = 0;
     // tunnelling bookkeeping (TUN only): every energy the walker takes is
     // checked against the two ends.  State in bits 0-1, events in the bits
-    // above, kept in shared memory (the pipeline ring already fills the
-    // registers) and touched on moves only.
-    __shared__ uint32_t s_tun[TUN ? kGroupMaxThreads : 1];
+    // above, kept in this thread's word of the kernel's shared array s_tun
+    // (the pipeline ring already fills the registers), touched on moves only.
     if constexpr (TUN) s_tun[threadIdx.x] = p.tun_state ? p.tun_state[w] : 0u;
     auto tunnel = [&](int b_now) {
         if (b_now <= p.tun_lo) {
@@ -555,9 +567,9 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
     }
 }
 
-// Work items of a launch: block b takes item b; with next_item non-NULL the
-// launch is persistent (fewer blocks than items) and a block that finishes
-// an item takes the next one from the counter (which starts at 0).
+// Work items of a launch: block b takes item b.  The persistent flavour
+// (PERSIST) launches fewer blocks than items; a block that finishes an item
+// takes the next one from the counter next_item (which starts at 0).
 __device__ __forceinline__ int next_work_item(int *next_item, int *s_item)
 {
     __syncthreads();   // the item's shared memory and *s_item are reused
@@ -566,15 +578,15 @@ __device__ __forceinline__ int next_work_item(int *next_item, int *s_item)
     return *s_item;
 }
 
-template <bool SB, bool ST, bool TUN>
+template <bool SB, bool ST, bool TUN, bool PERSIST>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
                      uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ int s_item;
-    for (int item = blockIdx.x; item < n_items;) {
-        const BlockWork wk = work[item];
+    __shared__ uint32_t s_tun[TUN ? kGroupMaxThreads : 1];   // tunnelling words, one per thread
+    // one work item per block, or (PERSIST) items pulled from the counter
+    auto item_body = [&](const BlockWork &wk) {
         const SysParams &p = sys[wk.sys];
         const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
         const int lw = threadIdx.x;
@@ -587,16 +599,25 @@ walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restr
             unsigned long long *hist = hist_row(p, w, wk.hist_row);
             const uint64_t A = sweeps * (uint64_t)p.N;
             if (p.d == 2) {
-                if (p.idx16) chain_thread<2, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
-                else chain_thread<2, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+                if (p.idx16) chain_thread<2, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter, s_tun);
+                else chain_thread<2, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter, s_tun);
             } else {
-                if (p.idx16) chain_thread<3, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
-                else chain_thread<3, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter);
+                if (p.idx16) chain_thread<3, uint16_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter, s_tun);
+                else chain_thread<3, uint32_t, SB, ST, TUN>(p, w, bits, thr, hist, A, iter, s_tun);
             }
         }
         block_finish(bs, SB ? 1 : 0);
-        if (!next_item) break;
-        item = next_work_item(next_item, &s_item);
+    };
+    if constexpr (!PERSIST) {
+        (void)n_items;
+        (void)next_item;
+        item_body(work[blockIdx.x]);
+    } else {
+        __shared__ int s_item;
+        for (int item = blockIdx.x; item < n_items;) {
+            item_body(work[item]);
+            item = next_work_item(next_item, &s_item);
+        }
     }
 }
 
@@ -622,68 +643,80 @@ __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &
     }
 }
 
-template <int G, bool SB, bool ST, bool TUN>
+template <int G, bool SB, bool ST, bool TUN, bool PERSIST>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
                     uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ int s_item;
-    for (int item = blockIdx.x; item < n_items;) {
-        const BlockWork wk = work[item];
+    if constexpr (!PERSIST) {
+        // one work item per block
+        (void)n_items;
+        (void)next_item;
+        const BlockWork wk = work[blockIdx.x];
         const SysParams &p = sys[wk.sys];
         const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
         group_body<G, SB, ST, TUN>(p, wk, smem, sweeps, iter);
         block_finish(bs, SB ? 1 : 0);
-        if (!next_item) break;
-        item = next_work_item(next_item, &s_item);
+    } else {
+        __shared__ int s_item;
+        for (int item = blockIdx.x; item < n_items;) {
+            const BlockWork wk = work[item];
+            const SysParams &p = sys[wk.sys];
+            const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
+            group_body<G, SB, ST, TUN>(p, wk, smem, sweeps, iter);
+            block_finish(bs, SB ? 1 : 0);
+            item = next_work_item(next_item, &s_item);
+        }
     }
 }
 
 // The walker-update kernel of a launch shape (one TUN flavour).
-template <int G, bool TUN>
+template <int G, bool TUN, bool PE>
 const void *group_fn(const LaunchShape &sh)
 {
-    if (sh.bits_in_smem && sh.thr_in_smem) return (const void *)walker_update_group<G, true, true, TUN>;
-    if (sh.bits_in_smem) return (const void *)walker_update_group<G, true, false, TUN>;
-    if (sh.thr_in_smem) return (const void *)walker_update_group<G, false, true, TUN>;
-    return (const void *)walker_update_group<G, false, false, TUN>;
+    if (sh.bits_in_smem && sh.thr_in_smem) return (const void *)walker_update_group<G, true, true, TUN, PE>;
+    if (sh.bits_in_smem) return (const void *)walker_update_group<G, true, false, TUN, PE>;
+    if (sh.thr_in_smem) return (const void *)walker_update_group<G, false, true, TUN, PE>;
+    return (const void *)walker_update_group<G, false, false, TUN, PE>;
 }
 
-template <bool TUN>
+// The kernel of a launch shape among the 24 of one (TUN, PE) flavour
+// (PE: persistent launch); the caller checks that shape.persistent == PE.
+template <bool TUN, bool PE>
 const void *walker_update_fn_t(const LaunchShape &sh)
 {
     if (sh.kernel == 0) {
-        if (sh.bits_in_smem && sh.thr_in_smem) return (const void *)walker_update_thread<true, true, TUN>;
-        if (sh.bits_in_smem) return (const void *)walker_update_thread<true, false, TUN>;
-        if (sh.thr_in_smem) return (const void *)walker_update_thread<false, true, TUN>;
-        return (const void *)walker_update_thread<false, false, TUN>;
+        if (sh.bits_in_smem && sh.thr_in_smem) return (const void *)walker_update_thread<true, true, TUN, PE>;
+        if (sh.bits_in_smem) return (const void *)walker_update_thread<true, false, TUN, PE>;
+        if (sh.thr_in_smem) return (const void *)walker_update_thread<false, true, TUN, PE>;
+        return (const void *)walker_update_thread<false, false, TUN, PE>;
     }
     switch (sh.lanes) {
-    case 2: return group_fn<2, TUN>(sh);
-    case 4: return group_fn<4, TUN>(sh);
-    case 8: return group_fn<8, TUN>(sh);
-    case 16: return group_fn<16, TUN>(sh);
-    case 32: return group_fn<32, TUN>(sh);
+    case 2: return group_fn<2, TUN, PE>(sh);
+    case 4: return group_fn<4, TUN, PE>(sh);
+    case 8: return group_fn<8, TUN, PE>(sh);
+    case 16: return group_fn<16, TUN, PE>(sh);
+    case 32: return group_fn<32, TUN, PE>(sh);
     default: return nullptr;
     }
 }
 
-// Every walker-update kernel of one TUN flavour (for their shared-memory
-// attributes).
-template <bool TUN>
+// Every walker-update kernel of one (TUN, PE) flavour (for their
+// shared-memory attributes).
+template <bool TUN, bool PE>
 void walker_update_fns(const void *(&fns)[24])
 {
     int i = 0;
-    fns[i++] = (const void *)walker_update_thread<true, true, TUN>;
-    fns[i++] = (const void *)walker_update_thread<true, false, TUN>;
-    fns[i++] = (const void *)walker_update_thread<false, true, TUN>;
-    fns[i++] = (const void *)walker_update_thread<false, false, TUN>;
-#define MUCAL_GROUP_FNS(G)                                               \
-    fns[i++] = (const void *)walker_update_group<G, true, true, TUN>;   \
-    fns[i++] = (const void *)walker_update_group<G, true, false, TUN>;  \
-    fns[i++] = (const void *)walker_update_group<G, false, true, TUN>;  \
-    fns[i++] = (const void *)walker_update_group<G, false, false, TUN>;
+    fns[i++] = (const void *)walker_update_thread<true, true, TUN, PE>;
+    fns[i++] = (const void *)walker_update_thread<true, false, TUN, PE>;
+    fns[i++] = (const void *)walker_update_thread<false, true, TUN, PE>;
+    fns[i++] = (const void *)walker_update_thread<false, false, TUN, PE>;
+#define MUCAL_GROUP_FNS(G)                                                   \
+    fns[i++] = (const void *)walker_update_group<G, true, true, TUN, PE>;   \
+    fns[i++] = (const void *)walker_update_group<G, true, false, TUN, PE>;  \
+    fns[i++] = (const void *)walker_update_group<G, false, true, TUN, PE>;  \
+    fns[i++] = (const void *)walker_update_group<G, false, false, TUN, PE>;
     MUCAL_GROUP_FNS(2)
     MUCAL_GROUP_FNS(4)
     MUCAL_GROUP_FNS(8)

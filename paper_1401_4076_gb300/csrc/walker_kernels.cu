@@ -219,14 +219,14 @@ cudaError_t walker_update_max_smem(int *bytes)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const void *plain[24], *tun[24];
-    walker_update_fns<false>(plain);
-    walker_update_tunnel_fns(tun);
-    const void *fns[48];
-    for (int i = 0; i < 24; ++i) {
-        fns[i] = plain[i];
-        fns[24 + i] = tun[i];
-    }
+    const void *fl[4][24];
+    walker_update_fns<false, false>(fl[0]);
+    walker_update_tunnel_fns(fl[1]);
+    walker_update_persist_fns(fl[2]);
+    walker_update_persist_tun_fns(fl[3]);
+    const void *fns[96];
+    for (int f = 0; f < 4; ++f)
+        for (int i = 0; i < 24; ++i) fns[24 * f + i] = fl[f][i];
     // the dynamic limit leaves room for the largest static shared array (the
     // thread kernel's tunnelling words)
     size_t max_static = 0;
@@ -246,7 +246,9 @@ cudaError_t walker_update_max_smem(int *bytes)
 
 const void *walker_update_fn(const LaunchShape &shape, bool tunnel)
 {
-    return tunnel ? walker_update_fn_tunnel(shape) : walker_update_fn_t<false>(shape);
+    if (shape.persistent)
+        return tunnel ? walker_update_fn_persist_tun(shape) : walker_update_fn_persist(shape);
+    return tunnel ? walker_update_fn_tunnel(shape) : walker_update_fn_t<false, false>(shape);
 }
 
 cudaError_t walker_update_grid(const LaunchShape &shape, bool tunnel, int n_items, int *grid)
