@@ -87,6 +87,13 @@ extern "C" {
  * re-evaluating after every accepted move, so the chain is identical to the
  * one-thread chain. */
 #define MUCAL_KERNEL_GROUP      1
+/* The group kernel with a local field: each walker of a block keeps the
+ * number of occupied neighbours of every site (one byte per site) in shared
+ * memory, so an attempt reads two counts instead of 2*2d occupation bits and
+ * a commit updates the 2*2d counts around the two sites.  Same chain as the
+ * other two; needs V bytes (rounded up to 16) of shared memory per walker of
+ * a block, so it suits lattices up to a few thousand sites. */
+#define MUCAL_KERNEL_FIELD      2
 
 typedef struct mucal_system_desc {
     int32_t d;          /* lattice dimension, 2 or 3 */
@@ -99,12 +106,13 @@ typedef struct mucal_system_desc {
 } mucal_system_desc;
 
 typedef struct mucal_launch_config {
-    int32_t kernel;            /* MUCAL_KERNEL_THREAD or MUCAL_KERNEL_GROUP */
-    int32_t lanes_per_walker;  /* 1 for THREAD; 2, 4, 8, 16 or 32 for GROUP */
+    int32_t kernel;            /* MUCAL_KERNEL_THREAD, _GROUP or _FIELD */
+    int32_t lanes_per_walker;  /* 1 for THREAD; 2, 4, 8, 16 or 32 for GROUP and FIELD */
     int32_t walkers_per_block; /* threads per block = walkers_per_block * lanes: <= 512;
-                                  a multiple of 32 for GROUP */
+                                  a multiple of 32 for GROUP and FIELD */
     int32_t bits_in_smem;      /* 1: stage each walker's occupation bitset in shared
-                                  memory for the launch; 0: use it in global memory */
+                                  memory for the launch; 0: use it in global memory.
+                                  FIELD keeps its counts in shared memory and needs 1 */
     int32_t persistent;        /* 1: launch only the blocks that fit on the device at
                                   once; each pulls the next block of walkers from a
                                   counter when it finishes one.  0: one block per block

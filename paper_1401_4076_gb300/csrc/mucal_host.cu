@@ -291,7 +291,10 @@ size_t smem_for(const LaunchShape &sh, const SysParams &p)
 {
     size_t bytes = 0;
     if (sh.thr_in_smem) bytes += mucal::thr_smem_words(p) * sizeof(uint32_t);
-    if (sh.bits_in_smem) bytes += (size_t)sh.walkers_per_block * (size_t)p.words * sizeof(uint32_t);
+    if (sh.kernel == MUCAL_KERNEL_FIELD)
+        bytes += (size_t)sh.walkers_per_block * mucal::field_smem_bytes(p);
+    else if (sh.bits_in_smem)
+        bytes += (size_t)sh.walkers_per_block * (size_t)p.words * sizeof(uint32_t);
     return bytes;
 }
 
@@ -365,13 +368,17 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
             return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
         if (sh.walkers_per_block > 512)
             return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel blocks hold at most 512 threads");
-    } else if (sh.kernel == MUCAL_KERNEL_GROUP) {
+    } else if (sh.kernel == MUCAL_KERNEL_GROUP || sh.kernel == MUCAL_KERNEL_FIELD) {
+        const char *name = sh.kernel == MUCAL_KERNEL_GROUP ? "GROUP" : "FIELD";
         if (sh.lanes != 2 && sh.lanes != 4 && sh.lanes != 8 && sh.lanes != 16 && sh.lanes != 32)
-            return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel needs lanes_per_walker in {2,4,8,16,32}");
+            return fail(c, MUCAL_ERR_INVALID_ARG, "%s kernel needs lanes_per_walker in {2,4,8,16,32}", name);
         if ((sh.walkers_per_block * sh.lanes) % 32 != 0)
-            return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel needs whole warps per block");
+            return fail(c, MUCAL_ERR_INVALID_ARG, "%s kernel needs whole warps per block", name);
         if (sh.walkers_per_block * sh.lanes > 512)
-            return fail(c, MUCAL_ERR_INVALID_ARG, "GROUP kernel blocks hold at most 512 threads");
+            return fail(c, MUCAL_ERR_INVALID_ARG, "%s kernel blocks hold at most 512 threads", name);
+        if (sh.kernel == MUCAL_KERNEL_FIELD && !sh.bits_in_smem)
+            return fail(c, MUCAL_ERR_INVALID_ARG, "FIELD kernel keeps its counts in shared memory: "
+                                                  "bits_in_smem must be 1");
     } else {
         return fail(c, MUCAL_ERR_INVALID_ARG, "unknown kernel %d", sh.kernel);
     }

@@ -44,8 +44,13 @@ struct BlockWork {
     int32_t hist_row;   // this block's histogram row when rows are per block, else -1
 };
 
+// Walker-update kernels of one (tunnelling, persistent) flavour: the thread
+// kernel and the group kernel in their shared-memory variants, and the
+// field kernel with and without the threshold table in shared memory.
+constexpr int kWalkerUpdateFns = 4 + 5 * 4 + 5 * 2;
+
 struct LaunchShape {
-    int kernel;             // MUCAL_KERNEL_THREAD / MUCAL_KERNEL_GROUP
+    int kernel;             // MUCAL_KERNEL_THREAD / _GROUP / _FIELD
     int lanes;              // lanes per walker
     int walkers_per_block;
     int bits_in_smem;
@@ -77,13 +82,15 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
 // walker_kernels_persist_tun.cu): the kernel of a launch shape and all 24
 // kernels of the flavour (for their shared-memory attributes).
 const void *walker_update_fn_tunnel(const LaunchShape &shape);
-void walker_update_tunnel_fns(const void *(&fns)[24]);
+void walker_update_tunnel_fns(const void *(&fns)[kWalkerUpdateFns]);
 const void *walker_update_fn_persist(const LaunchShape &shape);
-void walker_update_persist_fns(const void *(&fns)[24]);
+void walker_update_persist_fns(const void *(&fns)[kWalkerUpdateFns]);
 const void *walker_update_fn_persist_tun(const LaunchShape &shape);
-void walker_update_persist_tun_fns(const void *(&fns)[24]);
+void walker_update_persist_tun_fns(const void *(&fns)[kWalkerUpdateFns]);
 // Shared-memory layout of a walker-update block: [threshold table][bitsets].
 size_t thr_smem_words(const SysParams &p);
+// Shared-memory bytes of one walker's neighbour-count field (field kernel).
+size_t field_smem_bytes(const SysParams &p);
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                cudaStream_t stream);
 cudaError_t walker_update_max_smem(int *bytes);

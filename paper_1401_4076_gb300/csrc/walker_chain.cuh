@@ -433,6 +433,204 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
 }
 
 // ---------------------------------------------------------------------------
+// Local-field variant of the group kernel (MUCAL_KERNEL_FIELD).  Every walker
+// of the block keeps one byte per site in shared memory: the number of
+// occupied neighbours of that site (0 .. 2d).  An attempt's energy change is
+// then c[a] - c[b] + [a is a neighbour of b] (a is still occupied when b is
+// examined), two byte loads instead of the 2*2d occupation bits, and a commit
+// adds -1 to the counts of a's neighbours and +1 to those of b's.  Rounds,
+// commits and bookkeeping are those of chain_group, so the chain is the same
+// one.  The field is built from the particle list when a block starts and the
+// occupation bitset is rebuilt from the list when it ends; the bitset is not
+// touched in between.
+// ---------------------------------------------------------------------------
+template <int D>
+struct FieldMove {
+    uint32_t ca, cb;     // shared byte addresses of c[a] and c[b]
+    int adj;             // 1 if b is a neighbour of a
+    uint32_t ua[4 * D];  // shared word addresses of the 2*2d counts a commit changes
+    uint32_t uv[4 * D];  // what the commit adds there: -1 or +1 in the site's byte
+
+    __device__ __forceinline__ void build(const SysParams &p, uint32_t fbase, uint32_t a, uint32_t b)
+    {
+        uint32_t na[2 * D], nb[2 * D];
+        neighbours<D>(p, a, na);
+        neighbours<D>(p, b, nb);
+        ca = fbase + a;
+        cb = fbase + b;
+        adj = 0;
+#pragma unroll
+        for (int i = 0; i < 2 * D; ++i) {
+            adj |= (na[i] == b) ? 1 : 0;
+            ua[i] = fbase + (na[i] & ~3u);
+            uv[i] = 0u - (1u << ((na[i] & 3u) << 3));
+            ua[2 * D + i] = fbase + (nb[i] & ~3u);
+            uv[2 * D + i] = 1u << ((nb[i] & 3u) << 3);
+        }
+    }
+
+    __device__ __forceinline__ void load(uint32_t &va, uint32_t &vb) const
+    {
+        asm volatile("ld.shared.u8 %0, [%1];" : "=r"(va) : "r"(ca) : "memory");
+        asm volatile("ld.shared.u8 %0, [%1];" : "=r"(vb) : "r"(cb) : "memory");
+    }
+
+    // Byte counts stay in [0, 2d]: a decrement meets a count that includes
+    // the leaving particle, so no borrow or carry crosses a byte.
+    __device__ __forceinline__ void commit() const
+    {
+#pragma unroll
+        for (int i = 0; i < 4 * D; ++i)
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(ua[i]), "r"(uv[i]) : "memory");
+    }
+};
+
+template <int D, typename IdxT, int G, bool ST, bool TUN>
+__device__ __forceinline__ void chain_field(const SysParams &p, int w, bool active, uint32_t fbase,
+                                            const uint32_t *thr, unsigned long long *hist,
+                                            uint64_t A, uint32_t iter)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    // A later lane whose slot the commit moved is found either by comparing
+    // slot indices (k, m against the committing lane's, one more shuffle) or
+    // by comparing sites (a, b, no extra shuffle).  Both find the same lanes;
+    // which is faster depends on the code the compiler makes of the loop:
+    // measured on GB300, the slot compare for G = 8, the site compare for
+    // G = 4 and G = 16.
+    constexpr bool kFixBySlot = (G == 8);
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (G - 1);
+    const int gbase = lane - j;
+    IdxT *S = walker_S<IdxT>(p, w);
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t holes = (uint32_t)(p.V - p.N);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int width = p.width;
+    int bin = active ? p.E[w] - p.e_lo : 0;
+    int row = bin * width + 2 * D;
+    uint32_t run = 0;
+    uint32_t acc = 0;
+    // tunnelling bookkeeping (TUN only), meaningful in lane j == 0: every
+    // energy the walker takes is checked against the two ends
+    const int tlo = TUN ? p.tun_lo : 0, thi = TUN ? p.tun_hi : 0;
+    uint32_t tst = (TUN && active && p.tun_state) ? p.tun_state[w] : 0u;
+    uint32_t tcnt = 0;
+    auto tunnel = [&](int b_now) {
+        if (b_now <= tlo) {
+            tcnt += tst == 2u ? 1u : 0u;
+            tst = 1u;
+        } else if (b_now >= thi) {
+            tcnt += tst == 1u ? 1u : 0u;
+            tst = 2u;
+        }
+    };
+    if constexpr (TUN) tunnel(bin);
+    // random numbers and list reads of a batch are issued one batch early;
+    // commits that move a list slot such an early read covers patch it
+    uint32_t kn = 0, mn = 0, an = 0, bn = 0, r2n = 0;
+    auto draw = [&](uint64_t t0) {
+        const uint64_t t = t0 + (uint64_t)j;
+        if (active && t < A) {
+            const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
+            kn = __umulhi(r.x, N);
+            mn = __umulhi(r.y, holes);
+            r2n = r.z;
+            an = S[kn];
+            bn = S[N + mn];
+        }
+    };
+    draw(0);
+    for (uint64_t t0 = 0; t0 < A; t0 += G) {
+        const uint64_t left = A - t0;
+        const int n_valid = left < (uint64_t)G ? (int)left : G;
+        const bool valid = active && (j < n_valid);
+        uint32_t k = kn, m = mn, a = an, b = bn;
+        const uint32_t r2 = r2n;
+        draw(t0 + G);
+        // lanes without an attempt evaluate sites 0 and 0 so that every lane
+        // can evaluate unconditionally
+        FieldMove<D> mv;
+        mv.build(p, fbase, valid ? a : 0u, valid ? b : 0u);
+        // where this lane's own move would write if it commits
+        IdxT *pk = S + k;
+        IdxT *pm = S + N + m;
+        // counts of the first round; later rounds load theirs right after
+        // the previous commit, ahead of the bookkeeping
+        uint32_t va, vb;
+        mv.load(va, vb);
+        int pos = 0;
+        bool done = !active;
+        while (__any_sync(FULL, !done)) {
+            const int de = (int)va - (int)vb + mv.adj;
+            const uint32_t T = thr_load<ST>(thr, row + de);
+            const bool accept = !done && valid && j >= pos && ((T == 0xFFFFFFFFu) || (r2 < T));
+            const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
+            const int f = bal ? __ffs(bal) - 1 : G;
+            const int src = gbase + (f < G ? f : 0);
+            const int de_f = __shfl_sync(FULL, de, src);
+            uint32_t a_f, b_f, k_f = 0, m_f = 0;
+            shfl_pair<IdxT>(a, b, src, a_f, b_f);
+            if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
+            const bool commit = !done && f < G;       // the same in every lane of the group
+            const bool finish = !done && f >= G;
+            if (commit && j == f) {
+                mv.commit();
+                *pk = (IdxT)b;
+                *pm = (IdxT)a;
+            }
+            __syncwarp(FULL);
+            // the commit moved list slots k_f and N + m_f: slot k_f held a_f and
+            // slot N + m_f held b_f, and every site sits in exactly one slot,
+            // so a lane's slot k is k_f exactly when its (current) a is a_f
+            const bool later = commit && j > f;
+            const bool fix_a = later && (kFixBySlot ? k == k_f : a == a_f);
+            const bool fix_b = later && (kFixBySlot ? m == m_f : b == b_f);
+            if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
+                a = fix_a ? b_f : a;
+                b = fix_b ? a_f : b;
+                mv.build(p, fbase, a, b);
+            }
+            mv.load(va, vb);
+            // attempts pos .. f-1 were rejected at the current energy
+            run += commit ? (uint32_t)(f - pos) : (finish ? (uint32_t)(n_valid - pos) : 0u);
+            acc += commit ? 1u : 0u;
+            const bool moved = commit && de_f != 0;
+            if constexpr (TUN) {
+                if (moved && j == 0) {
+                    if (run) atomicAdd(hist + bin, (unsigned long long)run);
+                    tunnel(bin + de_f);
+                }
+            } else {
+                if (moved && j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
+            }
+            bin += moved ? de_f : 0;
+            row += moved ? de_f * width : 0;
+            run = moved ? 0u : run;
+            run += commit ? 1u : 0u;
+            an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
+            bn = (commit && (kFixBySlot ? mn == m_f : bn == b_f)) ? a_f : bn;
+            pos = commit ? f + 1 : pos;
+            done = done || finish || (commit && f + 1 >= n_valid);
+        }
+        if (run >= 0x40000000u) {
+            if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)run);
+            run = 0;
+        }
+    }
+    if (active && j == 0) {
+        if (run) atomicAdd(hist + bin, (unsigned long long)run);
+        p.E[w] = bin + p.e_lo;
+        p.accepts[w] = acc;
+        if (TUN && p.tun_state) {
+            p.tun_state[w] = (uint8_t)tst;
+            p.tun_count[w] += tcnt;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One thread, one walker: A attempts in order, software-pipelined.  The
 // random numbers and list reads of the next PF attempts are in flight in a
 // register ring while the current attempt is evaluated (the slot just
@@ -671,6 +869,117 @@ walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restri
     }
 }
 
+// Bytes of one walker's neighbour-count field in shared memory (V rounded up
+// to 16, so that every walker's field starts on a 16-byte boundary).
+__host__ __device__ __forceinline__ size_t field_bytes(const SysParams &p)
+{
+    return ((size_t)p.V + 15u) & ~(size_t)15u;
+}
+
+// Counts of the block's walkers from their particle lists: zero the fields,
+// then add 1 at every neighbour of every particle.
+template <int D, typename IdxT>
+__device__ __forceinline__ void field_build(const SysParams &p, const BlockWork &wk, uint32_t *fw)
+{
+    const size_t fwords = field_bytes(p) >> 2;
+    const size_t total = (size_t)wk.count * fwords;
+    for (size_t i = threadIdx.x; i < total; i += blockDim.x) fw[i] = 0u;
+    __syncthreads();
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t n_sites = (uint32_t)wk.count * N;
+    for (uint32_t i = threadIdx.x; i < n_sites; i += blockDim.x) {
+        const uint32_t lw = i / N;
+        const uint32_t s = walker_S<IdxT>(p, wk.walker0 + (int)lw)[i - lw * N];
+        uint32_t nb[2 * D];
+        neighbours<D>(p, s, nb);
+        uint32_t *f = fw + (size_t)lw * fwords;
+#pragma unroll
+        for (int k = 0; k < 2 * D; ++k) atomicAdd(f + (nb[k] >> 2), 1u << ((nb[k] & 3u) << 3));
+    }
+    __syncthreads();
+}
+
+// The block's occupation bitsets from their particle lists, assembled in the
+// (now unused) field memory and copied out.
+template <typename IdxT>
+__device__ __forceinline__ void field_finish(const SysParams &p, const BlockWork &wk, uint32_t *fw)
+{
+    __syncthreads();   // every chain is done with the fields; the list stores are visible
+    const size_t words = (size_t)p.words;
+    const size_t total = (size_t)wk.count * words;
+    for (size_t i = threadIdx.x; i < total; i += blockDim.x) fw[i] = 0u;
+    __syncthreads();
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t n_sites = (uint32_t)wk.count * N;
+    for (uint32_t i = threadIdx.x; i < n_sites; i += blockDim.x) {
+        const uint32_t lw = i / N;
+        const uint32_t s = walker_S<IdxT>(p, wk.walker0 + (int)lw)[i - lw * N];
+        atomicOr(fw + (size_t)lw * words + (s >> 5), 1u << (s & 31u));
+    }
+    __syncthreads();
+    block_copy_words(p.bits + (size_t)wk.walker0 * words, fw, total);
+}
+
+template <int D, typename IdxT, int G, bool ST, bool TUN>
+__device__ __forceinline__ void field_item(const SysParams &p, const BlockWork &wk, uint32_t *smem,
+                                           uint64_t sweeps, uint32_t iter)
+{
+    if constexpr (ST) block_copy_words(smem, p.thr, (size_t)p.n_bins * (size_t)p.width);
+    uint32_t *fw = smem + (ST ? thr_words_aligned(p) : 0);
+    field_build<D, IdxT>(p, wk, fw);   // ends with a block barrier, which also covers the table
+    const int lw = threadIdx.x / G;
+    const bool active = lw < wk.count;
+    const int w = wk.walker0 + (active ? lw : 0);
+    const uint32_t *thr = ST ? smem : p.thr;
+    const uint32_t fbase = (uint32_t)__cvta_generic_to_shared(fw) +
+                           (uint32_t)((size_t)(active ? lw : 0) * field_bytes(p));
+    unsigned long long *hist = hist_row(p, w, wk.hist_row);
+    chain_field<D, IdxT, G, ST, TUN>(p, w, active, fbase, thr, hist, sweeps * (uint64_t)p.N, iter);
+    field_finish<IdxT>(p, wk, fw);
+}
+
+template <int G, bool ST, bool TUN>
+__device__ __forceinline__ void field_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
+                                           uint64_t sweeps, uint32_t iter)
+{
+    if (p.d == 2) {
+        if (p.idx16) field_item<2, uint16_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
+        else field_item<2, uint32_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
+    } else {
+        if (p.idx16) field_item<3, uint16_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
+        else field_item<3, uint32_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
+    }
+}
+
+template <int G, bool ST, bool TUN, bool PERSIST>
+__global__ void __launch_bounds__(kGroupMaxThreads, 1)
+walker_update_field(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
+                    uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    if constexpr (!PERSIST) {
+        // one work item per block
+        (void)n_items;
+        (void)next_item;
+        const BlockWork wk = work[blockIdx.x];
+        field_body<G, ST, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
+    } else {
+        __shared__ int s_item;
+        for (int item = blockIdx.x; item < n_items;) {
+            const BlockWork wk = work[item];
+            field_body<G, ST, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
+            item = next_work_item(next_item, &s_item);
+        }
+    }
+}
+
+template <int G, bool TUN, bool PE>
+const void *field_fn(const LaunchShape &sh)
+{
+    if (sh.thr_in_smem) return (const void *)walker_update_field<G, true, TUN, PE>;
+    return (const void *)walker_update_field<G, false, TUN, PE>;
+}
+
 // The walker-update kernel of a launch shape (one TUN flavour).
 template <int G, bool TUN, bool PE>
 const void *group_fn(const LaunchShape &sh)
@@ -681,7 +990,7 @@ const void *group_fn(const LaunchShape &sh)
     return (const void *)walker_update_group<G, false, false, TUN, PE>;
 }
 
-// The kernel of a launch shape among the 24 of one (TUN, PE) flavour
+// The kernel of a launch shape among the kWalkerUpdateFns of one (TUN, PE) flavour
 // (PE: persistent launch); the caller checks that shape.persistent == PE.
 template <bool TUN, bool PE>
 const void *walker_update_fn_t(const LaunchShape &sh)
@@ -691,6 +1000,16 @@ const void *walker_update_fn_t(const LaunchShape &sh)
         if (sh.bits_in_smem) return (const void *)walker_update_thread<true, false, TUN, PE>;
         if (sh.thr_in_smem) return (const void *)walker_update_thread<false, true, TUN, PE>;
         return (const void *)walker_update_thread<false, false, TUN, PE>;
+    }
+    if (sh.kernel == 2) {
+        switch (sh.lanes) {
+        case 2: return field_fn<2, TUN, PE>(sh);
+        case 4: return field_fn<4, TUN, PE>(sh);
+        case 8: return field_fn<8, TUN, PE>(sh);
+        case 16: return field_fn<16, TUN, PE>(sh);
+        case 32: return field_fn<32, TUN, PE>(sh);
+        default: return nullptr;
+        }
     }
     switch (sh.lanes) {
     case 2: return group_fn<2, TUN, PE>(sh);
@@ -705,7 +1024,7 @@ const void *walker_update_fn_t(const LaunchShape &sh)
 // Every walker-update kernel of one (TUN, PE) flavour (for their
 // shared-memory attributes).
 template <bool TUN, bool PE>
-void walker_update_fns(const void *(&fns)[24])
+void walker_update_fns(const void *(&fns)[kWalkerUpdateFns])
 {
     int i = 0;
     fns[i++] = (const void *)walker_update_thread<true, true, TUN, PE>;
@@ -723,6 +1042,15 @@ void walker_update_fns(const void *(&fns)[24])
     MUCAL_GROUP_FNS(16)
     MUCAL_GROUP_FNS(32)
 #undef MUCAL_GROUP_FNS
+#define MUCAL_FIELD_FNS(G)                                                \
+    fns[i++] = (const void *)walker_update_field<G, true, TUN, PE>;      \
+    fns[i++] = (const void *)walker_update_field<G, false, TUN, PE>;
+    MUCAL_FIELD_FNS(2)
+    MUCAL_FIELD_FNS(4)
+    MUCAL_FIELD_FNS(8)
+    MUCAL_FIELD_FNS(16)
+    MUCAL_FIELD_FNS(32)
+#undef MUCAL_FIELD_FNS
 }
 
 }  // namespace

@@ -219,14 +219,14 @@ cudaError_t walker_update_max_smem(int *bytes)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const void *fl[4][24];
+    const void *fl[4][kWalkerUpdateFns];
     walker_update_fns<false, false>(fl[0]);
     walker_update_tunnel_fns(fl[1]);
     walker_update_persist_fns(fl[2]);
     walker_update_persist_tun_fns(fl[3]);
-    const void *fns[96];
+    const void *fns[4 * kWalkerUpdateFns];
     for (int f = 0; f < 4; ++f)
-        for (int i = 0; i < 24; ++i) fns[24 * f + i] = fl[f][i];
+        for (int i = 0; i < kWalkerUpdateFns; ++i) fns[kWalkerUpdateFns * f + i] = fl[f][i];
     // the dynamic limit leaves room for the largest static shared array (the
     // thread kernel's tunnelling words)
     size_t max_static = 0;
@@ -285,6 +285,8 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
 }
 
 size_t thr_smem_words(const SysParams &p) { return thr_words_aligned(p); }
+
+size_t field_smem_bytes(const SysParams &p) { return field_bytes(p); }
 
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                cudaStream_t stream)

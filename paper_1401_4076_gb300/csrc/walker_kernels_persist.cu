@@ -10,6 +10,6 @@ const void *walker_update_fn_persist(const LaunchShape &shape)
     return walker_update_fn_t<false, true>(shape);
 }
 
-void walker_update_persist_fns(const void *(&fns)[24]) { walker_update_fns<false, true>(fns); }
+void walker_update_persist_fns(const void *(&fns)[kWalkerUpdateFns]) { walker_update_fns<false, true>(fns); }
 
 }  // namespace mucal

@@ -10,6 +10,6 @@ const void *walker_update_fn_persist_tun(const LaunchShape &shape)
     return walker_update_fn_t<true, true>(shape);
 }
 
-void walker_update_persist_tun_fns(const void *(&fns)[24]) { walker_update_fns<true, true>(fns); }
+void walker_update_persist_tun_fns(const void *(&fns)[kWalkerUpdateFns]) { walker_update_fns<true, true>(fns); }
 
 }  // namespace mucal

@@ -10,6 +10,6 @@ const void *walker_update_fn_tunnel(const LaunchShape &shape)
     return walker_update_fn_t<true, false>(shape);
 }
 
-void walker_update_tunnel_fns(const void *(&fns)[24]) { walker_update_fns<true, false>(fns); }
+void walker_update_tunnel_fns(const void *(&fns)[kWalkerUpdateFns]) { walker_update_fns<true, false>(fns); }
 
 }  // namespace mucal

@@ -31,6 +31,7 @@ MUCAL_SCHEME_SIMPLE = 0
 MUCAL_SCHEME_RECURSIVE = 1
 MUCAL_KERNEL_THREAD = 0
 MUCAL_KERNEL_GROUP = 1
+MUCAL_KERNEL_FIELD = 2
 
 EXPORTED = [
     "mucal_init_systems", "mucal_destroy", "mucal_last_error", "mucal_set_weights",

@@ -19,6 +19,7 @@ GROUP8P = dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_bloc
 THREADP = dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=7,
                bits_in_smem=0, persistent=1)
 GROUP8 = dict(GROUP8P, persistent=0)
+FIELD8P = dict(GROUP8P, kernel=m.MUCAL_KERNEL_FIELD)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -32,9 +33,9 @@ def _built():
 
 
 @pytest.mark.parametrize("launch,graph", [(GROUP8P, False), (GROUP8P, True), (THREADP, True),
-                                          (GROUP8, True)],
+                                          (GROUP8, True), (FIELD8P, False), (FIELD8P, True)],
                          ids=["G8-persistent", "G8-persistent-graph", "thread-persistent-graph",
-                              "G8-graph"])
+                              "G8-graph", "field-G8-persistent", "field-G8-persistent-graph"])
 def test_small_2d_iterations_bit_exact(launch, graph):
     """2D L=16, N=32, 64 walkers (16 blocks of 4 walkers, or 10 blocks of 7
     for the thread kernel), 6 iterations of 500 sweeps with the recursion."""

@@ -91,9 +91,17 @@ LAUNCHES = [
     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16, walkers_per_block=2, bits_in_smem=1),
     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=32, walkers_per_block=5, bits_in_smem=0),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=2, walkers_per_block=16, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=4, walkers_per_block=24, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=16, walkers_per_block=2, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=32, walkers_per_block=1, bits_in_smem=1),
 ]
 GROUP8 = LAUNCHES[4]
 GROUP32 = LAUNCHES[6]
+FIELD8 = LAUNCHES[7]
+FIELD4 = LAUNCHES[9]
+FIELD32 = LAUNCHES[11]
 
 
 def _lid(c):
@@ -147,7 +155,7 @@ def test_simple_scheme_matches_oracle():
 
 # ---------------------------------------------------------- edge cases ------
 
-@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP32], ids=_lid)
+@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP32, FIELD4, FIELD32], ids=_lid)
 @pytest.mark.parametrize("desc,sweeps", [
     ((3, 6, 40, 37, 0, 0, 11), 30),          # 3D, ragged walker count
     ((2, 3, 1, 5, 0, 0, 77), 200),           # single particle on 3x3
@@ -170,8 +178,12 @@ def test_edge_cases_bit_exact(desc, sweeps, launch):
     with m.Mucal([desc], per_walker_hist=True) as mc:
         try:
             mc.set_launch(**launch)
-        except m.MucalError:        # bitsets too large for shared memory at this block size
-            mc.set_launch(**dict(launch, bits_in_smem=0))
+        except m.MucalError:
+            if launch["kernel"] == m.MUCAL_KERNEL_FIELD:
+                # the fields of a whole warp of walkers do not fit: one walker per block
+                mc.set_launch(**dict(launch, lanes_per_walker=32, walkers_per_block=1))
+            else:                   # bitsets too large for shared memory at this block size
+                mc.set_launch(**dict(launch, bits_in_smem=0))
         mc.set_weights(0, lnW)
         T = chain.thresholds(d, e_lo, e_hi, lnW)
         for it in range(2):
@@ -201,7 +213,7 @@ def test_window_boundary_is_never_crossed():
 
 # ------------------------------------------------ several systems, one launch
 
-@pytest.mark.parametrize("launch", [LAUNCHES[0], GROUP8], ids=_lid)
+@pytest.mark.parametrize("launch", [LAUNCHES[0], GROUP8, FIELD8], ids=_lid)
 def test_multi_system_launch_bit_exact(launch):
     systems = [(2, 16, 32, 40, 0, 0, 0), (3, 8, 60, 25, 0, 0, 500), (2, 24, 50, 33, 0, 0, 900)]
     with m.Mucal(systems, per_walker_hist=True) as mc:
@@ -245,14 +257,16 @@ def _sampled_full_size(wl, sweeps, pick, launch=None, lnW_seed=None):
             _assert_walker_equal(mc, 0, w, S[i], occ[i], E[i])
 
 
-@pytest.mark.parametrize("launch", [None, GROUP8], ids=["default", "G8"])
+@pytest.mark.parametrize("launch", [None, GROUP8, dict(FIELD8, walkers_per_block=28)],
+                         ids=["default", "G8", "field-G8"])
 def test_medium_2d_first_iteration_sampled(launch):
     """2D L=64, N=410, 4096 walkers, first iteration (lnW = 0) at full size."""
     _sampled_full_size(workloads.MEDIUM_2D, workloads.MEDIUM_2D.sweeps, [0, 1, 777, 2048, 4095],
                        launch=launch)
 
 
-@pytest.mark.parametrize("launch", [None, GROUP32], ids=["default", "G32"])
+@pytest.mark.parametrize("launch", [None, GROUP32, dict(FIELD8, walkers_per_block=4)],
+                         ids=["default", "G32", "field-G8"])
 def test_large_3d_first_iteration_sampled(launch):
     """3D L=32, N=3277, 8192 walkers, one iteration with non-trivial weights."""
     _sampled_full_size(workloads.LARGE_3D, 20, [0, 4097, 8191], launch=launch, lnW_seed=3)
@@ -260,7 +274,7 @@ def test_large_3d_first_iteration_sampled(launch):
 
 # ------------------------------------- production mode (per-block rows) -----
 
-@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP8, GROUP32], ids=_lid)
+@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP8, GROUP32, FIELD8], ids=_lid)
 def test_production_histogram_equals_oracle_sum(launch):
     """Without per-walker histograms the rows are per block; H must still be the
     exact sum of every walker's histogram (Eq. 2)."""
@@ -283,7 +297,9 @@ def test_production_histogram_equals_oracle_sum(launch):
      dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=16, bits_in_smem=1)),
     (workloads.LARGE_3D, 10, [0, 8191],
      dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=28, bits_in_smem=1)),
-], ids=["medium2d", "large3d"])
+    (workloads.MEDIUM_2D, 200, [0, 1500, 4095],
+     dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=28, bits_in_smem=1)),
+], ids=["medium2d", "large3d", "medium2d-field"])
 def test_full_size_production_sampled_states(wl, sweeps, pick, launch):
     """Full-size workloads in production mode: every walker's final state of a
     sample equals the oracle's, and sum H counts every attempt."""
@@ -305,15 +321,17 @@ def test_full_size_production_sampled_states(wl, sweeps, pick, launch):
             _assert_walker_equal(mc, 0, w, S[i], occ[i], E[i])
 
 
-def test_batched_uneven_systems_full_size_sampled():
+@pytest.mark.parametrize("launch", [
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16, walkers_per_block=8, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=16, walkers_per_block=2, bits_in_smem=1),
+], ids=["group", "field"])
+def test_batched_uneven_systems_full_size_sampled(launch):
     """The 27-system batch (2D L 32..128, 3D L 16..40, rho 0.02..0.1, 16384
-    walkers) in one launch, in the launch shape the benchmark picks for it:
-    per system sum H counts every attempt and sampled walkers of every system
-    end in the oracle's state."""
+    walkers) in one launch, in the launch shape the benchmark picks for it and
+    with the field kernel: per system sum H counts every attempt and sampled
+    walkers of every system end in the oracle's state."""
     wl = workloads.batched_uneven()
     sweeps = 5
-    launch = dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16, walkers_per_block=8,
-                  bits_in_smem=1)
     with m.Mucal(wl.systems) as mc:
         mc.set_launch(**launch)
         lnWs = []

@@ -16,6 +16,7 @@ LAUNCHES = [
     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=2, walkers_per_block=16, bits_in_smem=1),
     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
     dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=32, walkers_per_block=5, bits_in_smem=0),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
 ]
 
 
