@@ -1,7 +1,8 @@
 """Launch-shape autotuner for the walker update.
 
 For a set of systems it times every candidate launch shape: kernel (one
-thread per walker, or G lanes per walker), walkers per block, whether the
+thread per walker, G lanes per walker on the occupation bits, or G lanes per
+walker on a field of neighbour counts), walkers per block, whether the
 occupation bitsets are staged in shared memory, and (for the finalists)
 whether the launch is persistent.  All candidates compute the
 identical chain (the group kernel commits attempts in order), so only speed
@@ -34,6 +35,10 @@ def candidates(max_threads: int = 1024):
             for smem in (1, 0):
                 out.append(dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=g,
                                 walkers_per_block=wpb, bits_in_smem=smem))
+            # the field lives in shared memory; shapes it does not fit are
+            # rejected by the library and skipped
+            out.append(dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=g,
+                            walkers_per_block=wpb, bits_in_smem=1))
     return out
 
 

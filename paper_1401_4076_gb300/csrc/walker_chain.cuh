@@ -434,11 +434,13 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
 
 // ---------------------------------------------------------------------------
 // Local-field variant of the group kernel (MUCAL_KERNEL_FIELD).  Every walker
-// of the block keeps one byte per site in shared memory: the number of
-// occupied neighbours of that site (0 .. 2d).  An attempt's energy change is
-// then c[a] - c[b] + [a is a neighbour of b] (a is still occupied when b is
-// examined), two byte loads instead of the 2*2d occupation bits, and a commit
-// adds -1 to the counts of a's neighbours and +1 to those of b's.  Rounds,
+// of the block keeps one byte per site in shared memory: c = 4 times the
+// number of occupied neighbours of that site (0 .. 8d; times 4 so that a
+// difference of counts is a byte offset into a threshold row).  An attempt's
+// energy change is then (c[a] - c[b])/4 + [a is a neighbour of b] (a is still
+// occupied when b is examined), two byte loads instead of the 2*2d occupation
+// bits, and a commit subtracts 4 from the counts of a's neighbours and adds 4
+// to those of b's.  Rounds,
 // commits and bookkeeping are those of chain_group, so the chain is the same
 // one.  The field is built from the particle list when a block starts and the
 // occupation bitset is rebuilt from the list when it ends; the bitset is not
@@ -447,9 +449,9 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
 template <int D>
 struct FieldMove {
     uint32_t ca, cb;     // shared byte addresses of c[a] and c[b]
-    int adj;             // 1 if b is a neighbour of a
+    int adj;             // 4 if b is a neighbour of a (counts are kept times 4)
     uint32_t ua[4 * D];  // shared word addresses of the 2*2d counts a commit changes
-    uint32_t uv[4 * D];  // what the commit adds there: -1 or +1 in the site's byte
+    uint32_t uv[4 * D];  // what the commit adds there: -4 or +4 in the site's byte
 
     __device__ __forceinline__ void build(const SysParams &p, uint32_t fbase, uint32_t a, uint32_t b)
     {
@@ -461,11 +463,11 @@ struct FieldMove {
         adj = 0;
 #pragma unroll
         for (int i = 0; i < 2 * D; ++i) {
-            adj |= (na[i] == b) ? 1 : 0;
+            adj |= (na[i] == b) ? 4 : 0;
             ua[i] = fbase + (na[i] & ~3u);
-            uv[i] = 0u - (1u << ((na[i] & 3u) << 3));
+            uv[i] = 0u - (4u << ((na[i] & 3u) << 3));
             ua[2 * D + i] = fbase + (nb[i] & ~3u);
-            uv[2 * D + i] = 1u << ((nb[i] & 3u) << 3);
+            uv[2 * D + i] = 4u << ((nb[i] & 3u) << 3);
         }
     }
 
@@ -475,7 +477,7 @@ struct FieldMove {
         asm volatile("ld.shared.u8 %0, [%1];" : "=r"(vb) : "r"(cb) : "memory");
     }
 
-    // Byte counts stay in [0, 2d]: a decrement meets a count that includes
+    // Byte counts stay in [0, 8d]: a decrement meets a count that includes
     // the leaving particle, so no borrow or carry crosses a byte.
     __device__ __forceinline__ void commit() const
     {
@@ -492,13 +494,10 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
-    // A later lane whose slot the commit moved is found either by comparing
-    // slot indices (k, m against the committing lane's, one more shuffle) or
-    // by comparing sites (a, b, no extra shuffle).  Both find the same lanes;
-    // which is faster depends on the code the compiler makes of the loop:
-    // measured on GB300, the slot compare for G = 8, the site compare for
-    // G = 4 and G = 16.
-    constexpr bool kFixBySlot = (G == 8);
+    // later lanes whose slot the commit moved are found by comparing sites
+    // (see chain_group; measured on GB300, the site compare is the faster
+    // one here for every G)
+    constexpr bool kFixBySlot = false;
     const int lane = threadIdx.x & 31;
     const int j = lane & (G - 1);
     const int gbase = lane - j;
@@ -509,7 +508,10 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int width = p.width;
     int bin = active ? p.E[w] - p.e_lo : 0;
-    int row = bin * width + 2 * D;
+    // the current threshold row, entry dE = 0, as a shared byte address (or
+    // a byte offset into the global table)
+    const uint32_t thr_s = ST ? (uint32_t)__cvta_generic_to_shared(thr) : 0u;
+    uint32_t rb = thr_s + 4u * (uint32_t)(bin * width + 2 * D);
     uint32_t run = 0;
     uint32_t acc = 0;
     // tunnelling bookkeeping (TUN only), meaningful in lane j == 0: every
@@ -563,8 +565,14 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
         int pos = 0;
         bool done = !active;
         while (__any_sync(FULL, !done)) {
-            const int de = (int)va - (int)vb + mv.adj;
-            const uint32_t T = thr_load<ST>(thr, row + de);
+            const uint32_t toff = rb + (uint32_t)mv.adj + va - vb;
+            uint32_t T;
+            if constexpr (ST) {
+                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(T) : "r"(toff));
+            } else {
+                T = __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(thr) + toff));
+            }
+            const int de = ((int)va - (int)vb + mv.adj) >> 2;
             const bool accept = !done && valid && j >= pos && ((T == 0xFFFFFFFFu) || (r2 < T));
             const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
             const int f = bal ? __ffs(bal) - 1 : G;
@@ -606,7 +614,7 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
                 if (moved && j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
             }
             bin += moved ? de_f : 0;
-            row += moved ? de_f * width : 0;
+            rb += moved ? (uint32_t)(4 * de_f * width) : 0u;
             run = moved ? 0u : run;
             run += commit ? 1u : 0u;
             an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
@@ -877,7 +885,7 @@ __host__ __device__ __forceinline__ size_t field_bytes(const SysParams &p)
 }
 
 // Counts of the block's walkers from their particle lists: zero the fields,
-// then add 1 at every neighbour of every particle.
+// then add 4 at every neighbour of every particle.
 template <int D, typename IdxT>
 __device__ __forceinline__ void field_build(const SysParams &p, const BlockWork &wk, uint32_t *fw)
 {
@@ -894,7 +902,7 @@ __device__ __forceinline__ void field_build(const SysParams &p, const BlockWork 
         neighbours<D>(p, s, nb);
         uint32_t *f = fw + (size_t)lw * fwords;
 #pragma unroll
-        for (int k = 0; k < 2 * D; ++k) atomicAdd(f + (nb[k] >> 2), 1u << ((nb[k] & 3u) << 3));
+        for (int k = 0; k < 2 * D; ++k) atomicAdd(f + (nb[k] >> 2), 4u << ((nb[k] & 3u) << 3));
     }
     __syncthreads();
 }
