@@ -501,6 +501,7 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
     const int lane = threadIdx.x & 31;
     const int j = lane & (G - 1);
     const int gbase = lane - j;
+    const unsigned gm = GMASK << gbase;      // this group's lanes in a warp ballot
     IdxT *S = walker_S<IdxT>(p, w);
     const uint32_t N = (uint32_t)p.N;
     const uint32_t holes = (uint32_t)(p.V - p.N);
@@ -562,33 +563,39 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
         // the previous commit, ahead of the bookkeeping
         uint32_t va, vb;
         mv.load(va, vb);
+        uint32_t rba = rb + (uint32_t)mv.adj;   // the threshold row plus this attempt's adjacency
         int pos = 0;
         bool done = !active;
         while (__any_sync(FULL, !done)) {
-            const uint32_t toff = rb + (uint32_t)mv.adj + va - vb;
+            const uint32_t toff = rba + va - vb;
             uint32_t T;
             if constexpr (ST) {
                 asm volatile("ld.shared.u32 %0, [%1];" : "=r"(T) : "r"(toff));
             } else {
                 T = __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(thr) + toff));
             }
-            const int de = ((int)va - (int)vb + mv.adj) >> 2;
+            const int de4 = (int)va - (int)vb + mv.adj;   // 4 dE
             const bool accept = !done && valid && j >= pos && ((T == 0xFFFFFFFFu) || (r2 < T));
-            const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
-            const int f = bal ? __ffs(bal) - 1 : G;
-            const int src = gbase + (f < G ? f : 0);
-            const int de_f = __shfl_sync(FULL, de, src);
+            // the first accepting lane of the group, as a warp lane (src) and
+            // a group lane (f; G when none accepts)
+            const unsigned bal = __ballot_sync(FULL, accept) & gm;
+            const int src = bal ? __ffs(bal) - 1 : gbase;
+            const int f = bal ? src - gbase : G;
+            const int de_f = __shfl_sync(FULL, de4, src) >> 2;
             uint32_t a_f, b_f, k_f = 0, m_f = 0;
             shfl_pair<IdxT>(a, b, src, a_f, b_f);
             if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
-            const bool commit = !done && f < G;       // the same in every lane of the group
-            const bool finish = !done && f >= G;
-            if (commit && j == f) {
+            const bool commit = !done && bal != 0u;    // the same in every lane of the group
+            const bool finish = !done && bal == 0u;
+            if (commit && lane == src) {
                 mv.commit();
                 *pk = (IdxT)b;
                 *pm = (IdxT)a;
             }
             __syncwarp(FULL);
+            // the next round's counts, loaded before the (rare) fix below,
+            // which reloads them when it moves this lane's sites
+            mv.load(va, vb);
             // the commit moved list slots k_f and N + m_f: slot k_f held a_f and
             // slot N + m_f held b_f, and every site sits in exactly one slot,
             // so a lane's slot k is k_f exactly when its (current) a is a_f
@@ -599,8 +606,8 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
                 a = fix_a ? b_f : a;
                 b = fix_b ? a_f : b;
                 mv.build(p, fbase, a, b);
+                mv.load(va, vb);
             }
-            mv.load(va, vb);
             // attempts pos .. f-1 were rejected at the current energy
             run += commit ? (uint32_t)(f - pos) : (finish ? (uint32_t)(n_valid - pos) : 0u);
             acc += commit ? 1u : 0u;
@@ -615,6 +622,7 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
             }
             bin += moved ? de_f : 0;
             rb += moved ? (uint32_t)(4 * de_f * width) : 0u;
+            rba = rb + (uint32_t)mv.adj;
             run = moved ? 0u : run;
             run += commit ? 1u : 0u;
             an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
