@@ -287,6 +287,8 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
     const int lane = threadIdx.x & 31;
     const int j = lane & (G - 1);
     const int gbase = lane - j;
+    const unsigned gm = GMASK << gbase;              // this group's lanes in a warp ballot
+    const unsigned ltm = gm & ((1u << lane) - 1u);   // ... and those below this lane
     IdxT *S = walker_S<IdxT>(p, w);
     const BitAddr<SB> ba(bits);
     const uint32_t N = (uint32_t)p.N;
@@ -296,7 +298,10 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
     const int width = p.width;
     int bin = active ? p.E[w] - p.e_lo : 0;
     int row = bin * width + 2 * D;
-    uint32_t run = 0;
+    // histogram entries are added per run of attempts at one energy: carry
+    // holds the run's attempts from earlier batches, rs the warp lane of
+    // this batch at which it started
+    uint32_t carry = 0;
     uint32_t acc = 0;
     // tunnelling bookkeeping (TUN only), meaningful in lane j == 0: every
     // energy the walker takes is checked against the two ends
@@ -350,22 +355,19 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
         uint32_t wa[2 * D], wb[2 * D];
         na.load(wa);
         nb.load(wb);
-        int pos = 0;
-        bool done = !active;
-        while (__any_sync(FULL, !done)) {
+        bool pend = valid;                      // this lane's attempt is still undecided
+        int rs = gbase;
+        while (__any_sync(FULL, pend)) {
             const int de = na.count_from(wa) - nb.count_from(wb);
             const uint32_t T = thr_load<ST>(thr, row + de);
-            const bool accept = !done && valid && j >= pos && ((T == 0xFFFFFFFFu) || (r2 < T));
-            const unsigned bal = (__ballot_sync(FULL, accept) >> gbase) & GMASK;
-            const int f = bal ? __ffs(bal) - 1 : G;
-            const int src = gbase + (f < G ? f : 0);
-            const int de_f = __shfl_sync(FULL, de, src);
-            uint32_t a_f, b_f, k_f = 0, m_f = 0;
-            shfl_pair<IdxT>(a, b, src, a_f, b_f);
-            if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
-            const bool commit = !done && f < G;       // the same in every lane of the group
-            const bool finish = !done && f >= G;
-            if (commit && j == f) {
+            const bool accept = pend && ((T == 0xFFFFFFFFu) || (r2 < T));
+            // pending lanes are the group's last ones, so the first accepting
+            // lane commits, the pending lanes before it were rejected at the
+            // current state and those after it (later) evaluate again
+            const unsigned bal = __ballot_sync(FULL, accept) & gm;
+            const bool commit = bal != 0u;             // the same in every lane of the group
+            const bool later = (bal & ltm) != 0u;
+            if (accept && !later) {
                 if constexpr (SB) {
                     atomicAnd(wa_own, ~ma_own);
                     atomicOr(wb_own, mb_own);
@@ -376,11 +378,19 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
                 *pk = (IdxT)b;
                 *pm = (IdxT)a;
             }
+            const int src = commit ? __ffs(bal) - 1 : gbase;   // the committing warp lane
+            const int de_f = __shfl_sync(FULL, de, src);
+            uint32_t a_f, b_f, k_f = 0, m_f = 0;
+            shfl_pair<IdxT>(a, b, src, a_f, b_f);
+            if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
             __syncwarp(FULL);
+            // the next round's occupation words, loaded before the (rare) fix
+            // below, which reloads them when it moves this lane's sites
+            na.load(wa);
+            nb.load(wb);
             // the commit moved list slots k_f and N + m_f: slot k_f held a_f and
             // slot N + m_f held b_f, and every site sits in exactly one slot,
             // so a lane's slot k is k_f exactly when its (current) a is a_f
-            const bool later = commit && j > f;
             const bool fix_a = later && (kFixBySlot ? k == k_f : a == a_f);
             const bool fix_b = later && (kFixBySlot ? m == m_f : b == b_f);
             if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
@@ -392,37 +402,39 @@ __device__ __forceinline__ void chain_group(const SysParams &p, int w, bool acti
                 wb_own = bits + (b >> 5);
                 ma_own = 1u << (a & 31u);
                 mb_own = 1u << (b & 31u);
+                na.load(wa);
+                nb.load(wb);
             }
-            na.load(wa);
-            nb.load(wb);
-            // attempts pos .. f-1 were rejected at the current energy
-            run += commit ? (uint32_t)(f - pos) : (finish ? (uint32_t)(n_valid - pos) : 0u);
+            pend = pend && later;
             acc += commit ? 1u : 0u;
+            // a move ends the run at the old energy: attempts rs .. src - 1 of
+            // this batch (the committed one is the first at the new energy)
             const bool moved = commit && de_f != 0;
+            const uint32_t cnt = carry + (uint32_t)(src - rs);
             if constexpr (TUN) {
                 if (moved && j == 0) {
-                    if (run) atomicAdd(hist + bin, (unsigned long long)run);
+                    if (cnt) atomicAdd(hist + bin, (unsigned long long)cnt);
                     tunnel(bin + de_f);
                 }
             } else {
-                if (moved && j == 0 && run) atomicAdd(hist + bin, (unsigned long long)run);
+                if (moved && j == 0 && cnt) atomicAdd(hist + bin, (unsigned long long)cnt);
             }
+            carry = moved ? 0u : carry;
+            rs = moved ? src : rs;
             bin += moved ? de_f : 0;
             row += moved ? de_f * width : 0;
-            run = moved ? 0u : run;
-            run += commit ? 1u : 0u;
             an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
             bn = (commit && (kFixBySlot ? mn == m_f : bn == b_f)) ? a_f : bn;
-            pos = commit ? f + 1 : pos;
-            done = done || finish || (commit && f + 1 >= n_valid);
         }
-        if (run >= 0x40000000u) {
-            if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)run);
-            run = 0;
+        // the batch's attempts from rs on are at the final energy
+        carry += (uint32_t)(gbase + n_valid - rs);
+        if (carry >= 0x40000000u) {
+            if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)carry);
+            carry = 0;
         }
     }
     if (active && j == 0) {
-        if (run) atomicAdd(hist + bin, (unsigned long long)run);
+        if (carry) atomicAdd(hist + bin, (unsigned long long)carry);
         p.E[w] = bin + p.e_lo;
         p.accepts[w] = acc;
         if (TUN && p.tun_state) {
