@@ -48,17 +48,24 @@ def alg_ops_per_attempt(d: int) -> int:
 
 # DRAM bytes (read + write) of one walker-update launch of a workload's
 # default iteration, from the one-pass ncu capture summarised under profiles/,
-# valid only for the kernel source it was taken with (sha256 prefix of
-# walker_chain.cuh); any change to the kernel makes the figure stale (null).
+# valid only for the launch shape and the kernel source it was taken with
+# (sha256 prefix of walker_chain.cuh); any other shape or any change to the
+# kernel makes the figure stale (null).
 TRAFFIC_MEASURED = {
-    "2d-L64-N410-w4096": {"bytes": 36.36e6 + 378.84e6, "kernel_sha": "397be88b1e7d3a10"},
+    "2d-L64-N410-w4096": {"bytes": 33.96e6 + 970.74e6, "kernel_sha": "cc9fa5649a208a45",
+                          "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28,
+                                     "persistent": 0}},
 }
 
+KERNEL_NAMES = {0: "walker_update_thread", 1: "walker_update_group", 2: "walker_update_field"}
 
-def _measured_traffic(workload: str, sweeps_default: bool):
+
+def _measured_traffic(workload: str, sweeps_default: bool, launch: dict):
     import hashlib
     rec = TRAFFIC_MEASURED.get(workload)
     if rec is None or not sweeps_default:
+        return None
+    if any(launch.get(k) != v for k, v in rec["launch"].items()):
         return None
     # the walker-update kernels are compiled from walker_chain.cuh
     with open(os.path.join(ROOT, "paper_1401_4076_gb300", "csrc", "walker_chain.cuh"), "rb") as f:
@@ -367,10 +374,11 @@ def main(argv=None):
     achieved = ops_launch / (k_ms / 1000.0)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "Tops/s", "frac": achieved / peak_ops,
-                "traffic": _measured_traffic(wl.name, sweeps == wl.sweeps),
+                "traffic": _measured_traffic(wl.name, sweeps == wl.sweeps, args.launch_desc),
                 "peak_source": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz"
                                f" ({peak_kind} max clock)",
-                "kernel": "walker_update", "kernel_ms": k_ms,
+                "kernel": KERNEL_NAMES.get(args.launch_desc.get("kernel"), "walker_update"),
+                "kernel_ms": k_ms,
                 "alg_ops_per_attempt": alg_ops_per_attempt(d_max)}
 
     line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,

@@ -701,10 +701,17 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
                                  "system %d: initial energy %d outside window [%d, %d]", i, v,
                                  s.desc.e_lo, s.desc.e_hi));
     }
-    mucal_launch_config def{MUCAL_KERNEL_GROUP, 8, 16, 1, 0};
+    // default launch: the field kernel when every system's fields fit in
+    // shared memory, else the group kernel with the bitsets in shared memory
+    // when they fit, else in global memory (8 lanes, 16 walkers per block)
+    mucal_launch_config def{MUCAL_KERNEL_FIELD, 8, 16, 1, 0};
     for (auto &s : c->sys)
-        if (smem_for(LaunchShape{MUCAL_KERNEL_GROUP, 8, 16, 1, 0, 0, 0}, s.p) > (size_t)c->max_smem)
-            def.bits_in_smem = 0;
+        if (smem_for(LaunchShape{MUCAL_KERNEL_FIELD, 8, 16, 1, 0, 0, 0}, s.p) > (size_t)c->max_smem)
+            def.kernel = MUCAL_KERNEL_GROUP;
+    if (def.kernel == MUCAL_KERNEL_GROUP)
+        for (auto &s : c->sys)
+            if (smem_for(LaunchShape{MUCAL_KERNEL_GROUP, 8, 16, 1, 0, 0, 0}, s.p) > (size_t)c->max_smem)
+                def.bits_in_smem = 0;
     rc = apply_launch_config(c, def);
     if (rc != MUCAL_OK) return bail(rc);
     *out = c;
