@@ -50,11 +50,12 @@ def alg_ops_per_attempt(d: int) -> int:
 # default iteration, from the one-pass ncu capture summarised under profiles/,
 # valid only for the launch shape and the kernel source it was taken with
 # (sha256 prefix of walker_chain.cuh); any other shape or any change to the
-# kernel makes the figure stale (null).
+# kernel makes the figure stale (null).  The persistent flag is not part of
+# the shape here: when every block is resident at once (147 blocks of 28
+# walkers on 152 SMs) the persistent launch runs the same blocks.
 TRAFFIC_MEASURED = {
     "2d-L64-N410-w4096": {"bytes": 33.96e6 + 970.74e6, "kernel_sha": "cc9fa5649a208a45",
-                          "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28,
-                                     "persistent": 0}},
+                          "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28}},
 }
 
 KERNEL_NAMES = {0: "walker_update_thread", 1: "walker_update_group", 2: "walker_update_field"}
