@@ -159,12 +159,13 @@ __device__ __forceinline__ void block_finish(const BlockSetup &b, int bits_in_sm
 // ---------------------------------------------------------------------------
 // G lanes per walker (G divides 32).  Lane j of a group owns attempt t0 + j of
 // the current batch: it draws its random numbers, reads its particle and
-// empty site, and precomputes the words and bit positions of their 2*2d
-// neighbours once.  Every round the lanes still pending evaluate dE and the
-// acceptance against the walker's current state.  The first accepting lane f
-// commits; lanes before it were rejected by that same state and are recorded
-// at the current energy; lanes after it re-evaluate in the next round (their
-// list entries are patched in registers when the commit moved the same list
+// empty site, and prepares what evaluating them needs once (the words and bit
+// positions of their 2*2d neighbours, or their places in a count field).
+// Every round the lanes still pending evaluate dE and the acceptance against
+// the walker's current state.  The first accepting lane f commits; pending
+// lanes before it were rejected by that same state and are recorded at the
+// current energy; lanes after it re-evaluate in the next round (their list
+// entries are patched in registers when the commit moved the same list
 // slot).  The chain is therefore exactly the one-thread chain.  A warp's
 // groups step through the rounds in lock-step so no group diverges.
 // ---------------------------------------------------------------------------
@@ -270,203 +271,83 @@ __device__ __forceinline__ void shfl_pair(uint32_t x, uint32_t y, int src, uint3
     }
 }
 
-template <int D, typename IdxT, int G, bool SB, bool ST, bool TUN>
-__device__ __forceinline__ void chain_group(const SysParams &p, int w, bool active, uint32_t *bits,
-                                            const uint32_t *thr, unsigned long long *hist,
-                                            uint64_t A, uint32_t iter)
-{
-    constexpr unsigned FULL = 0xffffffffu;
-    constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
-    // A later lane whose slot the commit moved is found either by comparing
-    // slot indices (k, m against the committing lane's, one more shuffle) or
-    // by comparing sites (a, b, no extra shuffle).  Both find the same lanes;
-    // which is faster depends on the code the compiler makes of the loop:
-    // measured on GB300, the slot compare for G = 8, the site compare for
-    // G = 4 and G = 16.
-    constexpr bool kFixBySlot = (G == 8);
-    const int lane = threadIdx.x & 31;
-    const int j = lane & (G - 1);
-    const int gbase = lane - j;
-    const unsigned gm = GMASK << gbase;              // this group's lanes in a warp ballot
-    const unsigned ltm = gm & ((1u << lane) - 1u);   // ... and those below this lane
-    IdxT *S = walker_S<IdxT>(p, w);
-    const BitAddr<SB> ba(bits);
-    const uint32_t N = (uint32_t)p.N;
-    const uint32_t holes = (uint32_t)(p.V - p.N);
-    const uint64_t seed = p.seed_base + (uint64_t)w;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const int width = p.width;
-    int bin = active ? p.E[w] - p.e_lo : 0;
-    int row = bin * width + 2 * D;
-    // histogram entries are added per run of attempts at one energy: carry
-    // holds the run's attempts from earlier batches, rs the warp lane of
-    // this batch at which it started
-    uint32_t carry = 0;
-    uint32_t acc = 0;
-    // tunnelling bookkeeping (TUN only), meaningful in lane j == 0: every
-    // energy the walker takes is checked against the two ends
-    const int tlo = TUN ? p.tun_lo : 0, thi = TUN ? p.tun_hi : 0;
-    uint32_t tst = (TUN && active && p.tun_state) ? p.tun_state[w] : 0u;
-    uint32_t tcnt = 0;
-    auto tunnel = [&](int b_now) {
-        if (b_now <= tlo) {
-            tcnt += tst == 2u ? 1u : 0u;
-            tst = 1u;
-        } else if (b_now >= thi) {
-            tcnt += tst == 1u ? 1u : 0u;
-            tst = 2u;
-        }
-    };
-    if constexpr (TUN) tunnel(bin);
-    // random numbers and list reads of a batch are issued one batch early;
-    // commits that move a list slot such an early read covers patch it
-    uint32_t kn = 0, mn = 0, an = 0, bn = 0, r2n = 0;
-    auto draw = [&](uint64_t t0) {
-        const uint64_t t = t0 + (uint64_t)j;
-        if (active && t < A) {
-            const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
-            kn = __umulhi(r.x, N);
-            mn = __umulhi(r.y, holes);
-            r2n = r.z;
-            an = S[kn];
-            bn = S[N + mn];
-        }
-    };
-    draw(0);
-    for (uint64_t t0 = 0; t0 < A; t0 += G) {
-        const uint64_t left = A - t0;
-        const int n_valid = left < (uint64_t)G ? (int)left : G;
-        const bool valid = active && (j < n_valid);
-        uint32_t k = kn, m = mn, a = an, b = bn;
-        const uint32_t r2 = r2n;
-        draw(t0 + G);
-        // lanes without an attempt read site 0's neighbourhood so that every
-        // lane can evaluate unconditionally
-        NbSet<D, SB> na, nb;
+// ---------------------------------------------------------------------------
+// Views of a walker's occupation for the group rounds.  build() takes the
+// attempt (a, b) (a lane without one, valid false, evaluates site 0), load()
+// reads the state the round evaluates, d4() + adj4() is 4 dE (adj4() is the
+// part that depends on the attempt alone, so it joins the threshold row
+// address), commit() applies the lane's move.
+// ---------------------------------------------------------------------------
+
+// Through the occupation bitset: dE counts the occupied neighbour bits of a
+// and of b (a excluded from b's neighbours), a commit flips the two bits.
+template <int D, bool SB>
+struct BitView {
+    uint32_t *bits;
+    BitAddr<SB> ba;
+    NbSet<D, SB> na, nb;
+    uint32_t *wa_own, *wb_own;   // where this lane's own move would write if it commits
+    uint32_t ma_own, mb_own;
+    uint32_t wa[2 * D], wb[2 * D];
+
+    __device__ __forceinline__ explicit BitView(uint32_t *b) : bits(b), ba(b) {}
+
+    __device__ __forceinline__ void build(const SysParams &p, uint32_t a, uint32_t b, bool valid)
+    {
         na.build(p, ba, valid ? a : 0u, 0xFFFFFFFFu);
         nb.build(p, ba, valid ? b : 0u, valid ? a : 0xFFFFFFFFu);
-        // where this lane's own move would write if it commits
-        IdxT *pk = S + k;
-        IdxT *pm = S + N + m;
-        uint32_t *wa_own = bits + (a >> 5), *wb_own = bits + (b >> 5);
-        uint32_t ma_own = 1u << (a & 31u), mb_own = 1u << (b & 31u);
-        // occupation words of the first round; later rounds load theirs right
-        // after the previous commit, ahead of the bookkeeping
-        uint32_t wa[2 * D], wb[2 * D];
+        wa_own = bits + (a >> 5);
+        wb_own = bits + (b >> 5);
+        ma_own = 1u << (a & 31u);
+        mb_own = 1u << (b & 31u);
+    }
+
+    __device__ __forceinline__ void load()
+    {
         na.load(wa);
         nb.load(wb);
-        bool pend = valid;                      // this lane's attempt is still undecided
-        int rs = gbase;
-        while (__any_sync(FULL, pend)) {
-            const int de = na.count_from(wa) - nb.count_from(wb);
-            const uint32_t T = thr_load<ST>(thr, row + de);
-            const bool accept = pend && ((T == 0xFFFFFFFFu) || (r2 < T));
-            // pending lanes are the group's last ones, so the first accepting
-            // lane commits, the pending lanes before it were rejected at the
-            // current state and those after it (later) evaluate again
-            const unsigned bal = __ballot_sync(FULL, accept) & gm;
-            const bool commit = bal != 0u;             // the same in every lane of the group
-            const bool later = (bal & ltm) != 0u;
-            if (accept && !later) {
-                if constexpr (SB) {
-                    atomicAnd(wa_own, ~ma_own);
-                    atomicOr(wb_own, mb_own);
-                } else {
-                    *wa_own &= ~ma_own;
-                    *wb_own |= mb_own;
-                }
-                *pk = (IdxT)b;
-                *pm = (IdxT)a;
-            }
-            const int src = commit ? __ffs(bal) - 1 : gbase;   // the committing warp lane
-            const int de_f = __shfl_sync(FULL, de, src);
-            uint32_t a_f, b_f, k_f = 0, m_f = 0;
-            shfl_pair<IdxT>(a, b, src, a_f, b_f);
-            if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
-            __syncwarp(FULL);
-            // the next round's occupation words, loaded before the (rare) fix
-            // below, which reloads them when it moves this lane's sites
-            na.load(wa);
-            nb.load(wb);
-            // the commit moved list slots k_f and N + m_f: slot k_f held a_f and
-            // slot N + m_f held b_f, and every site sits in exactly one slot,
-            // so a lane's slot k is k_f exactly when its (current) a is a_f
-            const bool fix_a = later && (kFixBySlot ? k == k_f : a == a_f);
-            const bool fix_b = later && (kFixBySlot ? m == m_f : b == b_f);
-            if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
-                a = fix_a ? b_f : a;
-                b = fix_b ? a_f : b;
-                na.build(p, ba, a, 0xFFFFFFFFu);
-                nb.build(p, ba, b, a);
-                wa_own = bits + (a >> 5);
-                wb_own = bits + (b >> 5);
-                ma_own = 1u << (a & 31u);
-                mb_own = 1u << (b & 31u);
-                na.load(wa);
-                nb.load(wb);
-            }
-            pend = pend && later;
-            acc += commit ? 1u : 0u;
-            // a move ends the run at the old energy: attempts rs .. src - 1 of
-            // this batch (the committed one is the first at the new energy)
-            const bool moved = commit && de_f != 0;
-            const uint32_t cnt = carry + (uint32_t)(src - rs);
-            if constexpr (TUN) {
-                if (moved && j == 0) {
-                    if (cnt) atomicAdd(hist + bin, (unsigned long long)cnt);
-                    tunnel(bin + de_f);
-                }
-            } else {
-                if (moved && j == 0 && cnt) atomicAdd(hist + bin, (unsigned long long)cnt);
-            }
-            carry = moved ? 0u : carry;
-            rs = moved ? src : rs;
-            bin += moved ? de_f : 0;
-            row += moved ? de_f * width : 0;
-            an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
-            bn = (commit && (kFixBySlot ? mn == m_f : bn == b_f)) ? a_f : bn;
-        }
-        // the batch's attempts from rs on are at the final energy
-        carry += (uint32_t)(gbase + n_valid - rs);
-        if (carry >= 0x40000000u) {
-            if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)carry);
-            carry = 0;
-        }
     }
-    if (active && j == 0) {
-        if (carry) atomicAdd(hist + bin, (unsigned long long)carry);
-        p.E[w] = bin + p.e_lo;
-        p.accepts[w] = acc;
-        if (TUN && p.tun_state) {
-            p.tun_state[w] = (uint8_t)tst;
-            p.tun_count[w] += tcnt;
-        }
-    }
-}
 
-// ---------------------------------------------------------------------------
-// Local-field variant of the group kernel (MUCAL_KERNEL_FIELD).  Every walker
-// of the block keeps one byte per site in shared memory: c = 4 times the
-// number of occupied neighbours of that site (0 .. 8d; times 4 so that a
-// difference of counts is a byte offset into a threshold row).  An attempt's
-// energy change is then (c[a] - c[b])/4 + [a is a neighbour of b] (a is still
-// occupied when b is examined), two byte loads instead of the 2*2d occupation
-// bits, and a commit subtracts 4 from the counts of a's neighbours and adds 4
-// to those of b's.  Rounds,
-// commits and bookkeeping are those of chain_group, so the chain is the same
-// one.  The field is built from the particle list when a block starts and the
-// occupation bitset is rebuilt from the list when it ends; the bitset is not
-// touched in between.
-// ---------------------------------------------------------------------------
+    __device__ __forceinline__ int d4() const { return 4 * (na.count_from(wa) - nb.count_from(wb)); }
+    __device__ __forceinline__ int adj4() const { return 0; }
+
+    __device__ __forceinline__ void commit() const
+    {
+        if constexpr (SB) {
+            atomicAnd(wa_own, ~ma_own);
+            atomicOr(wb_own, mb_own);
+        } else {
+            *wa_own &= ~ma_own;
+            *wb_own |= mb_own;
+        }
+    }
+};
+
+// Through a local field (MUCAL_KERNEL_FIELD).  Every walker of the block
+// keeps one byte per site in shared memory: c = 4 times the number of
+// occupied neighbours of that site (0 .. 8d; times 4 so that a difference of
+// counts is a byte offset into a threshold row).  An attempt's energy change
+// is then (c[a] - c[b])/4 + [a is a neighbour of b] (a is still occupied when
+// b is examined), two byte loads instead of the 2*2d occupation bits, and a
+// commit subtracts 4 from the counts of a's neighbours and adds 4 to those
+// of b's.  The field is built from the particle list when a block starts and
+// the occupation bitset is rebuilt from the list when it ends; the bitset is
+// not touched in between.
 template <int D>
-struct FieldMove {
+struct FieldView {
+    uint32_t fbase;      // shared byte address of this walker's field
     uint32_t ca, cb;     // shared byte addresses of c[a] and c[b]
-    int adj;             // 4 if b is a neighbour of a (counts are kept times 4)
+    int adj;             // 4 if b is a neighbour of a
     uint32_t ua[4 * D];  // shared word addresses of the 2*2d counts a commit changes
     uint32_t uv[4 * D];  // what the commit adds there: -4 or +4 in the site's byte
+    uint32_t va, vb;     // c[a], c[b]
 
-    __device__ __forceinline__ void build(const SysParams &p, uint32_t fbase, uint32_t a, uint32_t b)
+    __device__ __forceinline__ explicit FieldView(uint32_t f) : fbase(f) {}
+
+    __device__ __forceinline__ void build(const SysParams &p, uint32_t a, uint32_t b, bool valid)
     {
+        a = valid ? a : 0u;
+        b = valid ? b : 0u;
         uint32_t na[2 * D], nb[2 * D];
         neighbours<D>(p, a, na);
         neighbours<D>(p, b, nb);
@@ -483,11 +364,14 @@ struct FieldMove {
         }
     }
 
-    __device__ __forceinline__ void load(uint32_t &va, uint32_t &vb) const
+    __device__ __forceinline__ void load()
     {
         asm volatile("ld.shared.u8 %0, [%1];" : "=r"(va) : "r"(ca) : "memory");
         asm volatile("ld.shared.u8 %0, [%1];" : "=r"(vb) : "r"(cb) : "memory");
     }
+
+    __device__ __forceinline__ int d4() const { return (int)va - (int)vb; }
+    __device__ __forceinline__ int adj4() const { return adj; }
 
     // Byte counts stay in [0, 8d]: a decrement meets a count that includes
     // the leaving particle, so no borrow or carry crosses a byte.
@@ -499,17 +383,19 @@ struct FieldMove {
     }
 };
 
-template <int D, typename IdxT, int G, bool ST, bool TUN>
-__device__ __forceinline__ void chain_field(const SysParams &p, int w, bool active, uint32_t fbase,
-                                            const uint32_t *thr, unsigned long long *hist,
-                                            uint64_t A, uint32_t iter)
+// The rounds of one walker's chain on G lanes, on a view of its occupation
+// (BitView or FieldView).  A later lane whose prefetched list slot a commit
+// moved is found by comparing slot indices with the committing lane's (one
+// more shuffle) when FIX_BY_SLOT, else by comparing sites; both find the
+// same lanes, and which is faster is a matter of the compiled loop.
+template <int D, typename IdxT, int G, bool ST, bool TUN, bool FIX_BY_SLOT, typename View>
+__device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool active, View v,
+                                             const uint32_t *thr, unsigned long long *hist,
+                                             uint64_t A, uint32_t iter)
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
-    // later lanes whose slot the commit moved are found by comparing sites
-    // (see chain_group; measured on GB300, the site compare is the faster
-    // one here for every G)
-    constexpr bool kFixBySlot = false;
+    constexpr bool kFixBySlot = FIX_BY_SLOT;
     const int lane = threadIdx.x & 31;
     const int j = lane & (G - 1);
     const int gbase = lane - j;
@@ -568,29 +454,28 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
         uint32_t k = kn, m = mn, a = an, b = bn;
         const uint32_t r2 = r2n;
         draw(t0 + G);
-        // lanes without an attempt evaluate sites 0 and 0 so that every lane
-        // can evaluate unconditionally
-        FieldMove<D> mv;
-        mv.build(p, fbase, valid ? a : 0u, valid ? b : 0u);
+        // lanes without an attempt evaluate site 0 so that every lane can
+        // evaluate unconditionally
+        v.build(p, a, b, valid);
         // where this lane's own move would write if it commits
         IdxT *pk = S + k;
         IdxT *pm = S + N + m;
-        // counts of the first round; later rounds load theirs right after
-        // the previous commit, ahead of the bookkeeping
-        uint32_t va, vb;
-        mv.load(va, vb);
-        uint32_t rba = rb + (uint32_t)mv.adj;   // the threshold row plus this attempt's adjacency
+        // state of the first round; later rounds load theirs right after the
+        // previous commit, ahead of the bookkeeping
+        v.load();
+        uint32_t rba = rb + (uint32_t)v.adj4();   // the threshold row plus this attempt's adjacency
         bool pend = valid;                      // this lane's attempt is still undecided
         int rs = gbase;
         while (__any_sync(FULL, pend)) {
-            const uint32_t toff = rba + va - vb;
+            const int d4 = v.d4();
+            const uint32_t toff = rba + (uint32_t)d4;
             uint32_t T;
             if constexpr (ST) {
                 asm volatile("ld.shared.u32 %0, [%1];" : "=r"(T) : "r"(toff));
             } else {
                 T = __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(thr) + toff));
             }
-            const int de4 = (int)va - (int)vb + mv.adj;   // 4 dE
+            const int de4 = d4 + v.adj4();   // 4 dE
             const bool accept = pend && ((T == 0xFFFFFFFFu) || (r2 < T));
             // pending lanes are the group's last ones, so the first accepting
             // lane commits, the pending lanes before it were rejected at the
@@ -599,7 +484,7 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
             const bool commit = bal != 0u;             // the same in every lane of the group
             const bool later = (bal & ltm) != 0u;
             if (accept && !later) {
-                mv.commit();
+                v.commit();
                 *pk = (IdxT)b;
                 *pm = (IdxT)a;
             }
@@ -609,9 +494,9 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
             shfl_pair<IdxT>(a, b, src, a_f, b_f);
             if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
             __syncwarp(FULL);
-            // the next round's counts, loaded before the (rare) fix below,
-            // which reloads them when it moves this lane's sites
-            mv.load(va, vb);
+            // the next round's state, loaded before the (rare) fix below,
+            // which reloads it when it moves this lane's sites
+            v.load();
             // the commit moved list slots k_f and N + m_f: slot k_f held a_f and
             // slot N + m_f held b_f, and every site sits in exactly one slot,
             // so a lane's slot k is k_f exactly when its (current) a is a_f
@@ -620,8 +505,8 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
             if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
                 a = fix_a ? b_f : a;
                 b = fix_b ? a_f : b;
-                mv.build(p, fbase, a, b);
-                mv.load(va, vb);
+                v.build(p, a, b, true);
+                v.load();
             }
             pend = pend && later;
             acc += commit ? 1u : 0u;
@@ -641,7 +526,7 @@ __device__ __forceinline__ void chain_field(const SysParams &p, int w, bool acti
             rs = moved ? src : rs;
             bin += moved ? de_f : 0;
             rb += moved ? (uint32_t)(4 * de_f * width) : 0u;
-            rba = rb + (uint32_t)mv.adj;
+            rba = rb + (uint32_t)v.adj4();
             an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
             bn = (commit && (kFixBySlot ? mn == m_f : bn == b_f)) ? a_f : bn;
         }
@@ -865,12 +750,14 @@ __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &
     uint32_t *bits = bits0 + (size_t)(active ? lw : 0) * p.words;
     unsigned long long *hist = hist_row(p, w, wk.hist_row);
     const uint64_t A = sweeps * (uint64_t)p.N;
+    // slot compare for G = 8, site compare otherwise (measured on GB300)
+    constexpr bool kSlot = (G == 8);
     if (p.d == 2) {
-        if (p.idx16) chain_group<2, uint16_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
-        else chain_group<2, uint32_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
+        if (p.idx16) chain_rounds<2, uint16_t, G, ST, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter);
+        else chain_rounds<2, uint32_t, G, ST, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter);
     } else {
-        if (p.idx16) chain_group<3, uint16_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
-        else chain_group<3, uint32_t, G, SB, ST, TUN>(p, w, active, bits, thr, hist, A, iter);
+        if (p.idx16) chain_rounds<3, uint16_t, G, ST, TUN, kSlot>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter);
+        else chain_rounds<3, uint32_t, G, ST, TUN, kSlot>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter);
     }
 }
 
@@ -967,7 +854,9 @@ __device__ __forceinline__ void field_item(const SysParams &p, const BlockWork &
     const uint32_t fbase = (uint32_t)__cvta_generic_to_shared(fw) +
                            (uint32_t)((size_t)(active ? lw : 0) * field_bytes(p));
     unsigned long long *hist = hist_row(p, w, wk.hist_row);
-    chain_field<D, IdxT, G, ST, TUN>(p, w, active, fbase, thr, hist, sweeps * (uint64_t)p.N, iter);
+    // site compare for moved slots (measured on GB300: the faster one here for every G)
+    chain_rounds<D, IdxT, G, ST, TUN, false>(p, w, active, FieldView<D>(fbase), thr, hist,
+                                             sweeps * (uint64_t)p.N, iter);
     field_finish<IdxT>(p, wk, fw);
 }
 
