@@ -408,10 +408,11 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int width = p.width;
     int bin = active ? p.E[w] - p.e_lo : 0;
-    // the current threshold row, entry dE = 0, as a shared byte address (or
-    // a byte offset into the global table)
+    // threshold rows as shared byte addresses (or byte offsets into the
+    // global table): row of bin b, entry dE = 0, at rbase + b * w4
     const uint32_t thr_s = ST ? (uint32_t)__cvta_generic_to_shared(thr) : 0u;
-    uint32_t rb = thr_s + 4u * (uint32_t)(bin * width + 2 * D);
+    const uint32_t rbase = thr_s + 8u * D;
+    const uint32_t w4 = 4u * (uint32_t)width;
     // histogram entries are added per run of attempts at one energy: carry
     // holds the run's attempts from earlier batches, rs the warp lane of
     // this batch at which it started
@@ -452,7 +453,8 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
         const int n_valid = left < (uint64_t)G ? (int)left : G;
         const bool valid = active && (j < n_valid);
         uint32_t k = kn, m = mn, a = an, b = bn;
-        const uint32_t r2 = r2n;
+        // acceptance T == 2^32 - 1 || r2 < T, as the single compare T >= r2p
+        const uint32_t r2p = (r2n == 0xFFFFFFFFu) ? r2n : r2n + 1u;
         draw(t0 + G);
         // lanes without an attempt evaluate site 0 so that every lane can
         // evaluate unconditionally
@@ -463,7 +465,8 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
         // state of the first round; later rounds load theirs right after the
         // previous commit, ahead of the bookkeeping
         v.load();
-        uint32_t rba = rb + (uint32_t)v.adj4();   // the threshold row plus this attempt's adjacency
+        uint32_t radj = rbase + (uint32_t)v.adj4();   // this attempt's adjacency joins the row address
+        uint32_t rba = (uint32_t)bin * w4 + radj;
         bool pend = valid;                      // this lane's attempt is still undecided
         int rs = gbase;
         while (__any_sync(FULL, pend)) {
@@ -476,7 +479,7 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
                 T = __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(thr) + toff));
             }
             const int de4 = d4 + v.adj4();   // 4 dE
-            const bool accept = pend && ((T == 0xFFFFFFFFu) || (r2 < T));
+            const bool accept = pend && T >= r2p;
             // pending lanes are the group's last ones, so the first accepting
             // lane commits, the pending lanes before it were rejected at the
             // current state and those after it (later) evaluate again
@@ -488,7 +491,9 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
                 *pk = (IdxT)b;
                 *pm = (IdxT)a;
             }
-            const int src = commit ? __ffs(bal) - 1 : gbase;   // the committing warp lane
+            // the committing warp lane (any lane when none commits: what the
+            // shuffles below bring is then not used)
+            const int src = (__ffs(bal) - 1) & 31;
             const int de_f = __shfl_sync(FULL, de4, src) >> 2;
             uint32_t a_f, b_f, k_f = 0, m_f = 0;
             shfl_pair<IdxT>(a, b, src, a_f, b_f);
@@ -507,6 +512,7 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
                 b = fix_b ? a_f : b;
                 v.build(p, a, b, true);
                 v.load();
+                radj = rbase + (uint32_t)v.adj4();
             }
             pend = pend && later;
             acc += commit ? 1u : 0u;
@@ -520,13 +526,14 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
                     tunnel(bin + de_f);
                 }
             } else {
+                // (the test of cnt is not needed, but without it the
+                // compiled loop is 4 % slower)
                 if (moved && j == 0 && cnt) atomicAdd(hist + bin, (unsigned long long)cnt);
             }
             carry = moved ? 0u : carry;
             rs = moved ? src : rs;
             bin += moved ? de_f : 0;
-            rb += moved ? (uint32_t)(4 * de_f * width) : 0u;
-            rba = rb + (uint32_t)v.adj4();
+            rba = (uint32_t)bin * w4 + radj;
             an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
             bn = (commit && (kFixBySlot ? mn == m_f : bn == b_f)) ? a_f : bn;
         }
