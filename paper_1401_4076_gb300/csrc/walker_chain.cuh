@@ -395,7 +395,6 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
-    constexpr bool kFixBySlot = FIX_BY_SLOT;
     const int lane = threadIdx.x & 31;
     const int j = lane & (G - 1);
     const int gbase = lane - j;
@@ -490,6 +489,7 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
                 v.commit();
                 *pk = (IdxT)b;
                 *pm = (IdxT)a;
+                ++acc;                       // summed over the group's lanes at the end
             }
             // the committing warp lane (any lane when none commits: what the
             // shuffles below bring is then not used)
@@ -497,7 +497,7 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
             const int de_f = __shfl_sync(FULL, de4, src) >> 2;
             uint32_t a_f, b_f, k_f = 0, m_f = 0;
             shfl_pair<IdxT>(a, b, src, a_f, b_f);
-            if constexpr (kFixBySlot) shfl_pair<IdxT>(k, m, src, k_f, m_f);
+            if constexpr (FIX_BY_SLOT) shfl_pair<IdxT>(k, m, src, k_f, m_f);
             __syncwarp(FULL);
             // the next round's state, loaded before the (rare) fix below,
             // which reloads it when it moves this lane's sites
@@ -505,8 +505,8 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
             // the commit moved list slots k_f and N + m_f: slot k_f held a_f and
             // slot N + m_f held b_f, and every site sits in exactly one slot,
             // so a lane's slot k is k_f exactly when its (current) a is a_f
-            const bool fix_a = later && (kFixBySlot ? k == k_f : a == a_f);
-            const bool fix_b = later && (kFixBySlot ? m == m_f : b == b_f);
+            const bool fix_a = later && (FIX_BY_SLOT ? k == k_f : a == a_f);
+            const bool fix_b = later && (FIX_BY_SLOT ? m == m_f : b == b_f);
             if (fix_a || fix_b) {            // rare: no warp vote, the lane branches alone
                 a = fix_a ? b_f : a;
                 b = fix_b ? a_f : b;
@@ -515,7 +515,6 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
                 radj = rbase + (uint32_t)v.adj4();
             }
             pend = pend && later;
-            acc += commit ? 1u : 0u;
             // a move ends the run at the old energy: attempts rs .. src - 1 of
             // this batch (the committed one is the first at the new energy)
             const bool moved = commit && de_f != 0;
@@ -534,8 +533,8 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
             rs = moved ? src : rs;
             bin += moved ? de_f : 0;
             rba = (uint32_t)bin * w4 + radj;
-            an = (commit && (kFixBySlot ? kn == k_f : an == a_f)) ? b_f : an;
-            bn = (commit && (kFixBySlot ? mn == m_f : bn == b_f)) ? a_f : bn;
+            an = (commit && (FIX_BY_SLOT ? kn == k_f : an == a_f)) ? b_f : an;
+            bn = (commit && (FIX_BY_SLOT ? mn == m_f : bn == b_f)) ? a_f : bn;
         }
         // the batch's attempts from rs on are at the final energy
         carry += (uint32_t)(gbase + n_valid - rs);
@@ -544,6 +543,8 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
             carry = 0;
         }
     }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
     if (active && j == 0) {
         if (carry) atomicAdd(hist + bin, (unsigned long long)carry);
         p.E[w] = bin + p.e_lo;

@@ -120,3 +120,15 @@ def test_persistent_batched_full_size_sampled():
                 hist, _ = chain.run_walkers(d, L, N, seed, it, sweeps * N, -d * N, 0, T, S, occ, E,
                                             walkers=pick)
             np.testing.assert_array_equal(per[pick], hist)
+
+
+def test_default_launch_is_field_kernel_where_fields_fit():
+    """The library's default launch is the field kernel when every system's
+    neighbour-count fields fit into shared memory at 16 walkers per block
+    (2D L=64: 4 KB per walker), else the group kernel (3D L=32: 32 KB)."""
+    with m.Mucal([(2, 64, 410, 64, 0, 0, 0)]) as mc:
+        assert mc.launch()["kernel"] == m.MUCAL_KERNEL_FIELD
+    with m.Mucal([(3, 32, 3277, 64, 0, 0, 0)]) as mc:
+        assert mc.launch()["kernel"] == m.MUCAL_KERNEL_GROUP
+    with m.Mucal([(2, 16, 32, 8, 0, 0, 0), (3, 32, 3277, 8, 0, 0, 1)]) as mc:
+        assert mc.launch()["kernel"] == m.MUCAL_KERNEL_GROUP
