@@ -245,6 +245,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["mucal", "reference"], default="mucal")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="medium2d")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
+    ap.add_argument("--walkers", type=int, default=0,
+                    help="override the walker count of a one-system workload (the workload "
+                         "name's -w suffix follows)")
     ap.add_argument("--kernel", type=int, default=-1)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--wpb", type=int, default=0)
@@ -269,6 +272,14 @@ def main(argv=None):
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
+    if args.walkers:
+        if len(wl.systems) != 1 or args.walkers < 1:
+            ap.error("--walkers needs a one-system workload and a count >= 1")
+        import dataclasses
+        import re
+        d, L, N, _, lo, hi, seed = wl.systems[0]
+        wl = dataclasses.replace(wl, name=re.sub(r"-w\d+$", f"-w{args.walkers}", wl.name),
+                                 systems=((d, L, N, args.walkers, lo, hi, seed),))
     world, rank, local = _dist_setup()
     args.launch_desc = None
 
