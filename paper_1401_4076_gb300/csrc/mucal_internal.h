@@ -79,15 +79,18 @@ cudaError_t launch_walker_update(const SysParams *dev_sys, const BlockWork *dev_
                                  bool tunnel, int grid, int *next_item, cudaStream_t stream);
 // The other three flavours of the walker update, one translation unit each
 // (walker_kernels_tun.cu, walker_kernels_persist.cu,
-// walker_kernels_persist_tun.cu): the kernel of a launch shape and all 24
-// kernels of the flavour (for their shared-memory attributes).
+// walker_kernels_persist_tun.cu): the kernel of a launch shape and all
+// kWalkerUpdateFns kernels of the flavour (for their shared-memory
+// attributes).
 const void *walker_update_fn_tunnel(const LaunchShape &shape);
 void walker_update_tunnel_fns(const void *(&fns)[kWalkerUpdateFns]);
 const void *walker_update_fn_persist(const LaunchShape &shape);
 void walker_update_persist_fns(const void *(&fns)[kWalkerUpdateFns]);
 const void *walker_update_fn_persist_tun(const LaunchShape &shape);
 void walker_update_persist_tun_fns(const void *(&fns)[kWalkerUpdateFns]);
-// Shared-memory layout of a walker-update block: [threshold table][bitsets].
+// Shared-memory layout of a walker-update block: [threshold table][bitsets]
+// (group and thread kernels) or [threshold table][count fields] (field
+// kernel).
 size_t thr_smem_words(const SysParams &p);
 // Shared-memory bytes of one walker's neighbour-count field (field kernel).
 size_t field_smem_bytes(const SysParams &p);
