@@ -54,7 +54,7 @@ def alg_ops_per_attempt(d: int) -> int:
 # the shape here: when every block is resident at once (147 blocks of 28
 # walkers on 152 SMs) the persistent launch runs the same blocks.
 TRAFFIC_MEASURED = {
-    "2d-L64-N410-w4096": {"bytes": 34.26e6 + 902.58e6, "kernel_sha": "2b4c6ed0703ef37f",
+    "2d-L64-N410-w4096": {"bytes": 33.89e6 + 954.13e6, "kernel_sha": "a476ebb38f79900c",
                           "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28}},
 }
 
