@@ -391,7 +391,10 @@ def main(argv=None):
                                f" ({peak_kind} max clock)",
                 "kernel": KERNEL_NAMES.get(args.launch_desc.get("kernel"), "walker_update"),
                 "kernel_ms": k_ms,
-                "alg_ops_per_attempt": alg_ops_per_attempt(d_max)}
+                "alg_ops_per_attempt": alg_ops_per_attempt(d_max),
+                # independent chains (walkers) per SM: the parallelism that
+                # bounds these latency-bound kernels
+                "chains_per_sm": sum(s[3] for s in systems) / sm_count}
 
     line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
