@@ -351,3 +351,103 @@ def test_batched_uneven_systems_full_size_sampled(launch):
             assert (H >= hist.sum(axis=0)).all()
             for q, w in enumerate(pick):
                 _assert_walker_equal(mc, i, w, S[q], occ[q], E[q])
+
+
+# ------------------------ full size, every walker, in the benchmark shapes --
+# The launch shapes the benchmark's autotuner picks on GB300 (kernel, lanes
+# per walker, walkers per block, bitsets in shared memory, persistent), plus
+# whatever the autotuner picks live for the same weights.
+
+BENCH_SHAPES = {
+    "2d-L64-N410-w4096": dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8,
+                              walkers_per_block=28, bits_in_smem=1, persistent=0),
+    "3d-L32-N3277-w8192": dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=4,
+                               walkers_per_block=56, bits_in_smem=1, persistent=1),
+    "batched-27-systems-w16384": dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16,
+                                      walkers_per_block=8, bits_in_smem=1, persistent=0),
+}
+
+
+def _tuned_shape(systems, lnWs):
+    from paper_1401_4076_gb300.autotune import autotune
+    best, _ = autotune(systems, lnW=lnWs, sweeps=5, repeats=2, finalists=3)
+    return best
+
+
+def _every_walker_one_iteration(systems, sys_ids, sweeps, it, launch, lnWs):
+    """One iteration of every system in one launch; for the systems in
+    sys_ids every walker's histogram and final state against the oracle."""
+    with m.Mucal(systems, per_walker_hist=True) as mc:
+        mc.set_launch(**launch)
+        for i, lnW in enumerate(lnWs):
+            mc.set_weights(i, lnW)
+        mc.run_iteration(sweeps, it)
+        for i in sys_ids:
+            d, L, N, W, lo, hi, seed = systems[i]
+            e_lo, e_hi = _window(d, N, lo, hi)
+            H, per = mc.histogram(i, per_walker=True)
+            assert H.sum() == W * sweeps * N
+            S, occ, E = _oracle_states(d, L, N, W, seed)
+            T = chain.thresholds(d, e_lo, e_hi, lnWs[i])
+            np.testing.assert_array_equal(mc.thresholds(i), T)
+            hist, _ = chain.run_walkers(d, L, N, seed, it, sweeps * N, e_lo, e_hi, T, S, occ, E)
+            np.testing.assert_array_equal(per, hist)
+            np.testing.assert_array_equal(H, hist.sum(axis=0))
+            for w in range(W):
+                _assert_walker_equal(mc, i, w, S[w], occ[w], E[w])
+
+
+@pytest.mark.parametrize("shape", ["bench", "tuned"])
+def test_medium_2d_every_walker_first_iteration(shape):
+    """2D L=64, N=410, 4096 walkers, the first iteration from lnW = 0 at the
+    benchmark's 1000 sweeps (410 000 attempts per walker): all 4096
+    per-walker histograms and final states bit-exact (Eq. 2 summed on the
+    device equals the oracle's sum)."""
+    wl = workloads.MEDIUM_2D
+    d, L, N, W, lo, hi, seed = wl.systems[0]
+    lnWs = [np.zeros(d * N + 1)]
+    launch = BENCH_SHAPES[wl.name] if shape == "bench" else _tuned_shape(wl.systems, lnWs)
+    _every_walker_one_iteration(wl.systems, [0], wl.sweeps, 0, launch, lnWs)
+
+
+@pytest.mark.parametrize("shape", ["bench", "tuned"])
+def test_large_3d_every_walker_of_a_block_range(shape):
+    """3D L=32, N=3277, 8192 walkers in one launch with non-trivial weights:
+    256 walkers spread over the launch (every 32nd, so every block of the
+    shape holds some) compared with the oracle one by one, sum H counts every
+    attempt."""
+    wl = workloads.LARGE_3D
+    d, L, N, W, lo, hi, seed = wl.systems[0]
+    lnW = workloads.random_log_weights(d * N + 1, 3, 0.05)
+    launch = BENCH_SHAPES[wl.name] if shape == "bench" else _tuned_shape(wl.systems, [lnW])
+    sweeps = 20
+    pick = list(range(0, W, 32))
+    with m.Mucal(wl.systems, per_walker_hist=True) as mc:
+        mc.set_launch(**launch)
+        mc.set_weights(0, lnW)
+        mc.run_iteration(sweeps, 0)
+        H, per = mc.histogram(0, per_walker=True)
+        assert H.sum() == W * sweeps * N
+        np.testing.assert_array_equal(H, per.sum(axis=0))
+        S, occ, E = _oracle_states(d, L, N, W, seed, pick)
+        T = chain.thresholds(d, -d * N, 0, lnW)
+        hist, _ = chain.run_walkers(d, L, N, seed, 0, sweeps * N, -d * N, 0, T, S, occ, E,
+                                    walkers=pick)
+        np.testing.assert_array_equal(per[pick], hist)
+        for i, w in enumerate(pick):
+            _assert_walker_equal(mc, 0, w, S[i], occ[i], E[i])
+
+
+@pytest.mark.parametrize("shape", ["bench", "tuned"])
+def test_batched_every_walker_of_two_systems(shape):
+    """The 27-system batch in one launch: every walker of its largest system
+    (3D L=40, N=6400, 2366 walkers) and of the largest 2D system (L=128,
+    N=1638, 606 walkers) bit-exact against the oracle."""
+    wl = workloads.batched_uneven()
+    lnWs = [workloads.random_log_weights(s[0] * s[2] + 1, 200 + i, scale=0.05)
+            for i, s in enumerate(wl.systems)]
+    launch = (BENCH_SHAPES[wl.name] if shape == "bench"
+              else _tuned_shape(wl.systems, lnWs))
+    big3 = max(range(len(wl.systems)), key=lambda i: (wl.systems[i][0] == 3, wl.systems[i][2]))
+    big2 = max(range(len(wl.systems)), key=lambda i: (wl.systems[i][0] == 2, wl.systems[i][2]))
+    _every_walker_one_iteration(wl.systems, [big3, big2], 5, 7, launch, lnWs)
