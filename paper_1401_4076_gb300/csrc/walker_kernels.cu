@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "mucal.h"
@@ -374,22 +375,57 @@ walker_update_noalloc(SysParams p, uint64_t sweeps, uint32_t iter, const unsigne
 
 // Per-device set-up: the device address of the scratch array (the array's
 // name is only a host-side stand-in in host code) and the shared-memory
-// opt-in of the kernel variants.
+// opt-in of the kernel variants.  Both belong to the device's context, so the
+// set-up is remembered together with that context's unique id and redone
+// when the context has been replaced (after cudaDeviceReset the next call
+// finds a new id).
 struct NoAllocDevice {
     unsigned long long *scratch = nullptr;
     int max_smem = 0;
+    unsigned long long ctx_id = 0;
     bool ready = false;
 };
 
 std::mutex g_noalloc_mutex;
 NoAllocDevice g_noalloc_dev[64];
 
+// Unique id of the calling thread's current CUDA context, through the driver
+// entry points the runtime hands out (the library does not link the driver
+// library itself).  False when there is no current context or the entry
+// points are unavailable; the set-up then runs again on the next call.
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrentFn = CUresult (*)(CUcontext *);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+                cudaSuccess && q1 == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrentFn>(f1);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+                cudaSuccess && q2 == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetIdFn>(f2);
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
 cudaError_t noalloc_setup(int dev, NoAllocDevice **out)
 {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     NoAllocDevice &d = g_noalloc_dev[dev];
-    if (!d.ready) {
+    unsigned long long id = 0;
+    const bool known = current_context_id(&id);
+    if (!d.ready || !known || id != d.ctx_id) {
+        d.ready = false;
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
@@ -406,7 +442,8 @@ cudaError_t noalloc_setup(int dev, NoAllocDevice **out)
         }
         d.scratch = static_cast<unsigned long long *>(ptr);
         d.max_smem = smem;
-        d.ready = true;
+        // the symbol lookup has made a context current if none was
+        d.ready = current_context_id(&d.ctx_id);
     }
     *out = &d;
     return cudaSuccess;

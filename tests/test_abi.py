@@ -68,3 +68,24 @@ def test_no_device_is_an_error_not_a_fallback(lib):
 def test_calls_on_null_context_fail(lib):
     assert lib.mucal_run_iteration(None, 1, 0) == m.MUCAL_ERR_INVALID_ARG
     assert lib.mucal_set_weights(None, 0, None, 0) == m.MUCAL_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("desc,msg", [
+    ((2, 64, 100, (1 << 20) + 1, 0, 0, 0), "n_walkers"),
+    # ceil(8000 / 32) * 19201 bins > 2^22 histogram entries of the fixed scratch
+    ((3, 40, 6400, 8000, 0, 0, 0), "histogram entries"),
+    ((2, 16, 300, 8, 0, 0, 0), "0 < N"),
+])
+def test_noalloc_limits_rejected_before_device_use(lib, desc, msg):
+    """The allocation-free call rejects sizes beyond its fixed scratch on the
+    host, before it looks for a device (the pointers are never touched)."""
+    with pytest.raises(m.MucalError) as ei:
+        m.mucal_run_walkers_noalloc(desc, 1, 0, 16, 16, 16, 16, 16, None)
+    assert ei.value.code == m.MUCAL_ERR_INVALID_ARG
+    assert msg in str(ei.value)
+
+
+def test_noalloc_null_buffer_rejected(lib):
+    with pytest.raises(m.MucalError) as ei:
+        m.mucal_run_walkers_noalloc((2, 8, 4, 2, 0, 0, 0), 1, 0, 16, 0, 16, 16, 16, None)
+    assert ei.value.code == m.MUCAL_ERR_INVALID_ARG
