@@ -213,6 +213,42 @@ int mucal_update_weights(void *ctx, int32_t sys, int32_t scheme, double *lnW_out
  * lowest visited energy to the highest).  t_lo = t_hi = 0 restores it. */
 int mucal_set_target_window(void *ctx, int32_t sys, int32_t t_lo, int32_t t_hi);
 
+/* Replace the summed histogram that the next mucal_update_weights of system
+ * sys uses by H (host int64[n_bins], copied).  This is how several processes
+ * that each run part of the walkers with identical weights combine their
+ * histograms (Eq. 2: H^i = sum over processes of H^i_j): every process sums
+ * its local histograms with the others' (for example by an all-reduce) and
+ * hands the total to its own context, so that every process computes the same
+ * next weights (Sec. 2, the redistribution of the weights needs no further
+ * message).  Waits for the context's stream.  Errors: INVALID_ARG (index,
+ * size, a negative count), NOT_READY (no iteration run yet), CUDA. */
+int mucal_set_histogram(void *ctx, int32_t sys, const int64_t *H, int32_t n_bins);
+
+/* Resident blocks per SM of the current walker-update launch shape (the
+ * CUDA occupancy of that kernel at its block size and shared memory) and the
+ * device's SM count.  Not part of the paper; used to state how many walkers'
+ * chains run at once.  Errors: INVALID_ARG, CUDA. */
+int mucal_get_launch_occupancy(void *ctx, int32_t *blocks_per_sm, int32_t *sm_count);
+
+/* One weight update of Sec. 2 on caller-owned host arrays, without a
+ * context: the same double-precision code mucal_update_weights runs.
+ *   scheme     MUCAL_SCHEME_SIMPLE or MUCAL_SCHEME_RECURSIVE
+ *   H          int64[n_bins], the summed histogram of the iteration (in)
+ *   lnW        float64[n_bins], the weights H was sampled with (in), the next
+ *              weights shifted to maximum 0 (out)
+ *   visited    uint8[n_bins] cumulative visited set (in/out; start with zeros)
+ *   pacc       float64[n_bins] accumulated pair weights of the recursion
+ *              (in/out; start with zeros; unused and nullable for SIMPLE)
+ *   t_lo, t_hi flatness target window in bins (t_lo < 0: the visited range)
+ *   flatness_out (nullable) min/max of H over the visited bins of the target
+ *              window, -1 while an end of it is unvisited.
+ * Errors: INVALID_ARG (unknown scheme, NULL arrays, n_bins < 1, a negative
+ * H, a non-finite lnW, a target window outside the bins).  Message:
+ * mucal_last_error(NULL). */
+int mucal_weight_update(int32_t scheme, int32_t n_bins, const int64_t *H, double *lnW,
+                        uint8_t *visited, double *pacc, int32_t t_lo, int32_t t_hi,
+                        double *flatness_out);
+
 /* Copy walker w's state of system sys to host buffers (any may be NULL):
  * occ uint8[V] (n_i), S int32[V] (particle then empty sites), E (energy). */
 int mucal_get_walker_state(void *ctx, int32_t sys, int32_t walker, uint8_t *occ, int32_t *S,
@@ -299,6 +335,24 @@ int mucal_multi_histogram(const int64_t *H, const double *lnW, int32_t K, int32_
  * gas is E_Ising = 4 (E - c(N)) at fixed magnetisation M = 2N - V, and the
  * Ising temperature is 4T.  Errors: INVALID_ARG (d outside {2,3}, V < 1,
  * N outside [0, V], NULL c_N). */
+/* Estimate of ln Omega(E) from one histogram and the weights it was
+ * sampled with: the ideal weights W = 1/Omega give a flat histogram (Sec. 2),
+ * so Omega(E) is proportional to H(E) / W(E).  ln_omega (host
+ * float64[n_bins]) receives ln H(E) - lnW(E) on the bins with H > 0, NaN
+ * elsewhere, shifted so that the visited bins together hold all C(V, N)
+ * configurations of N particles on V sites.  Errors: INVALID_ARG (NULL
+ * arrays, n_bins < 1, a negative H, no visited bin, a non-finite lnW where
+ * H > 0, V < 1 or N outside [0, V]).  Message: mucal_last_error(NULL). */
+int mucal_ln_omega(const int64_t *H, const double *lnW, int32_t n_bins, int64_t V, int64_t N,
+                   double *ln_omega);
+
+/* Shift the finite entries of ln_omega[n_bins] in place so that their
+ * exponentials sum to C(V, N) (every configuration has some energy); NaN
+ * entries (unvisited energies) stay NaN.  For the output of
+ * mucal_multi_histogram.  Errors: INVALID_ARG (NULL, n_bins < 1, no finite
+ * entry, V < 1 or N outside [0, V]). */
+int mucal_ln_omega_normalise(double *ln_omega, int32_t n_bins, int64_t V, int64_t N);
+
 int mucal_ising_constant(int32_t d, int64_t V, int64_t N, double J, double *c_N);
 
 /* mucal_reweight of system sys's last summed histogram with the weights it
@@ -430,14 +484,17 @@ int mucal_droplet_lambda(int32_t d, double Delta, double *lambda);
  * ceil(n_walkers / 32) * n_bins <= 4194304; larger sizes return
  * MUCAL_ERR_INVALID_ARG with a message.  Energies outside the window or list
  * entries outside the lattice are detected on the device and reported as
- * MUCAL_ERR_INVALID_ARG (the state is then left unchanged).  The first call
- * on a device looks up the scratch array's device address and sets the
- * kernels' shared-memory limit; make that first call before any stream
- * capture.  All calls share the one scratch array, which keeps the last
- * call's contents (the call clears what must start at zero): calls that
- * overlap on the GPU, from several streams or threads, race and give wrong
- * results.  mucal_run_walkers_noalloc_error() returns the message of the
- * calling thread's last failure. */
+ * MUCAL_ERR_INVALID_ARG (bits, S and E are then left unchanged; H is
+ * cleared).  The first call on a device looks up the scratch array's device
+ * address and sets the kernels' shared-memory limit; make that first call
+ * before any stream capture.  The look-up is repeated when the device's
+ * context has been replaced (after cudaDeviceReset).  Every call reads the
+ * input check's result back to the host, so it returns only after
+ * cuda_stream has finished its work.  All calls share the one scratch
+ * array, which keeps the last call's contents (the call clears what must
+ * start at zero): calls that overlap on the GPU, from several streams or
+ * threads, race and give wrong results.  mucal_run_walkers_noalloc_error()
+ * returns the message of the calling thread's last failure. */
 int mucal_run_walkers_noalloc(const mucal_system_desc *sys, int64_t sweeps, uint32_t iteration,
                               uint32_t *bits, void *S, int32_t *E, const uint32_t *thr, uint64_t *H,
                               void *cuda_stream);

@@ -5,6 +5,7 @@
 // (Eqs. 8-10).  Double precision, no device work: the inputs are a few
 // hundred bins.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -158,6 +159,49 @@ int mucal_multi_histogram(const int64_t *H, const double *lnW, int32_t K, int32_
         if (num[b] > 0.0) ln_omega[b] -= mx;
     if (iterations) *iterations = std::min(it, max_iter);
     return MUCAL_OK;
+}
+
+int mucal_ln_omega_normalise(double *ln_omega, int32_t n_bins, int64_t V, int64_t N)
+{
+    if (!ln_omega || n_bins < 1) return bad("need ln_omega and n_bins >= 1");
+    if (V < 1 || N < 0 || N > V) return bad("need V >= 1 and 0 <= N <= V");
+    // logsumexp over the finite entries, shifted by their maximum
+    double mx = -INFINITY;
+    for (int b = 0; b < n_bins; ++b)
+        if (std::isfinite(ln_omega[b])) mx = std::max(mx, ln_omega[b]);
+    if (!std::isfinite(mx)) return bad("no finite entry to normalise");
+    double sum = 0.0;
+    for (int b = 0; b < n_bins; ++b)
+        if (std::isfinite(ln_omega[b])) sum += std::exp(ln_omega[b] - mx);
+    const double lse = mx + std::log(sum);
+    // ln C(V, N): every configuration has some energy
+    const double ln_total = std::lgamma((double)V + 1.0) - std::lgamma((double)N + 1.0) -
+                            std::lgamma((double)(V - N) + 1.0);
+    for (int b = 0; b < n_bins; ++b)
+        if (std::isfinite(ln_omega[b])) ln_omega[b] += ln_total - lse;
+    return MUCAL_OK;
+}
+
+int mucal_ln_omega(const int64_t *H, const double *lnW, int32_t n_bins, int64_t V, int64_t N,
+                   double *ln_omega)
+{
+    if (!H || !lnW || !ln_omega) return bad("H, lnW and ln_omega must not be NULL");
+    if (n_bins < 1) return bad("n_bins must be >= 1");
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    bool any = false;
+    for (int b = 0; b < n_bins; ++b) {
+        if (H[b] < 0) return bad("H[%d] is negative", b);
+        if (H[b] == 0) {
+            ln_omega[b] = nan;
+            continue;
+        }
+        if (!std::isfinite(lnW[b])) return bad("lnW[%d] is not finite", b);
+        // W = 1/Omega makes H flat (Sec. 2): Omega(E) is proportional to H(E) / W(E)
+        ln_omega[b] = std::log((double)H[b]) - lnW[b];
+        any = true;
+    }
+    if (!any) return bad("no visited bin (H is zero everywhere)");
+    return mucal_ln_omega_normalise(ln_omega, n_bins, V, N);
 }
 
 int mucal_ising_constant(int32_t d, int64_t V, int64_t N, double J, double *c_N)

@@ -140,88 +140,99 @@ int upload_thresholds(Context *c, System &s)
     return MUCAL_OK;
 }
 
-void normalise_max_zero(std::vector<double> &w)
+void normalise_max_zero(double *w, int n)
 {
     double mx = -INFINITY;
-    for (double v : w) mx = std::max(mx, v);
-    for (double &v : w) v -= mx;
+    for (int b = 0; b < n; ++b) mx = std::max(mx, w[b]);
+    for (int b = 0; b < n; ++b) w[b] -= mx;
 }
 
 // W^{i+1} = W^i / H^i where H^i > 0 (Sec. 2), in logs.
-void update_simple(System &s)
+void simple_step(int nb, const int64_t *H, double *lnW, uint8_t *visited)
 {
-    const int nb = s.p.n_bins;
     for (int b = 0; b < nb; ++b) {
-        if (s.H[b] > 0) {
-            s.visited[b] = 1;
-            s.lnW[b] -= std::log((double)s.H[b]);
+        if (H[b] > 0) {
+            visited[b] = 1;
+            lnW[b] -= std::log((double)H[b]);
         }
     }
-    normalise_max_zero(s.lnW);
+    normalise_max_zero(lnW, nb);
 }
 
 // Accumulated-statistics recursion on consecutive members of the cumulative
 // visited set (the recursive scheme cited in Sec. 2).
-void update_recursive(System &s)
+void recursive_step(int nb, const int64_t *H, double *w, uint8_t *visited, double *pacc)
 {
-    const int nb = s.p.n_bins;
     for (int b = 0; b < nb; ++b)
-        if (s.H[b] > 0) s.visited[b] = 1;
+        if (H[b] > 0) visited[b] = 1;
     std::vector<int> mem;
     mem.reserve(nb);
     for (int b = 0; b < nb; ++b)
-        if (s.visited[b]) mem.push_back(b);
+        if (visited[b]) mem.push_back(b);
     if (mem.empty()) {
-        normalise_max_zero(s.lnW);
+        normalise_max_zero(w, nb);
         return;
     }
-    const std::vector<double> old = s.lnW;
-    std::vector<double> &w = s.lnW;
+    const std::vector<double> old(w, w + nb);
     // rebuild from the top member downwards
     for (size_t j = mem.size() - 1; j >= 1; --j) {
         const int hi = mem[j], lo = mem[j - 1];
         double lnr = old[hi] - old[lo];
-        const double hlo = (double)s.H[lo], hhi = (double)s.H[hi];
+        const double hlo = (double)H[lo], hhi = (double)H[hi];
         const double g = (hlo > 0.0 && hhi > 0.0) ? hlo * hhi / (hlo + hhi) : 0.0;
-        s.pacc[hi] += g;
-        if (g > 0.0) lnr += (g / s.pacc[hi]) * (std::log(hlo) - std::log(hhi));
+        pacc[hi] += g;
+        if (g > 0.0) lnr += (g / pacc[hi]) * (std::log(hlo) - std::log(hhi));
         w[lo] = w[hi] - lnr;
     }
     // bins outside the visited set ride with the nearest member above
     // (or the top member when none is above)
     int next_member = -1;
     for (int b = nb - 1; b >= 0; --b) {
-        if (s.visited[b]) {
+        if (visited[b]) {
             next_member = b;
             continue;
         }
         const int ref = next_member >= 0 ? next_member : mem.back();
         w[b] = old[b] + (w[ref] - old[ref]);
     }
-    normalise_max_zero(w);
+    normalise_max_zero(w, nb);
 }
 
-double flatness(const System &s)
+// min/max of H over the visited bins of the target window [lo, hi] (bins;
+// lo < 0 selects the visited range), -1 while an end of it is unvisited.
+double flatness_of(int nb, const int64_t *H, const uint8_t *visited, int t_lo, int t_hi)
 {
-    const int nb = s.p.n_bins;
     int first = -1, last = -1;
     for (int b = 0; b < nb; ++b)
-        if (s.visited[b]) {
+        if (visited[b]) {
             if (first < 0) first = b;
             last = b;
         }
     if (first < 0) return -1.0;
-    const int lo = s.target_default ? first : s.t_lo;
-    const int hi = s.target_default ? last : s.t_hi;
-    if (!s.visited[lo] || !s.visited[hi]) return -1.0;
+    const int lo = t_lo < 0 ? first : t_lo;
+    const int hi = t_lo < 0 ? last : t_hi;
+    if (!visited[lo] || !visited[hi]) return -1.0;
     double mn = INFINITY, mx = 0.0;
     for (int b = lo; b <= hi; ++b) {
-        if (!s.visited[b]) continue;
-        const double h = (double)s.H[b];
+        if (!visited[b]) continue;
+        const double h = (double)H[b];
         mn = std::min(mn, h);
         mx = std::max(mx, h);
     }
     return mx > 0.0 ? mn / mx : 0.0;
+}
+
+void update_simple(System &s) { simple_step(s.p.n_bins, s.H.data(), s.lnW.data(), s.visited.data()); }
+
+void update_recursive(System &s)
+{
+    recursive_step(s.p.n_bins, s.H.data(), s.lnW.data(), s.visited.data(), s.pacc.data());
+}
+
+double flatness(const System &s)
+{
+    return flatness_of(s.p.n_bins, s.H.data(), s.visited.data(), s.target_default ? -1 : s.t_lo,
+                       s.t_hi);
 }
 
 int check_desc(const mucal_system_desc &d, int i)
@@ -891,6 +902,62 @@ int mucal_update_weights(void *ctx, int32_t sys, int32_t scheme, double *lnW_out
     if (rc != MUCAL_OK) return rc;
     if (lnW_out) std::copy(s.lnW.begin(), s.lnW.end(), lnW_out);
     if (flatness_out) *flatness_out = f;
+    return MUCAL_OK;
+}
+
+int mucal_set_histogram(void *ctx, int32_t sys, const int64_t *H, int32_t n_bins)
+{
+    Context *c = as_ctx(ctx);
+    int rc = check_sys(c, sys);
+    if (rc != MUCAL_OK) return rc;
+    System &s = c->sys[sys];
+    if (!H || n_bins != s.p.n_bins) return fail(c, MUCAL_ERR_INVALID_ARG, "H must hold n_bins = %d", s.p.n_bins);
+    if (!c->ran) return fail(c, MUCAL_ERR_NOT_READY, "no iteration has been run");
+    for (int b = 0; b < n_bins; ++b)
+        if (H[b] < 0) return fail(c, MUCAL_ERR_INVALID_ARG, "H[%d] is negative", b);
+    // the local histogram must not land on top of the given one later
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::copy(H, H + n_bins, s.H.begin());
+    s.hist_on_host = true;
+    return MUCAL_OK;
+}
+
+int mucal_get_launch_occupancy(void *ctx, int32_t *blocks_per_sm, int32_t *sm_count)
+{
+    Context *c = as_ctx(ctx);
+    if (!c || !blocks_per_sm || !sm_count) return MUCAL_ERR_INVALID_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const void *fn = mucal::walker_update_fn(c->shape, c->tunnel);
+    if (!fn) return fail(c, MUCAL_ERR_INVALID_ARG, "no kernel for the current launch shape");
+    int per_sm = 0, sms = 0;
+    CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, fn, c->shape.walkers_per_block * c->shape.lanes, c->shape.smem_bytes));
+    CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    *blocks_per_sm = per_sm;
+    *sm_count = sms;
+    return MUCAL_OK;
+}
+
+int mucal_weight_update(int32_t scheme, int32_t n_bins, const int64_t *H, double *lnW,
+                        uint8_t *visited, double *pacc, int32_t t_lo, int32_t t_hi,
+                        double *flatness_out)
+{
+    if (scheme != MUCAL_SCHEME_SIMPLE && scheme != MUCAL_SCHEME_RECURSIVE)
+        return fail(nullptr, MUCAL_ERR_INVALID_ARG, "unknown scheme %d", scheme);
+    if (n_bins < 1 || !H || !lnW || !visited || (scheme == MUCAL_SCHEME_RECURSIVE && !pacc))
+        return fail(nullptr, MUCAL_ERR_INVALID_ARG, "need n_bins >= 1 and H, lnW, visited (and pacc)");
+    if (t_lo >= 0 && (t_hi < t_lo || t_hi >= n_bins))
+        return fail(nullptr, MUCAL_ERR_INVALID_ARG, "target bins must satisfy 0 <= t_lo <= t_hi < n_bins");
+    for (int b = 0; b < n_bins; ++b) {
+        if (H[b] < 0) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "H[%d] is negative", b);
+        if (!std::isfinite(lnW[b])) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "lnW[%d] is not finite", b);
+    }
+    if (scheme == MUCAL_SCHEME_SIMPLE)
+        simple_step(n_bins, H, lnW, visited);
+    else
+        recursive_step(n_bins, H, lnW, visited, pacc);
+    if (flatness_out) *flatness_out = flatness_of(n_bins, H, visited, t_lo < 0 ? -1 : t_lo, t_hi);
     return MUCAL_OK;
 }
 

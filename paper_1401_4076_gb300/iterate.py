@@ -26,15 +26,8 @@ def ln_binomial(V: int, N: int) -> float:
 def ln_omega_estimate(lnW: np.ndarray, H: np.ndarray, V: int, N: int) -> np.ndarray:
     """ln Omega(E) = ln H(E) - lnW(E) on visited bins (W = 1/Omega makes H flat,
     Sec. 2), shifted so that the visited bins carry all C(V, N) states; NaN
-    where H = 0."""
-    H = np.asarray(H)
-    out = np.full(len(H), np.nan)
-    vis = H > 0
-    out[vis] = np.log(H[vis].astype(np.float64)) - np.asarray(lnW)[vis]
-    mx = out[vis].max()
-    lse = mx + math.log(np.exp(out[vis] - mx).sum())
-    out[vis] += ln_binomial(V, N) - lse
-    return out
+    where H = 0 (computed by the library)."""
+    return m.mucal_ln_omega(H, lnW, V, N)
 
 
 @dataclass
@@ -57,11 +50,7 @@ def ln_omega_multi(history, V: int, N: int) -> np.ndarray:
     H = np.stack([h for h, _ in history])
     W = np.stack([w for _, w in history])
     lo, _ = m.mucal_multi_histogram(H, W)
-    vis = ~np.isnan(lo)
-    mx = lo[vis].max()
-    lse = mx + math.log(np.exp(lo[vis] - mx).sum())
-    lo[vis] += ln_binomial(V, N) - lse
-    return lo
+    return m.mucal_ln_omega_normalise(lo, V, N)
 
 
 def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None, goal=0.5,

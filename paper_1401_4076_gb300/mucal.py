@@ -48,7 +48,8 @@ EXPORTED = [
     "mucal_droplet_lambda", "mucal_replica_exchange", "mucal_set_tunnel_window",
     "mucal_get_tunnel_counts", "mucal_reset_tunnel_counts", "mucal_set_graph_mode",
     "mucal_mlp_forward_tcgen05", "mucal_mlp_use_tcgen05", "mucal_multi_histogram",
-    "mucal_ising_constant",
+    "mucal_ising_constant", "mucal_set_histogram", "mucal_get_launch_occupancy",
+    "mucal_weight_update", "mucal_ln_omega", "mucal_ln_omega_normalise",
 ]
 
 
@@ -141,6 +142,11 @@ def load_library(path: str = LIB_PATH):
         "mucal_mlp_use_tcgen05": (ctypes.c_int, [P, I32]),
         "mucal_multi_histogram": (ctypes.c_int, [P, P, I32, I32, I32, ctypes.c_double, P, P]),
         "mucal_ising_constant": (ctypes.c_int, [I32, I64, I64, ctypes.c_double, P]),
+        "mucal_set_histogram": (ctypes.c_int, [P, I32, P, I32]),
+        "mucal_get_launch_occupancy": (ctypes.c_int, [P, P, P]),
+        "mucal_weight_update": (ctypes.c_int, [I32, I32, P, P, P, P, I32, I32, P]),
+        "mucal_ln_omega": (ctypes.c_int, [P, P, I32, I64, I64, P]),
+        "mucal_ln_omega_normalise": (ctypes.c_int, [P, I32, I64, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -367,6 +373,66 @@ def mucal_ising_constant(d, V, N, J=1.0):
     return c.value
 
 
+def mucal_set_histogram(ctx, sys, H):
+    """Hand system sys a summed histogram (e.g. the sum over processes) for
+    its next weight update."""
+    h = np.ascontiguousarray(H, dtype=np.int64)
+    _check(load_library().mucal_set_histogram(ctx, sys, _ptr(h), h.size), ctx)
+
+
+def mucal_get_launch_occupancy(ctx):
+    """(resident blocks per SM of the current launch shape, SM count)."""
+    b = ctypes.c_int32()
+    n = ctypes.c_int32()
+    _check(load_library().mucal_get_launch_occupancy(ctx, ctypes.addressof(b),
+                                                     ctypes.addressof(n)), ctx)
+    return b.value, n.value
+
+
+class WeightState:
+    """Host arrays of one weight iteration (lnW, cumulative visited set,
+    accumulated pair weights) for ``mucal_weight_update``."""
+
+    def __init__(self, n_bins, lnW=None):
+        self.lnW = np.zeros(n_bins) if lnW is None else np.array(lnW, dtype=np.float64)
+        self.visited = np.zeros(n_bins, dtype=np.uint8)
+        self.pacc = np.zeros(n_bins)
+
+
+def mucal_weight_update(state, H, scheme=MUCAL_SCHEME_RECURSIVE, target=None):
+    """One weight update of Sec. 2 on a WeightState, in place; returns the
+    flatness.  target: (t_lo, t_hi) in bins, or None for the visited range."""
+    h = np.ascontiguousarray(H, dtype=np.int64)
+    n = h.size
+    if state.lnW.size != n:
+        raise ValueError("H and the weight state differ in length")
+    t_lo, t_hi = (-1, -1) if target is None else (int(target[0]), int(target[1]))
+    f = ctypes.c_double()
+    _check(load_library().mucal_weight_update(int(scheme), n, _ptr(h), _ptr(state.lnW),
+                                              _ptr(state.visited), _ptr(state.pacc), t_lo, t_hi,
+                                              ctypes.addressof(f)), None)
+    return f.value
+
+
+def mucal_ln_omega(H, lnW, V, N):
+    """ln Omega(E) = ln H - lnW on visited bins, normalised to C(V, N) states."""
+    h = np.ascontiguousarray(H, dtype=np.int64)
+    w = np.ascontiguousarray(lnW, dtype=np.float64)
+    if h.size != w.size:
+        raise ValueError("H and lnW differ in length")
+    out = np.zeros(h.size)
+    _check(load_library().mucal_ln_omega(_ptr(h), _ptr(w), h.size, int(V), int(N), _ptr(out)),
+           None)
+    return out
+
+
+def mucal_ln_omega_normalise(ln_omega, V, N):
+    """Shift finite entries so that their exponentials sum to C(V, N)."""
+    out = np.array(ln_omega, dtype=np.float64)
+    _check(load_library().mucal_ln_omega_normalise(_ptr(out), out.size, int(V), int(N)), None)
+    return out
+
+
 def mucal_reweight_system(ctx, sys, n_bins, beta, obs=None):
     b, o, n_obs, mE, mE2, out = _reweight_args(beta, obs, n_bins)
     _check(load_library().mucal_reweight_system(ctx, sys, _ptr(b), b.size, _ptr(o), n_obs,
@@ -512,6 +578,12 @@ class Mucal:
 
     def set_target_window(self, sys, t_lo, t_hi):
         mucal_set_target_window(self.ctx, sys, t_lo, t_hi)
+
+    def set_histogram(self, sys, H):
+        mucal_set_histogram(self.ctx, sys, H)
+
+    def occupancy(self):
+        return mucal_get_launch_occupancy(self.ctx)
 
     def walker_state(self, sys, walker):
         return mucal_get_walker_state(self.ctx, sys, walker, self.info[sys]["V"])

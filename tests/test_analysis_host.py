@@ -187,3 +187,111 @@ def test_ising_constant_matches_oracle():
         assert m.mucal_ising_constant(d, V, N) == pytest.approx(muca.ising_constant(d, L, N), rel=1e-15)
     with pytest.raises(m.MucalError):
         m.mucal_ising_constant(4, 10, 1)
+
+
+# ------------------------------------- context-free weight update and ln Omega
+
+def _histogram_sequence(nb, n_iter, seed):
+    """Histograms whose visited range grows and moves, with gaps and zeros."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_iter):
+        H = np.zeros(nb, dtype=np.int64)
+        lo = max(0, nb // 2 - 3 * i - int(rng.integers(0, 3)))
+        hi = min(nb, nb // 2 + 2 * i + 5)
+        H[lo:hi] = rng.integers(1, 10 ** 7, hi - lo)
+        H[lo + rng.integers(0, max(1, hi - lo), 2)] = 0
+        out.append(H)
+    return out
+
+
+@pytest.mark.parametrize("nb", [1, 9, 161])
+def test_weight_update_matches_oracle_recursion(nb):
+    """mucal_weight_update (the code the contexts run) against the oracle's
+    recursion and simple iteration of Sec. 2: weights to 1e-12, visited set
+    and accumulated pair weights, flatness."""
+    from oracle.recursion import flatness, recursive_update, simple_update
+    seq = _histogram_sequence(nb, 12, nb)
+    st = m.WeightState(nb)
+    lnW = np.zeros(nb)
+    s_cum = np.zeros(nb, bool)
+    phat = np.zeros(nb)
+    for H in seq:
+        f = m.mucal_weight_update(st, H, m.MUCAL_SCHEME_RECURSIVE)
+        lnW, s_cum, phat = recursive_update(lnW, H, s_cum, phat)
+        np.testing.assert_allclose(st.lnW, lnW, rtol=1e-12, atol=1e-12 * max(1, np.abs(lnW).max()))
+        np.testing.assert_array_equal(st.visited.astype(bool), s_cum)
+        np.testing.assert_allclose(st.pacc, phat, rtol=1e-12)
+        assert f == pytest.approx(flatness(H, s_cum), rel=1e-15, abs=0)
+    st = m.WeightState(nb)
+    lnW = np.zeros(nb)
+    for H in seq:
+        m.mucal_weight_update(st, H, m.MUCAL_SCHEME_SIMPLE)
+        lnW = simple_update(lnW, H)
+        np.testing.assert_allclose(st.lnW, lnW, rtol=1e-12, atol=1e-12 * max(1, np.abs(lnW).max()))
+
+
+def test_weight_update_target_window_and_errors():
+    from oracle.recursion import flatness
+    H = np.array([0, 5, 10, 20, 0, 40], dtype=np.int64)
+    st = m.WeightState(6)
+    f = m.mucal_weight_update(st, H, m.MUCAL_SCHEME_RECURSIVE, target=(1, 3))
+    assert f == pytest.approx(flatness(H, st.visited.astype(bool), 1, 3)) == 0.25
+    st2 = m.WeightState(6)
+    assert m.mucal_weight_update(st2, H, m.MUCAL_SCHEME_RECURSIVE, target=(0, 3)) == -1.0
+    with pytest.raises(m.MucalError):
+        m.mucal_weight_update(m.WeightState(6), H, 7)
+    with pytest.raises(m.MucalError):
+        m.mucal_weight_update(m.WeightState(6), -H, m.MUCAL_SCHEME_SIMPLE)
+    with pytest.raises(m.MucalError):
+        m.mucal_weight_update(m.WeightState(6), H, m.MUCAL_SCHEME_SIMPLE, target=(2, 9))
+
+
+def test_ln_omega_matches_oracle():
+    """O8: ln Omega = ln H - lnW on visited bins, normalised to C(V, N)."""
+    from oracle.recursion import ln_omega
+    rng = np.random.default_rng(11)
+    for V, N, nb in ((16, 8, 13), (4096, 410, 821), (110592, 11059, 300)):
+        H = rng.integers(0, 10 ** 9, nb)
+        H[rng.random(nb) < 0.2] = 0
+        H[0] = 3
+        lnW = rng.normal(scale=50.0, size=nb)
+        got = m.mucal_ln_omega(H, lnW, V, N)
+        ref = ln_omega(lnW, H, V, N)
+        np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+        v = ~np.isnan(ref)
+        np.testing.assert_allclose(got[v], ref[v], rtol=1e-12, atol=1e-12 * np.abs(ref[v]).max())
+    with pytest.raises(m.MucalError):
+        m.mucal_ln_omega(np.zeros(4, np.int64), np.zeros(4), 16, 8)
+
+
+def test_ln_omega_of_exact_enumeration():
+    """With the exact multicanonical histogram H = Omega W (4x4, N = 8), the
+    estimate returns the enumerated ln Omega itself."""
+    om = chain.enumerate_omega(2, 4, 8)
+    nb = 2 * 8 + 1
+    Om = np.zeros(nb)
+    for e, c in om.items():
+        Om[e + 16] = c
+    lnW = np.where(Om > 0, -np.log(np.where(Om > 0, Om, 1)), 0.0)
+    H = np.where(Om > 0, 1000, 0).astype(np.int64)       # flat: H = Omega W x 1000
+    got = m.mucal_ln_omega(H, lnW, 16, 8)
+    v = Om > 0
+    np.testing.assert_allclose(got[v], np.log(Om[v]), rtol=0, atol=1e-12)
+    assert np.isnan(got[~v]).all()
+
+
+def test_ln_omega_normalise_of_multi_histogram_matches_oracle():
+    from oracle.recursion import multi_histogram
+    rng = np.random.default_rng(3)
+    nb = 60
+    H = rng.integers(1, 10 ** 6, (3, nb))
+    H[0, :10] = 0
+    W = rng.normal(scale=5.0, size=(3, nb))
+    lo, _ = m.mucal_multi_histogram(H, W)
+    ref, _ = multi_histogram(H, W)
+    got = m.mucal_ln_omega_normalise(lo, 1000, 100)
+    # the oracle's combination normalised by its own definition: logsumexp = ln C(V, N)
+    v = ~np.isnan(ref)
+    shift = (math.lgamma(1001) - math.lgamma(101) - math.lgamma(901)) - np.logaddexp.reduce(ref[v])
+    np.testing.assert_allclose(got[v], ref[v] + shift, rtol=1e-9, atol=1e-9)
