@@ -35,15 +35,23 @@ WORKLOADS = {
     "large3d": workloads.LARGE_3D,
     "batched": workloads.batched_uneven(),
 }
+# one-system workloads timed briefly beside the headline
+EXTRA_WORKLOADS = ("medium2d", "large3d")
 METRIC = "attempted moves/s"
 
-# Algorithmic integer work per attempted move (thread-instruction equivalents),
-# used for the issue-slot roofline: Philox4x32-10 (10 rounds x (4 multiplies,
-# 4 xor, 2 key adds) = 100), two multiply-high index maps (2), list reads (2),
-# neighbour sites (2 sites x 5 ops per axis), occupancy bit tests
-# (2 x 2d x 3 ops), dE and threshold compare (6), histogram run-length (2).
+# Algorithmic integer work per attempted move, in thread-instruction
+# equivalents, for the issue-slot roofline: one Philox4x32-10 block counted
+# as 70 integer operations (ten rounds of two 32x32->64 multiplies, the xors
+# with the key and the key bumps: 60-80 operations depending on how a
+# wide multiply is counted; the middle is taken), the two multiply-high index
+# maps (2), the reads of P[k] and Q[m] (2), the 2*2d occupancy bit tests
+# (4d), the threshold compare (1) and the histogram increment (1):
+# 84 in 2D, 88 in 3D.
+PHILOX_OPS = 70
+
+
 def alg_ops_per_attempt(d: int) -> int:
-    return 100 + 2 + 2 + 2 * 5 * d + 2 * 2 * d * 3 + 6 + 2
+    return PHILOX_OPS + 2 + 2 + 4 * d + 1 + 1
 
 
 # DRAM bytes (read + write) of one walker-update launch of a workload's
@@ -58,20 +66,34 @@ TRAFFIC_MEASURED = {
                           "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28}},
 }
 
+# Executed instructions per attempted move of the walker-update kernel, from
+# one ncu capture of a launch of the workload (smsp__inst_executed.sum x 32
+# and smsp__thread_inst_executed.sum, divided by the launch's attempts), under
+# the same validity rule as the traffic record: launch shape and kernel source.
+INSTR_MEASURED = {}
+
 KERNEL_NAMES = {0: "walker_update_thread", 1: "walker_update_group", 2: "walker_update_field"}
 
 
-def _measured_traffic(workload: str, sweeps_default: bool, launch: dict):
+def _kernel_sha() -> str:
     import hashlib
-    rec = TRAFFIC_MEASURED.get(workload)
+    # the walker-update kernels are compiled from walker_chain.cuh
+    with open(os.path.join(ROOT, "paper_1401_4076_gb300", "csrc", "walker_chain.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _record_for(table: dict, workload: str, sweeps_default: bool, launch: dict):
+    rec = table.get(workload)
     if rec is None or not sweeps_default:
         return None
     if any(launch.get(k) != v for k, v in rec["launch"].items()):
         return None
-    # the walker-update kernels are compiled from walker_chain.cuh
-    with open(os.path.join(ROOT, "paper_1401_4076_gb300", "csrc", "walker_chain.cuh"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return rec["bytes"] if sha == rec["kernel_sha"] else None
+    return rec if _kernel_sha() == rec["kernel_sha"] else None
+
+
+def _measured_traffic(workload: str, sweeps_default: bool, launch: dict):
+    rec = _record_for(TRAFFIC_MEASURED, workload, sweeps_default, launch)
+    return None if rec is None else rec["bytes"]
 
 
 def _peaks():
@@ -155,13 +177,34 @@ def _barrier(world):
 
 
 def shard_systems(systems, rank):
-    """Weak scaling: rank r runs an independent copy of the workload with its
-    own walker seeds (seed_base shifted past every walker of lower ranks)."""
+    """Walkers of rank r: every system keeps its walker count per rank, with
+    walker seeds shifted past every walker of the lower ranks, so the ranks
+    together run one multicanonical simulation with world x n_walkers
+    walkers per system (weak scaling: fixed work per GPU)."""
     total = sum(s[3] for s in systems)
     out = []
     for (d, L, N, W, lo, hi, seed) in systems:
         out.append((d, L, N, W, lo, hi, seed + rank * total))
     return out
+
+
+def allreduce_histograms(mc, n_sys, world, device):
+    """Eq. 2 across processes: sum every system's histogram over the ranks
+    (one int64 all-reduce per iteration) and hand the totals back, so that
+    every rank computes the same next weights."""
+    if world <= 1:
+        return
+    import torch
+    import torch.distributed as dist
+    Hs = [mc.histogram(s) for s in range(n_sys)]
+    sizes = [h.size for h in Hs]
+    t = torch.from_numpy(np.concatenate(Hs)).to(device)
+    dist.all_reduce(t)
+    tot = t.cpu().numpy()
+    off = 0
+    for s, n in enumerate(sizes):
+        mc.set_histogram(s, tot[off:off + n])
+        off += n
 
 
 def cpu_oracle_rate(wl, budget_s: float, seed_offset: int = 0):
@@ -243,7 +286,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mucal", "reference"], default="mucal")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="medium2d")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched",
+                    help="the headline workload (default: the 27-system batch, the largest "
+                         "workload on one GPU)")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
     ap.add_argument("--walkers", type=int, default=0,
                     help="override the walker count of a one-system workload (the workload "
@@ -267,6 +312,11 @@ def main(argv=None):
                     help="run every iteration's device work as one CUDA graph launch")
     ap.add_argument("--persistent", type=int, default=-1,
                     help="1: persistent walker-update launch, 0: one block per work item")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the short timings of the one-system workloads (2D L=64 and "
+                         "3D L=32) reported beside the headline")
+    ap.add_argument("--no-ceiling", action="store_true",
+                    help="skip the latency ceiling (single-warp runs of every system)")
     ap.add_argument("--no-aux", action="store_true",
                     help="skip the timings of the analysis kernels (run after the timing)")
     args = ap.parse_args(argv)
@@ -294,7 +344,6 @@ def main(argv=None):
         return rc
 
     import torch
-    from paper_1401_4076_gb300 import mucal as m
 
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
@@ -305,112 +354,38 @@ def main(argv=None):
     # flush): the timing events are recorded on the stream the kernels run on
     stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(stream)
-    sweeps = args.sweeps or wl.sweeps
     systems = shard_systems(wl.systems, rank)
-    attempts_per_step = sweeps * sum(s[2] * s[3] for s in systems)
-
-    mc = m.Mucal(systems, cuda_stream=stream.cuda_stream)
-    if args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0:
-        cur = mc.launch()
-        cfg = dict(kernel=args.kernel if args.kernel >= 0 else cur["kernel"],
-                   lanes_per_walker=args.lanes or cur["lanes_per_walker"],
-                   walkers_per_block=args.wpb or cur["walkers_per_block"],
-                   bits_in_smem=args.smem if args.smem >= 0 else cur["bits_in_smem"],
-                   persistent=args.persistent if args.persistent >= 0 else cur["persistent"])
-        mc.set_launch(**cfg)
-    if args.graph:
-        mc.set_graph_mode(True)
-    args.launch_desc = mc.launch()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
 
-    def step(it):
-        mc.run_iteration(sweeps, it)
-        for s in range(len(systems)):
-            mc.update_weights(s, m.MUCAL_SCHEME_RECURSIVE)
-
-    for it in range(args.prerun):
-        step(it)
-    for it in range(args.prerun, args.prerun + args.warmup):
-        step(it)
-    torch.cuda.synchronize(device)
-    explicit = args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0
-    if not args.no_autotune and not explicit:
-        from paper_1401_4076_gb300.autotune import autotune
-        lnWs = [mc.weights(s) for s in range(len(systems))]
-        best, table = autotune(systems, lnW=lnWs, sweeps=args.tune_sweeps, repeats=5,
-                               cuda_stream=stream.cuda_stream)
-        mc.set_launch(**best)
-        args.launch_desc = mc.launch()
-        for cfg, ms in table[:5]:
-            print(json.dumps({"autotune": cfg, "kernel_ms": ms}), file=sys.stderr)
-    acc0 = mc.stats(0)
-    print(json.dumps({"warmup_acceptance": acc0["accepts"] / max(1, acc0["attempts"])}),
-          file=sys.stderr)
-    torch.cuda.synchronize(device)
-    _barrier(world)
-    torch.cuda.synchronize(device)
-
-    clocks = ClockSampler(local) if rank == 0 else None
-    if clocks:
-        clocks.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kernel_ms = []
-    accs = []
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        starts[i].record(stream)
-        step(args.prerun + args.warmup + i)
-        ends[i].record(stream)
-        st = mc.stats(0)
-        kernel_ms.append(st["kernel_ms"])
-        accs.append(st["accepts"] / max(1, st["attempts"]))
-    torch.cuda.synchronize(device)
-    wall = time.perf_counter() - wall0
-    _barrier(world)
-    torch.cuda.synchronize(device)
-    clk = clocks.stop() if clocks else None
-    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    step_ms = _max_over_ranks(step_ms, world, device)
-    total_attempts = attempts_per_step * args.steps * world
-    value = total_attempts / (step_ms / 1000.0)
-
-    # dominant kernel (walker update): algorithmic integer ops per launch / its duration
-    d_max = max(s[0] for s in systems)
-    ops_launch = sum(alg_ops_per_attempt(s[0]) * s[2] * s[3] * sweeps for s in systems)
-    k_ms = statistics.mean(kernel_ms)
-    peaks, peak_kind = _peaks()
-    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
-    peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6  # thread-instr/s
-    achieved = ops_launch / (k_ms / 1000.0)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s", "frac": achieved / peak_ops,
-                "traffic": _measured_traffic(wl.name, sweeps == wl.sweeps, args.launch_desc),
-                "peak_source": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz"
-                               f" ({peak_kind} max clock)",
-                "kernel": KERNEL_NAMES.get(args.launch_desc.get("kernel"), "walker_update"),
-                "kernel_ms": k_ms,
-                "alg_ops_per_attempt": alg_ops_per_attempt(d_max),
-                # independent chains (walkers) per SM: the parallelism that
-                # bounds these latency-bound kernels
-                "chains_per_sm": sum(s[3] for s in systems) / sm_count}
-
-    line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
+    res = measure(wl, args, systems, stream, device, world, flush, clocks_rank0=(rank == 0),
+                  ceiling=not args.no_ceiling)
+    line = {"metric": METRIC, "value": res["value"], "unit": "attempts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": _config(wl, args), "roofline": roofline,
-            "clocks": clk, "gpu_launches": None,
-            "acceptance": statistics.mean(accs)}
-    # launches inside the timed region: per step one walker update, one memset pair
-    # per system is a driver memset, one histogram-reduce launch per system
-    line["gpu_launches"] = args.steps * (1 + len(systems))
-    mc.close()
+            "data": "synthetic", "config": _config(wl, args), "roofline": res["roofline"],
+            "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
+            "acceptance": res["acceptance"]}
 
     if not args.no_e2e:
         line["e2e"] = e2e_measure(wl, args, systems, stream, device, world)
+    if rank == 0 and world == 1 and not args.no_extra_workloads:
+        extra = {}
+        for name in EXTRA_WORKLOADS:
+            if WORKLOADS[name].name == wl.name:
+                continue
+            xw = WORKLOADS[name]
+            xargs = argparse.Namespace(**dict(vars(args), steps=5, warmup=3, sweeps=0, prerun=0,
+                                              launch_desc=None))
+            r = measure(xw, xargs, xw.systems, stream, device, 1, flush, clocks_rank0=False,
+                        ceiling=not args.no_ceiling)
+            extra[xw.name] = {"value": r["value"], "unit": "attempts/s",
+                              "ms_per_step": r["ms_per_step"], "steps": 5, "warmup": 3,
+                              "acceptance": r["acceptance"], "launch": xargs.launch_desc,
+                              "attempts_per_step": xw.attempts_per_iteration(),
+                              "roofline": r["roofline"]}
+        line["workloads"] = extra
     if rank == 0 and world == 1 and not args.no_convergence:
-        line["convergence"] = convergence_measure(stream)
+        line["convergence_half_window"] = convergence_measure(stream)
     if rank == 0 and world == 1 and not args.no_aux:
         line["aux_kernels"] = aux_measure(stream, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -427,6 +402,170 @@ def main(argv=None):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _explicit_launch(args):
+    return args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0
+
+
+def measure(wl, args, systems, stream, device, world, flush, clocks_rank0=True, ceiling=True):
+    """The timed steps of one workload: W warm-up iterations of the weight
+    recursion from lnW = 0, the launch-shape autotuner, then K timed
+    iterations (walker update, histogram sums, histogram all-reduce across
+    ranks, weight update and threshold upload), each bracketed by CUDA events
+    on the library's stream after an L2 flush.  Returns the timing, the
+    roofline of the walker-update kernel and (optionally) its latency ceiling."""
+    import torch
+    from paper_1401_4076_gb300 import mucal as m
+    sweeps = args.sweeps or wl.sweeps
+    attempts_per_step = sweeps * sum(s[2] * s[3] for s in systems)
+    mc = m.Mucal(systems, cuda_stream=stream.cuda_stream)
+    if _explicit_launch(args):
+        cur = mc.launch()
+        cfg = dict(kernel=args.kernel if args.kernel >= 0 else cur["kernel"],
+                   lanes_per_walker=args.lanes or cur["lanes_per_walker"],
+                   walkers_per_block=args.wpb or cur["walkers_per_block"],
+                   bits_in_smem=args.smem if args.smem >= 0 else cur["bits_in_smem"],
+                   persistent=args.persistent if args.persistent >= 0 else cur["persistent"])
+        mc.set_launch(**cfg)
+    if args.graph:
+        mc.set_graph_mode(True)
+    args.launch_desc = mc.launch()
+    n_sys = len(systems)
+
+    def step(it):
+        mc.run_iteration(sweeps, it)
+        allreduce_histograms(mc, n_sys, world, device)
+        for s in range(n_sys):
+            mc.update_weights(s, m.MUCAL_SCHEME_RECURSIVE)
+
+    for it in range(args.prerun):
+        step(it)
+    for it in range(args.prerun, args.prerun + args.warmup):
+        step(it)
+    torch.cuda.synchronize(device)
+    if not args.no_autotune and not _explicit_launch(args):
+        from paper_1401_4076_gb300.autotune import autotune
+        lnWs = [mc.weights(s) for s in range(n_sys)]
+        best, table = autotune(systems, lnW=lnWs, sweeps=args.tune_sweeps, repeats=5,
+                               cuda_stream=stream.cuda_stream)
+        mc.set_launch(**best)
+        args.launch_desc = mc.launch()
+        for cfg, ms in table[:5]:
+            print(json.dumps({"workload": wl.name, "autotune": cfg, "kernel_ms": ms}),
+                  file=sys.stderr)
+    torch.cuda.synchronize(device)
+    _barrier(world)
+    torch.cuda.synchronize(device)
+
+    clocks = ClockSampler(device.index or 0) if clocks_rank0 else None
+    if clocks:
+        clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    accs = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step(args.prerun + args.warmup + i)
+        ends[i].record(stream)
+        st = [mc.stats(s) for s in range(n_sys)]
+        kernel_ms.append(st[0]["kernel_ms"])
+        accs.append(sum(x["accepts"] for x in st) / max(1, sum(x["attempts"] for x in st)))
+    torch.cuda.synchronize(device)
+    _barrier(world)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop() if clocks else None
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    step_ms = _max_over_ranks(step_ms, world, device)
+    value = attempts_per_step * args.steps * world / (step_ms / 1000.0)
+
+    # dominant kernel (walker update): algorithmic integer ops per launch / its
+    # average duration (CUDA events on the library's stream around the launch)
+    d_max = max(s[0] for s in systems)
+    ops_launch = sum(alg_ops_per_attempt(s[0]) * s[2] * s[3] * sweeps for s in systems)
+    k_ms = statistics.mean(kernel_ms)
+    peaks, peak_kind = _peaks()
+    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+    f_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = sm_count * 128 * f_mhz * 1e6          # thread-instructions/s
+    achieved = ops_launch / (k_ms / 1000.0)
+    kernel_rate = attempts_per_step / (k_ms / 1000.0)
+    blocks_per_sm, _ = mc.occupancy()
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops,
+                "traffic": _measured_traffic(wl.name, sweeps == wl.sweeps, args.launch_desc),
+                "peak_source": f"{sm_count} SMs x 128 lanes x {f_mhz} MHz ({peak_kind} max clock)",
+                "kernel": KERNEL_NAMES.get(args.launch_desc.get("kernel"), "walker_update"),
+                "kernel_ms": k_ms,
+                "kernel_attempts_per_s": kernel_rate,
+                "alg_ops_per_attempt": alg_ops_per_attempt(d_max),
+                "alg_ops_basis": "Philox 70 + index maps 2 + list reads 2 + bit tests 4d + "
+                                 "threshold 1 + histogram 1",
+                "chains_per_sm": sum(s[3] for s in systems) / sm_count,
+                "resident_blocks_per_sm": blocks_per_sm}
+    rec = _record_for(INSTR_MEASURED, wl.name, sweeps == wl.sweeps, args.launch_desc)
+    if rec is not None:
+        # issue slots: 4 warp instructions per SM and clock
+        roofline["issue"] = {"warp_inst_per_attempt": rec["warp_inst_per_attempt"],
+                             "thread_inst_per_attempt": rec["thread_inst_per_attempt"],
+                             "frac": kernel_rate * rec["warp_inst_per_attempt"] / 32.0
+                             / (sm_count * 4 * f_mhz * 1e6)}
+    lnWs = [mc.weights(s) for s in range(n_sys)]
+    mc.close()
+    if ceiling:
+        try:
+            roofline["latency_ceiling"] = latency_ceiling(systems, lnWs, args.launch_desc, sweeps,
+                                                          stream, blocks_per_sm, sm_count,
+                                                          kernel_rate)
+        except Exception as exc:   # reported, never fatal for the benchmark line
+            roofline["latency_ceiling"] = {"error": repr(exc)[:200]}
+    # launches inside the timed region: per step one walker update and one
+    # histogram-reduce launch per system (the clears are driver memsets)
+    return {"value": value, "ms_per_step": step_ms / args.steps, "roofline": roofline,
+            "clocks": clk, "gpu_launches": args.steps * (1 + n_sys),
+            "acceptance": statistics.mean(accs)}
+
+
+def latency_ceiling(systems, lnWs, launch, sweeps, stream, blocks_per_sm, sm_count, kernel_rate):
+    """What the launch's parallelism allows if its chains never waited for one
+    another: every system's walkers run alone, one warp (32 / lanes walkers)
+    on an otherwise idle GPU, with the weights of the timed steps and the
+    launch's kernel and lanes; that warp's attempted moves per second is the
+    inverse of its critical path per attempt.  The ceiling is the number of
+    warps resident at once (occupancy of the launch shape, at most the
+    launch's warps) times the attempt-weighted mean single-warp rate."""
+    from paper_1401_4076_gb300 import mucal as m
+    G = max(1, launch["lanes_per_walker"])
+    per_warp = 32 // G
+    rates = []
+    work = []
+    for i, (d, L, N, W, lo, hi, seed) in enumerate(systems):
+        desc = (d, L, N, per_warp, lo, hi, seed + (1 << 41))
+        sw = max(1, int(4e5 // (per_warp * N)))
+        with m.Mucal([desc], cuda_stream=stream.cuda_stream) as mc:
+            mc.set_weights(0, lnWs[i])
+            shape = dict(launch, walkers_per_block=per_warp, persistent=0)
+            try:
+                mc.set_launch(**shape)
+            except m.MucalError:
+                mc.set_launch(**dict(shape, bits_in_smem=0))
+            mc.run_iteration(sw, 0)
+            mc.run_iteration(sw, 1)
+            ms = mc.stats(0)["kernel_ms"]
+        rates.append(per_warp * sw * N / (ms / 1000.0))
+        work.append(W * sweeps * N)
+    t_mean = sum(a / r for a, r in zip(work, rates)) / sum(work)   # s per attempt per warp
+    warps_per_block = max(1, launch["walkers_per_block"] * G // 32)
+    launch_warps = sum(-(-s[3] // launch["walkers_per_block"]) for s in systems) * warps_per_block
+    resident = min(launch_warps, blocks_per_sm * warps_per_block * sm_count)
+    ceil = resident / t_mean
+    return {"value": ceil, "unit": "attempts/s", "frac": kernel_rate / ceil,
+            "resident_warps": resident, "launch_warps": launch_warps,
+            "single_warp_attempts_per_s": 1.0 / t_mean,
+            "basis": "resident warps x attempt-weighted single-warp rate (each system alone, "
+                     "one warp, weights of the timed steps)"}
 
 
 AUX_SYSTEM = (2, 64, 410, 4096, 0, 0, 0)   # the 2D L=64, N=410, 4096-walker system

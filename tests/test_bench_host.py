@@ -36,7 +36,27 @@ def test_walker_override_needs_a_one_system_workload():
 
 
 def test_algorithmic_ops_per_attempt():
-    # Philox4x32-10 100, index maps 2, list reads 2, neighbour sites 10d,
-    # bit tests 12d, dE and compare 6, histogram 2
-    assert bench.alg_ops_per_attempt(2) == 156
-    assert bench.alg_ops_per_attempt(3) == 178
+    # the scope table's count: Philox4x32-10 70 (of 60-80), index maps 2,
+    # list reads 2, occupancy bit tests 2 x 2d, threshold 1, histogram 1
+    assert bench.alg_ops_per_attempt(2) == 84
+    assert bench.alg_ops_per_attempt(3) == 88
+
+
+def test_headline_is_the_largest_workload():
+    """The default workload is the one with the most attempted moves per
+    iteration that fits one GPU (the 27-system batch)."""
+    sizes = {k: w.attempts_per_iteration() for k, w in bench.WORKLOADS.items()}
+    assert max(sizes, key=sizes.get) == "batched"
+    import inspect
+    src = inspect.getsource(bench.main)
+    assert 'default="batched"' in src
+
+
+def test_instruction_record_follows_shape_and_source():
+    rec = {"x": {"launch": {"kernel": 1, "lanes_per_walker": 4}, "kernel_sha": bench._kernel_sha(),
+                 "warp_inst_per_attempt": 100.0, "thread_inst_per_attempt": 900.0}}
+    assert bench._record_for(rec, "x", True, {"kernel": 1, "lanes_per_walker": 4}) is rec["x"]
+    assert bench._record_for(rec, "x", True, {"kernel": 1, "lanes_per_walker": 8}) is None
+    assert bench._record_for(rec, "x", False, {"kernel": 1, "lanes_per_walker": 4}) is None
+    rec["x"]["kernel_sha"] = "0" * 16
+    assert bench._record_for(rec, "x", True, {"kernel": 1, "lanes_per_walker": 4}) is None
