@@ -70,7 +70,17 @@ def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 3, cuda_stream=
                 if w is not None:
                     mc.set_weights(i, w)
         it = 0
-        for cfg in (cands or candidates()):
+        seen = set()
+        for cfg in (cands or with_threshold_modes(candidates())):
+            try:
+                mc.set_launch(**cfg)
+            except m.MucalError:
+                continue
+            # shapes the library resolves to the same launch are timed once
+            eff = tuple(sorted(mc.launch().items()))
+            if eff in seen:
+                continue
+            seen.add(eff)
             try:
                 ms, it = _time(mc, cfg, sweeps, 1, it)
             except m.MucalError:
@@ -91,3 +101,15 @@ def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 3, cuda_stream=
                     log(json.dumps({"launch": c, "kernel_ms": ms}))
     table.sort(key=lambda x: x[1])
     return table[0][0], table + first[finalists:]
+
+
+def with_threshold_modes(cands):
+    """Every group and field candidate also with thr_window = 0 (thresholds
+    read from global memory when the table does not fit in shared memory;
+    the default 1 keeps a window of rows per walker there instead)."""
+    out = []
+    for c in cands:
+        out.append(c)
+        if c["kernel"] != m.MUCAL_KERNEL_THREAD:
+            out.append(dict(c, thr_window=0))
+    return out

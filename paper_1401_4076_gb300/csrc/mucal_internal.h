@@ -14,6 +14,8 @@ struct SysParams {
     int32_t L2;                // L*L
     int32_t e_lo, n_bins;      // energy window [e_lo, e_lo + n_bins - 1]
     int32_t width;             // 4d + 1 thresholds per bin
+    int32_t tstride;           // words between threshold rows in thr: width rounded up to a
+                               // multiple of 4, so that every row starts on 16 bytes
     int32_t words;             // 32-bit words of one occupation bitset, ceil(V/32)
     int32_t idx16;             // 1: S holds uint16 site indices, 0: uint32
     int32_t n_walkers;
@@ -25,7 +27,8 @@ struct SysParams {
     unsigned long long *hist;  // [rows][n_bins] histogram rows: one per walker (H_j(E)) when
                                // per-walker histograms are kept, else one per launch block
     int32_t hist_rows;         // rows in use for the current launch shape
-    const uint32_t *thr;       // [n_bins][width] acceptance thresholds
+    const uint32_t *thr;       // [n_bins][tstride] acceptance thresholds (entries width..tstride-1
+                               // of a row unused)
     unsigned long long *accepts; // [n_walkers] accepted moves in the last iteration
     unsigned long long *H;     // [n_bins] summed histogram H(E) (Eq. 2)
     int32_t tun_lo, tun_hi;    // tunnelling ends as bins: a walker at bin <= tun_lo is at the
@@ -33,7 +36,14 @@ struct SysParams {
     uint8_t *tun_state;        // [n_walkers] 0 = no end reached yet, 1 = low end last, 2 = high
                                // end last (NULL: no tunnelling bookkeeping)
     uint32_t *tun_count;       // [n_walkers] tunnelling events (end-to-end travels) so far
+    unsigned int *err;         // set non-zero when a bounded wait of a walker kernel ran out
 };
+
+// Threshold-row window of the group and field kernels (threshold mode 2):
+// each walker keeps kThrWindowRows consecutive rows of the table in shared
+// memory as a ring indexed by bin mod kThrWindowRows, rows c - 15 .. c + 16
+// around a centre c that follows the walker's energy.
+constexpr int kThrWindowRows = 32;
 
 // One block of the walker-update launch works on walkers
 // [walker0, walker0 + count) of system sys.
@@ -45,9 +55,11 @@ struct BlockWork {
 };
 
 // Walker-update kernels of one (tunnelling, persistent) flavour: the thread
-// kernel and the group kernel in their shared-memory variants, and the
-// field kernel with and without the threshold table in shared memory.
-constexpr int kWalkerUpdateFns = 4 + 5 * 4 + 5 * 2;
+// kernel in its shared-memory variants, the group kernel with the bitsets in
+// shared or global memory and the thresholds in global memory, in shared
+// memory or in a per-walker row window, and the field kernel with the three
+// threshold modes.
+constexpr int kWalkerUpdateFns = 4 + 5 * 2 * 3 + 5 * 3;
 
 struct LaunchShape {
     int kernel;             // MUCAL_KERNEL_THREAD / _GROUP / _FIELD
@@ -57,6 +69,8 @@ struct LaunchShape {
     int thr_in_smem;        // stage the system's threshold table in shared memory
     size_t smem_bytes;      // dynamic shared memory per block
     int persistent;         // resident blocks pull work items from a counter
+    int thr_window;         // (group and field kernels, when the table is not in shared
+                            // memory) keep a window of rows per walker in shared memory
 };
 
 // Kernel launchers (walker_kernels.cu).  All are asynchronous on `stream`.
@@ -92,6 +106,8 @@ void walker_update_persist_tun_fns(const void *(&fns)[kWalkerUpdateFns]);
 // (group and thread kernels) or [threshold table][count fields] (field
 // kernel).
 size_t thr_smem_words(const SysParams &p);
+// Shared-memory bytes of one walker's threshold-row window and its barrier.
+size_t thr_window_bytes(const SysParams &p);
 // Shared-memory bytes of one walker's neighbour-count field (field kernel).
 size_t field_smem_bytes(const SysParams &p);
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,

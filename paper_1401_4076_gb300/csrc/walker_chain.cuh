@@ -4,6 +4,11 @@
 // walker_kernels_persist_tun.cu (persistent launches).  Everything here has internal linkage; each unit
 // gets its own copy of what it instantiates.
 //
+// The threshold rows a walker's acceptance test reads come from the table in
+// global memory, from the whole table staged in shared memory, or (group and
+// field kernels) from a per-walker window of rows in shared memory that bulk
+// copies refill as the walker's energy moves (see ThrWindow).
+//
 // The walker update is integer work with a serial dependency per walker
 // (each attempt reads the state the previous accepted attempt wrote), so it
 // is bound by latency and issue slots, not by tensor cores or HBM.  Two
@@ -92,11 +97,25 @@ __device__ __forceinline__ IdxT *walker_S(const SysParams &p, int w)
     return reinterpret_cast<IdxT *>(p.S) + (size_t)w * (size_t)p.V;
 }
 
-// Shared-memory words used by the threshold table of system p (rounded up to
-// 16 bytes so that the bitsets behind it stay aligned).
+// Shared-memory words used by the threshold table of system p (rows of
+// tstride words, a multiple of 4, so the bitsets behind it stay aligned).
 __host__ __device__ __forceinline__ size_t thr_words_aligned(const SysParams &p)
 {
-    return (((size_t)p.n_bins * (size_t)p.width) + 3u) & ~(size_t)3u;
+    return (((size_t)p.n_bins * (size_t)p.tstride) + 3u) & ~(size_t)3u;
+}
+
+// Threshold modes of the group and field kernels: rows read from global
+// memory, the whole table staged in shared memory, or a window of rows per
+// walker in shared memory.
+constexpr int kThrGlobal = 0;
+constexpr int kThrShared = 1;
+constexpr int kThrWindow = 2;
+
+// Shared-memory bytes of one walker's threshold-row window (kThrWindowRows
+// rows of tstride words) and of its 8-byte barrier.
+__host__ __device__ __forceinline__ size_t window_bytes(const SysParams &p)
+{
+    return (size_t)kThrWindowRows * (size_t)p.tstride * 4u + 8u;
 }
 
 // Histogram row a walker records into: its own row when per-walker histograms
@@ -132,7 +151,7 @@ __device__ __forceinline__ BlockSetup block_setup(const SysParams &p, const Bloc
     b.gbits = p.bits + (size_t)wk.walker0 * (size_t)p.words;
     uint32_t *sb = smem;
     if (thr_in_smem) {
-        block_copy_words(smem, p.thr, (size_t)p.n_bins * (size_t)p.width);
+        block_copy_words(smem, p.thr, (size_t)p.n_bins * (size_t)p.tstride);
         sb = smem + thr_words_aligned(p);
         b.thr = smem;
     } else {
@@ -255,6 +274,119 @@ __device__ __forceinline__ uint32_t thr_load(const uint32_t *thr, int idx)
         return __ldg(thr + idx);
     }
 }
+
+// ---------------------------------------------------------------------------
+// Threshold-row window (kThrWindow).  A walker's acceptance test reads one
+// row of the threshold table per round: the row of its current energy.  When
+// the table does not fit in shared memory, every walker keeps the
+// kThrWindowRows = 32 rows c - 15 .. c + 16 around a centre c in shared
+// memory, as a ring indexed by row mod 32.  When the energy has moved more
+// than 3 bins from c, the centre moves to it and the rows that enter the
+// window are fetched with asynchronous bulk copies completing on the
+// walker's memory barrier.  An energy step is at most 2d bins, so between
+// two re-centrings the rounds read rows within 3 of c, which were all in the
+// window before the last fetch (the fetched rows lie 7 or more away); the
+// fetch of one re-centring is waited for at the next, before any of its rows
+// can be read.  Device table rows are tstride = 12 (2D) or 16 (3D) words, so
+// every row starts on 16 bytes as the bulk copy requires.  Waits are bounded:
+// if one runs out the kernel records it in p.err and carries on.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kWaitLimit = 1u << 20;
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous (bulk-copy) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint32_t a)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing on the barrier at mbar.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                              uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
+struct ThrWindow {
+    uint32_t ring = 0;           // shared byte address of the walker's ring of rows
+    uint32_t mbar = 0;           // shared byte address of its barrier
+    const uint32_t *table = nullptr;
+    int n_rows = 0;
+    uint32_t tstride = 0;        // words per row
+    int c = 0;                   // centre of the window
+    uint32_t phase = 0;          // parity of the barrier phase the next fetch completes
+    bool pend = false;           // a fetch is in flight
+    bool broken = false;         // a wait ran out: no further fetches or waits
+
+    // Fetch rows [r0, r1] (clipped to the table) into their ring slots; the
+    // leader lane issues the copies, every lane of the group records them.
+    __device__ __forceinline__ void fetch(int r0, int r1, bool leader)
+    {
+        if (broken) return;
+        r0 = r0 < 0 ? 0 : r0;
+        r1 = r1 > n_rows - 1 ? n_rows - 1 : r1;
+        if (r0 > r1) return;
+        if (leader) {
+            constexpr uint32_t NR = (uint32_t)kThrWindowRows;
+            const uint32_t rowb = 4u * tstride;
+            const uint32_t n = (uint32_t)(r1 - r0 + 1);
+            const uint32_t s0 = (uint32_t)r0 & (NR - 1u);
+            const uint32_t n1 = n < NR - s0 ? n : NR - s0;
+            // earlier reads of the slots being replaced come before the copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive_expect_tx(mbar, n * rowb);
+            bulk_copy_g2s(ring + s0 * rowb, table + (size_t)r0 * tstride, n1 * rowb, mbar);
+            if (n > n1)
+                bulk_copy_g2s(ring, table + (size_t)(r0 + (int)n1) * tstride, (n - n1) * rowb, mbar);
+        }
+        pend = true;
+    }
+
+    // Wait (bounded) for the fetch in flight, if any.  If the wait runs out
+    // the failure is recorded in p.err and the window stops fetching (the
+    // rounds then read stale rows; the host reports the iteration invalid).
+    __device__ __forceinline__ void wait(const SysParams &p)
+    {
+        if (!pend) return;
+        uint32_t ok = 0;
+        for (uint32_t i = 0; i < kWaitLimit && !ok; ++i) ok = mbar_try_wait(mbar, phase);
+        if (!ok) {
+            atomicOr(p.err, 1u);
+            broken = true;
+            return;             // pend stays set: the end of the chain waits once more
+        }
+        phase ^= 1u;
+        pend = false;
+    }
+};
 
 // Broadcast a pair of list values from lane src: one shuffle when both fit
 // in 16 bits, two otherwise.
@@ -388,10 +520,15 @@ struct FieldView {
 // moved is found by comparing slot indices with the committing lane's (one
 // more shuffle) when FIX_BY_SLOT, else by comparing sites; both find the
 // same lanes, and which is faster is a matter of the compiled loop.
-template <int D, typename IdxT, int G, bool ST, bool TUN, bool FIX_BY_SLOT, typename View>
+// TM is the threshold mode: kThrGlobal reads the rows from thr in global
+// memory, kThrShared from thr staged in shared memory, kThrWindow from the
+// walker's ring of rows at shared address ring_s with its barrier at mbar_s
+// (thr then being the global table the ring is filled from).
+template <int D, typename IdxT, int G, int TM, bool TUN, bool FIX_BY_SLOT, typename View>
 __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool active, View v,
                                              const uint32_t *thr, unsigned long long *hist,
-                                             uint64_t A, uint32_t iter)
+                                             uint64_t A, uint32_t iter, uint32_t ring_s = 0u,
+                                             uint32_t mbar_s = 0u)
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
@@ -405,13 +542,32 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
     const uint32_t holes = (uint32_t)(p.V - p.N);
     const uint64_t seed = p.seed_base + (uint64_t)w;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const int width = p.width;
     int bin = active ? p.E[w] - p.e_lo : 0;
     // threshold rows as shared byte addresses (or byte offsets into the
-    // global table): row of bin b, entry dE = 0, at rbase + b * w4
-    const uint32_t thr_s = ST ? (uint32_t)__cvta_generic_to_shared(thr) : 0u;
+    // global table): row of bin b, entry dE = 0, at rbase + row(b) * w4,
+    // row(b) = b, or b mod kThrWindowRows in the walker's ring
+    const uint32_t thr_s = TM == kThrShared ? (uint32_t)__cvta_generic_to_shared(thr)
+                                            : (TM == kThrWindow ? ring_s : 0u);
     const uint32_t rbase = thr_s + 8u * D;
-    const uint32_t w4 = 4u * (uint32_t)width;
+    const uint32_t w4 = 4u * (uint32_t)p.tstride;
+    auto row_of = [](int b) -> uint32_t {
+        return TM == kThrWindow ? ((uint32_t)b & (uint32_t)(kThrWindowRows - 1)) : (uint32_t)b;
+    };
+    ThrWindow tw;
+    if constexpr (TM == kThrWindow) {
+        tw.ring = ring_s;
+        tw.mbar = mbar_s;
+        tw.table = thr;
+        tw.n_rows = p.n_bins;
+        tw.tstride = (uint32_t)p.tstride;
+        tw.c = bin;
+        if (active) {
+            if (j == 0) mbar_init(mbar_s, 1u);
+            __syncwarp(gm);
+            tw.fetch(bin - (kThrWindowRows / 2 - 1), bin + kThrWindowRows / 2, j == 0);
+            tw.wait(p);
+        }
+    }
     // histogram entries are added per run of attempts at one energy: carry
     // holds the run's attempts from earlier batches, rs the warp lane of
     // this batch at which it started
@@ -498,14 +654,14 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
         // previous commit, ahead of the bookkeeping
         v.load();
         uint32_t radj = rbase + (uint32_t)v.adj4();   // this attempt's adjacency joins the row address
-        uint32_t rba = (uint32_t)bin * w4 + radj;
+        uint32_t rba = row_of(bin) * w4 + radj;
         bool pend = valid;                      // this lane's attempt is still undecided
         int rs = gbase;
         while (__any_sync(FULL, pend)) {
             const int d4 = v.d4();
             const uint32_t toff = rba + (uint32_t)d4;
             uint32_t T;
-            if constexpr (ST) {
+            if constexpr (TM != kThrGlobal) {
                 asm volatile("ld.shared.u32 %0, [%1];" : "=r"(T) : "r"(toff));
             } else {
                 T = __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(thr) + toff));
@@ -565,7 +721,19 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
             carry = moved ? 0u : carry;
             rs = moved ? src : rs;
             bin += moved ? de_f : 0;
-            rba = (uint32_t)bin * w4 + radj;
+            if constexpr (TM == kThrWindow) {
+                // moved is the same in every lane of the group
+                if (moved && (bin - tw.c > 3 || tw.c - bin > 3)) {
+                    constexpr int LO = kThrWindowRows / 2 - 1, HI = kThrWindowRows / 2;
+                    tw.wait(p);        // the previous fetch, before its rows can be read
+                    if (bin > tw.c)
+                        tw.fetch(max(tw.c + HI + 1, bin - LO), bin + HI, j == 0);
+                    else
+                        tw.fetch(bin - LO, min(tw.c - LO - 1, bin + HI), j == 0);
+                    tw.c = bin;
+                }
+            }
+            rba = row_of(bin) * w4 + radj;
             an = (commit && (FIX_BY_SLOT ? kn == k_f : an == a_f)) ? b_f : an;
             bn = (commit && (FIX_BY_SLOT ? mn == m_f : bn == b_f)) ? a_f : bn;
         }
@@ -574,6 +742,19 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
         if (carry >= 0x40000000u) {
             if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)carry);
             carry = 0;
+        }
+    }
+    if constexpr (TM == kThrWindow) {
+        if (active) {
+            // no copy may still write into the ring when the block moves on
+            if (tw.broken) {
+                uint32_t ok = 0;
+                for (uint32_t i = 0; i < kWaitLimit && !ok; ++i) ok = mbar_try_wait(mbar_s, tw.phase);
+            } else {
+                tw.wait(p);
+            }
+            __syncwarp(gm);
+            if (j == 0) mbar_inval(mbar_s);
         }
     }
 #pragma unroll
@@ -612,7 +793,7 @@ __device__ __forceinline__ void chain_thread(const SysParams &p, int w, uint32_t
     const uint32_t holes = (uint32_t)(p.V - p.N);
     const uint64_t seed = p.seed_base + (uint64_t)w;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const int width = p.width;
+    const int width = p.tstride;      // words between threshold rows
     int bin = p.E[w] - p.e_lo;
     int row = bin * width + 2 * D;
     uint32_t run = 0;
@@ -778,52 +959,73 @@ walker_update_thread(const SysParams *__restrict__ sys, const BlockWork *__restr
     }
 }
 
-template <int G, bool SB, bool ST, bool TUN>
+// Shared byte addresses of walker lw's threshold-row window and barrier: the
+// block's windows start at the first 16-byte boundary at or after `after`
+// (behind the bitsets or fields), one per walker of the launch shape, and
+// the barriers follow them.
+__device__ __forceinline__ void window_addrs(const SysParams &p, uint32_t after, int wpb, int lw,
+                                             uint32_t &ring_s, uint32_t &mbar_s)
+{
+    const uint32_t base = (after + 15u) & ~15u;
+    const uint32_t rb = (uint32_t)kThrWindowRows * 4u * (uint32_t)p.tstride;
+    ring_s = base + (uint32_t)lw * rb;
+    mbar_s = base + (uint32_t)wpb * rb + (uint32_t)lw * 8u;
+}
+
+template <int G, bool SB, int TM, bool TUN>
 __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
                                            uint64_t sweeps, uint32_t iter)
 {
     const int lw = threadIdx.x / G;
     const bool active = lw < wk.count;
     const int w = wk.walker0 + (active ? lw : 0);
-    const uint32_t *thr = ST ? smem : p.thr;
-    uint32_t *bits0 = SB ? smem + (ST ? thr_words_aligned(p) : 0)
+    const uint32_t *thr = TM == kThrShared ? smem : p.thr;
+    uint32_t *bits0 = SB ? smem + (TM == kThrShared ? thr_words_aligned(p) : 0)
                          : p.bits + (size_t)wk.walker0 * (size_t)p.words;
     uint32_t *bits = bits0 + (size_t)(active ? lw : 0) * p.words;
     unsigned long long *hist = hist_row(p, w, wk.hist_row);
     const uint64_t A = sweeps * (uint64_t)p.N;
+    uint32_t ring_s = 0u, mbar_s = 0u;
+    if constexpr (TM == kThrWindow) {
+        const int wpb = (int)blockDim.x / G;
+        const uint32_t after = (uint32_t)__cvta_generic_to_shared(smem) +
+                               (SB ? (uint32_t)wpb * (uint32_t)p.words * 4u : 0u);
+        window_addrs(p, after, wpb, active ? lw : 0, ring_s, mbar_s);
+    }
     // slot compare for G = 8, site compare otherwise (measured on GB300)
     constexpr bool kSlot = (G == 8);
     if (p.d == 2) {
-        if (p.idx16) chain_rounds<2, uint16_t, G, ST, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter);
-        else chain_rounds<2, uint32_t, G, ST, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter);
+        if (p.idx16) chain_rounds<2, uint16_t, G, TM, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);
+        else chain_rounds<2, uint32_t, G, TM, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);
     } else {
-        if (p.idx16) chain_rounds<3, uint16_t, G, ST, TUN, kSlot>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter);
-        else chain_rounds<3, uint32_t, G, ST, TUN, kSlot>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter);
+        if (p.idx16) chain_rounds<3, uint16_t, G, TM, TUN, kSlot>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);
+        else chain_rounds<3, uint32_t, G, TM, TUN, kSlot>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);
     }
 }
 
-template <int G, bool SB, bool ST, bool TUN, bool PERSIST>
+template <int G, bool SB, int TM, bool TUN, bool PERSIST>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
                     uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
 {
     extern __shared__ __align__(16) uint32_t smem[];
+    constexpr int kTS = TM == kThrShared ? 1 : 0;
     if constexpr (!PERSIST) {
         // one work item per block
         (void)n_items;
         (void)next_item;
         const BlockWork wk = work[blockIdx.x];
         const SysParams &p = sys[wk.sys];
-        const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
-        group_body<G, SB, ST, TUN>(p, wk, smem, sweeps, iter);
+        const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, kTS);
+        group_body<G, SB, TM, TUN>(p, wk, smem, sweeps, iter);
         block_finish(bs, SB ? 1 : 0);
     } else {
         __shared__ int s_item;
         for (int item = blockIdx.x; item < n_items;) {
             const BlockWork wk = work[item];
             const SysParams &p = sys[wk.sys];
-            const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
-            group_body<G, SB, ST, TUN>(p, wk, smem, sweeps, iter);
+            const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, kTS);
+            group_body<G, SB, TM, TUN>(p, wk, smem, sweeps, iter);
             block_finish(bs, SB ? 1 : 0);
             item = next_work_item(next_item, &s_item);
         }
@@ -881,40 +1083,47 @@ __device__ __forceinline__ void field_finish(const SysParams &p, const BlockWork
     block_copy_words(p.bits + (size_t)wk.walker0 * words, fw, total);
 }
 
-template <int D, typename IdxT, int G, bool ST, bool TUN>
+template <int D, typename IdxT, int G, int TM, bool TUN>
 __device__ __forceinline__ void field_item(const SysParams &p, const BlockWork &wk, uint32_t *smem,
                                            uint64_t sweeps, uint32_t iter)
 {
-    if constexpr (ST) block_copy_words(smem, p.thr, (size_t)p.n_bins * (size_t)p.width);
-    uint32_t *fw = smem + (ST ? thr_words_aligned(p) : 0);
+    if constexpr (TM == kThrShared) block_copy_words(smem, p.thr, (size_t)p.n_bins * (size_t)p.tstride);
+    uint32_t *fw = smem + (TM == kThrShared ? thr_words_aligned(p) : 0);
     field_build<D, IdxT>(p, wk, fw);   // ends with a block barrier, which also covers the table
     const int lw = threadIdx.x / G;
     const bool active = lw < wk.count;
     const int w = wk.walker0 + (active ? lw : 0);
-    const uint32_t *thr = ST ? smem : p.thr;
+    const uint32_t *thr = TM == kThrShared ? smem : p.thr;
     const uint32_t fbase = (uint32_t)__cvta_generic_to_shared(fw) +
                            (uint32_t)((size_t)(active ? lw : 0) * field_bytes(p));
     unsigned long long *hist = hist_row(p, w, wk.hist_row);
+    uint32_t ring_s = 0u, mbar_s = 0u;
+    if constexpr (TM == kThrWindow) {
+        const int wpb = (int)blockDim.x / G;
+        const uint32_t after = (uint32_t)__cvta_generic_to_shared(fw) +
+                               (uint32_t)((size_t)wpb * field_bytes(p));
+        window_addrs(p, after, wpb, active ? lw : 0, ring_s, mbar_s);
+    }
     // site compare for moved slots (measured on GB300: the faster one here for every G)
-    chain_rounds<D, IdxT, G, ST, TUN, false>(p, w, active, FieldView<D>(fbase), thr, hist,
-                                             sweeps * (uint64_t)p.N, iter);
+    chain_rounds<D, IdxT, G, TM, TUN, false>(p, w, active, FieldView<D>(fbase), thr, hist,
+                                             sweeps * (uint64_t)p.N, iter, ring_s, mbar_s);
     field_finish<IdxT>(p, wk, fw);
 }
 
-template <int G, bool ST, bool TUN>
+template <int G, int TM, bool TUN>
 __device__ __forceinline__ void field_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
                                            uint64_t sweeps, uint32_t iter)
 {
     if (p.d == 2) {
-        if (p.idx16) field_item<2, uint16_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
-        else field_item<2, uint32_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
+        if (p.idx16) field_item<2, uint16_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
+        else field_item<2, uint32_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
     } else {
-        if (p.idx16) field_item<3, uint16_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
-        else field_item<3, uint32_t, G, ST, TUN>(p, wk, smem, sweeps, iter);
+        if (p.idx16) field_item<3, uint16_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
+        else field_item<3, uint32_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
     }
 }
 
-template <int G, bool ST, bool TUN, bool PERSIST>
+template <int G, int TM, bool TUN, bool PERSIST>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_field(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
                     uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
@@ -925,32 +1134,48 @@ walker_update_field(const SysParams *__restrict__ sys, const BlockWork *__restri
         (void)n_items;
         (void)next_item;
         const BlockWork wk = work[blockIdx.x];
-        field_body<G, ST, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
+        field_body<G, TM, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
     } else {
         __shared__ int s_item;
         for (int item = blockIdx.x; item < n_items;) {
             const BlockWork wk = work[item];
-            field_body<G, ST, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
+            field_body<G, TM, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
             item = next_work_item(next_item, &s_item);
         }
     }
 }
 
+// Threshold mode of a launch shape (group and field kernels).
+inline int thr_mode(const LaunchShape &sh)
+{
+    return sh.thr_in_smem ? kThrShared : (sh.thr_window ? kThrWindow : kThrGlobal);
+}
+
 template <int G, bool TUN, bool PE>
 const void *field_fn(const LaunchShape &sh)
 {
-    if (sh.thr_in_smem) return (const void *)walker_update_field<G, true, TUN, PE>;
-    return (const void *)walker_update_field<G, false, TUN, PE>;
+    switch (thr_mode(sh)) {
+    case kThrShared: return (const void *)walker_update_field<G, kThrShared, TUN, PE>;
+    case kThrWindow: return (const void *)walker_update_field<G, kThrWindow, TUN, PE>;
+    default: return (const void *)walker_update_field<G, kThrGlobal, TUN, PE>;
+    }
+}
+
+template <int G, bool SB, bool TUN, bool PE>
+const void *group_fn_sb(const LaunchShape &sh)
+{
+    switch (thr_mode(sh)) {
+    case kThrShared: return (const void *)walker_update_group<G, SB, kThrShared, TUN, PE>;
+    case kThrWindow: return (const void *)walker_update_group<G, SB, kThrWindow, TUN, PE>;
+    default: return (const void *)walker_update_group<G, SB, kThrGlobal, TUN, PE>;
+    }
 }
 
 // The walker-update kernel of a launch shape (one TUN flavour).
 template <int G, bool TUN, bool PE>
 const void *group_fn(const LaunchShape &sh)
 {
-    if (sh.bits_in_smem && sh.thr_in_smem) return (const void *)walker_update_group<G, true, true, TUN, PE>;
-    if (sh.bits_in_smem) return (const void *)walker_update_group<G, true, false, TUN, PE>;
-    if (sh.thr_in_smem) return (const void *)walker_update_group<G, false, true, TUN, PE>;
-    return (const void *)walker_update_group<G, false, false, TUN, PE>;
+    return sh.bits_in_smem ? group_fn_sb<G, true, TUN, PE>(sh) : group_fn_sb<G, false, TUN, PE>(sh);
 }
 
 // The kernel of a launch shape among the kWalkerUpdateFns of one (TUN, PE) flavour
@@ -994,20 +1219,23 @@ void walker_update_fns(const void *(&fns)[kWalkerUpdateFns])
     fns[i++] = (const void *)walker_update_thread<true, false, TUN, PE>;
     fns[i++] = (const void *)walker_update_thread<false, true, TUN, PE>;
     fns[i++] = (const void *)walker_update_thread<false, false, TUN, PE>;
-#define MUCAL_GROUP_FNS(G)                                                   \
-    fns[i++] = (const void *)walker_update_group<G, true, true, TUN, PE>;   \
-    fns[i++] = (const void *)walker_update_group<G, true, false, TUN, PE>;  \
-    fns[i++] = (const void *)walker_update_group<G, false, true, TUN, PE>;  \
-    fns[i++] = (const void *)walker_update_group<G, false, false, TUN, PE>;
+#define MUCAL_GROUP_FNS(G)                                                          \
+    fns[i++] = (const void *)walker_update_group<G, true, kThrShared, TUN, PE>;    \
+    fns[i++] = (const void *)walker_update_group<G, true, kThrGlobal, TUN, PE>;    \
+    fns[i++] = (const void *)walker_update_group<G, true, kThrWindow, TUN, PE>;    \
+    fns[i++] = (const void *)walker_update_group<G, false, kThrShared, TUN, PE>;   \
+    fns[i++] = (const void *)walker_update_group<G, false, kThrGlobal, TUN, PE>;   \
+    fns[i++] = (const void *)walker_update_group<G, false, kThrWindow, TUN, PE>;
     MUCAL_GROUP_FNS(2)
     MUCAL_GROUP_FNS(4)
     MUCAL_GROUP_FNS(8)
     MUCAL_GROUP_FNS(16)
     MUCAL_GROUP_FNS(32)
 #undef MUCAL_GROUP_FNS
-#define MUCAL_FIELD_FNS(G)                                                \
-    fns[i++] = (const void *)walker_update_field<G, true, TUN, PE>;      \
-    fns[i++] = (const void *)walker_update_field<G, false, TUN, PE>;
+#define MUCAL_FIELD_FNS(G)                                                     \
+    fns[i++] = (const void *)walker_update_field<G, kThrShared, TUN, PE>;     \
+    fns[i++] = (const void *)walker_update_field<G, kThrGlobal, TUN, PE>;     \
+    fns[i++] = (const void *)walker_update_field<G, kThrWindow, TUN, PE>;
     MUCAL_FIELD_FNS(2)
     MUCAL_FIELD_FNS(4)
     MUCAL_FIELD_FNS(8)

@@ -289,6 +289,8 @@ size_t thr_smem_words(const SysParams &p) { return thr_words_aligned(p); }
 
 size_t field_smem_bytes(const SysParams &p) { return field_bytes(p); }
 
+size_t thr_window_bytes(const SysParams &p) { return window_bytes(p); }
+
 cudaError_t launch_hist_reduce(const SysParams *host_sys, const SysParams *dev_sys, int n_sys,
                                cudaStream_t stream)
 {
@@ -369,7 +371,7 @@ walker_update_noalloc(SysParams p, uint64_t sweeps, uint32_t iter, const unsigne
     wk.count = min(kNoAllocWalkersPerBlock, p.n_walkers - wk.walker0);
     wk.hist_row = blockIdx.x;
     const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, ST ? 1 : 0);
-    group_body<kNoAllocLanes, SB, ST, false>(p, wk, smem, sweeps, iter);
+    group_body<kNoAllocLanes, SB, ST ? kThrShared : kThrGlobal, false>(p, wk, smem, sweeps, iter);
     block_finish(bs, SB ? 1 : 0);
 }
 
@@ -500,6 +502,7 @@ extern "C" int mucal_run_walkers_noalloc(const mucal_system_desc *sys, int64_t s
     p.e_lo = e_lo;
     p.n_bins = e_hi - e_lo + 1;
     p.width = 4 * d.d + 1;
+    p.tstride = p.width;           // the caller's table has width words per row
     p.words = (int32_t)((V + 31) / 32);
     p.idx16 = V <= 65536 ? 1 : 0;
     p.n_walkers = d.n_walkers;

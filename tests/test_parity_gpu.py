@@ -451,3 +451,94 @@ def test_batched_every_walker_of_two_systems(shape):
     big3 = max(range(len(wl.systems)), key=lambda i: (wl.systems[i][0] == 3, wl.systems[i][2]))
     big2 = max(range(len(wl.systems)), key=lambda i: (wl.systems[i][0] == 2, wl.systems[i][2]))
     _every_walker_one_iteration(wl.systems, [big3, big2], 5, 7, launch, lnWs)
+
+
+# ------------------------------------------ threshold-row window (mode 2) ---
+# Each walker keeps 32 rows of the threshold table around its energy in
+# shared memory and refills them with bulk copies as the energy moves; the
+# chain must stay the oracle's.  thr_window = 2 forces the windows even where
+# the table would fit in shared memory, so small systems exercise them: few
+# bins (the window holds the whole table), walkers at the window's ends,
+# strongly sloped weights (energies run far, many refills), every lane count,
+# both views, persistent and tunnelling flavours.
+
+WINDOW_LAUNCHES = [
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=2, walkers_per_block=16, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=4, walkers_per_block=24, bits_in_smem=0),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16, walkers_per_block=2, bits_in_smem=1,
+         persistent=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=32, walkers_per_block=3, bits_in_smem=0),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=4, walkers_per_block=8, bits_in_smem=1,
+         persistent=1),
+]
+
+
+@pytest.mark.parametrize("launch", WINDOW_LAUNCHES, ids=_lid)
+@pytest.mark.parametrize("desc,sweeps,slope", [
+    ((2, 8, 6, 21, 0, 0, 4), 60, 0.0),         # 13 bins: the window covers the whole table
+    ((2, 24, 80, 37, 0, 0, 8), 40, -1.5),      # 161 bins, weights favour low E: runs down
+    ((3, 10, 150, 29, 0, 0, 12), 15, 0.8),     # 3D, 451 bins, weights favour high E
+    ((2, 40, 300, 19, -450, -30, 16), 20, 0.3),  # user window, walkers near its top
+])
+def test_threshold_window_bit_exact(desc, sweeps, slope, launch):
+    d, L, N, W, lo, hi, seed = desc
+    e_lo, e_hi = _window(d, N, lo, hi)
+    nb = e_hi - e_lo + 1
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    if lo or hi:
+        ok = (E >= e_lo) & (E <= e_hi)
+        if not ok.all():
+            pytest.skip("a random placement lies outside the user window")
+    lnW = workloads.random_log_weights(nb, 7, scale=0.3) + slope * np.arange(nb)
+    lnW -= lnW.max()
+    with m.Mucal([desc], per_walker_hist=True) as mc:
+        mc.set_launch(**dict(launch, thr_window=2))
+        assert mc.launch()["thr_window"] == 2
+        mc.set_weights(0, lnW)
+        T = chain.thresholds(d, e_lo, e_hi, lnW)
+        for it in range(3):
+            mc.run_iteration(sweeps, it)
+            hist, _ = chain.run_walkers(d, L, N, seed, it, sweeps * N, e_lo, e_hi, T, S, occ, E)
+            H, per = mc.histogram(0, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+        for w in range(W):
+            _assert_walker_equal(mc, 0, w, S[w], occ[w], E[w])
+
+
+def test_threshold_window_tunnel_flavour_bit_exact():
+    d, L, N, W, seed = 2, 20, 60, 24, 31
+    nb = d * N + 1
+    lnW = workloads.random_log_weights(nb, 3, 0.6)
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    T = chain.thresholds(d, -d * N, 0, lnW)
+    tstate = np.zeros(W, np.uint8)
+    tcount = np.zeros(W, np.int64)
+    with m.Mucal([(d, L, N, W, 0, 0, seed)], per_walker_hist=True) as mc:
+        mc.set_launch(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=8,
+                      bits_in_smem=1, thr_window=2)
+        mc.set_weights(0, lnW)
+        mc.set_tunnel_window(0, -60, -20)
+        for it in range(2):
+            mc.run_iteration(50, it)
+            hist = chain.run_walkers_tunnel(d, L, N, seed, it, 50 * N, -d * N, 0, T, S, occ, E,
+                                            -60, -20, tstate, tcount)
+            _, per = mc.histogram(0, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+        total, per_w, st = mc.tunnel_counts(0)
+        np.testing.assert_array_equal(per_w.astype(np.int64), tcount)
+        np.testing.assert_array_equal(st, tstate)
+
+
+def test_window_setting_falls_back_when_it_does_not_fit():
+    """3D L=32 with 56 walkers per block: the bitsets fill shared memory, the
+    windows cannot join them, the launch reads thresholds from global memory
+    and reports it; with fewer walkers per block the windows are used."""
+    with m.Mucal([(3, 32, 3277, 64, 0, 0, 0)]) as mc:
+        mc.set_launch(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=4, walkers_per_block=56,
+                      bits_in_smem=1, thr_window=1)
+        assert mc.launch()["thr_window"] == 0
+        mc.set_launch(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=4, walkers_per_block=32,
+                      bits_in_smem=1, thr_window=1)
+        assert mc.launch()["thr_window"] == 1
