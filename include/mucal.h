@@ -77,6 +77,15 @@ extern "C" {
  * none is above).  Its first step equals MUCAL_SCHEME_SIMPLE on the visited
  * bins. */
 #define MUCAL_SCHEME_RECURSIVE  1
+/* Flag, or-ed with either scheme: after the update, bins below the lowest
+ * visited energy and above the highest take lnW continued linearly with the
+ * slope between that end and the 8th visited bin counted inwards from it
+ * (canonical weights at the microcanonical temperature of the sampled edge;
+ * without the flag they keep the edge's weight).  The walkers then keep
+ * moving into the energies not sampled yet instead of being held back by the
+ * entropy there, which is how the range of Sec. 2's iteration grows.  Not
+ * stated in the paper (its recursion is cited, not printed). */
+#define MUCAL_SCHEME_EXTRAPOLATE 0x10
 
 /* ---- walker-update kernels (mucal_launch_config.kernel) ------------------ */
 /* One thread advances one walker, attempt after attempt; the random numbers
@@ -117,6 +126,18 @@ typedef struct mucal_launch_config {
                                   once; each pulls the next block of walkers from a
                                   counter when it finishes one.  0: one block per block
                                   of walkers, scheduled by the hardware */
+    int32_t thr_window;        /* GROUP and FIELD kernels, when some system's threshold
+                                  table does not fit in shared memory next to the
+                                  block's bitsets or fields: 1 = every walker keeps the
+                                  32 rows around its current energy in shared memory
+                                  (refilled by asynchronous bulk copies as the energy
+                                  moves), 0 = thresholds are read from global memory;
+                                  2 = the row windows even when the table would fit.
+                                  If the windows do not fit next to the block's
+                                  walkers, thresholds are read from global memory
+                                  (mucal_get_launch_config then reports 0, as it does
+                                  when the whole table is staged in shared memory).
+                                  Ignored by THREAD.  Default 1 */
 } mucal_launch_config;
 
 typedef struct mucal_system_info {
@@ -199,7 +220,8 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration);
 int mucal_get_histogram(void *ctx, int32_t sys, int64_t *H, int32_t n_bins, int64_t *per_walker);
 
 /* Weight update from the last histogram of system sys (Sec. 2):
- * scheme MUCAL_SCHEME_SIMPLE or MUCAL_SCHEME_RECURSIVE, in double precision on
+ * scheme MUCAL_SCHEME_SIMPLE or MUCAL_SCHEME_RECURSIVE, optionally or-ed with
+ * MUCAL_SCHEME_EXTRAPOLATE, in double precision on
  * the host, then lnW is shifted to max 0, the thresholds are rebuilt and
  * uploaded (the redistribution of the weights to all walkers).  lnW_out
  * (nullable, host float64[n_bins]) receives the new lnW; flatness_out
@@ -232,7 +254,8 @@ int mucal_get_launch_occupancy(void *ctx, int32_t *blocks_per_sm, int32_t *sm_co
 
 /* One weight update of Sec. 2 on caller-owned host arrays, without a
  * context: the same double-precision code mucal_update_weights runs.
- *   scheme     MUCAL_SCHEME_SIMPLE or MUCAL_SCHEME_RECURSIVE
+ *   scheme     MUCAL_SCHEME_SIMPLE or MUCAL_SCHEME_RECURSIVE, optionally or-ed
+ *              with MUCAL_SCHEME_EXTRAPOLATE
  *   H          int64[n_bins], the summed histogram of the iteration (in)
  *   lnW        float64[n_bins], the weights H was sampled with (in), the next
  *              weights shifted to maximum 0 (out)

@@ -10,7 +10,7 @@ import math
 import numpy as np
 
 from . import chain
-from .recursion import flatness, recursive_update, simple_update
+from .recursion import extrapolate_edges, flatness, recursive_update, simple_update
 
 
 class System:
@@ -39,25 +39,27 @@ class System:
         H = hist.sum(axis=0)
         return H, hist, acc
 
-    def update(self, H, scheme="recursive", t_lo=None, t_hi=None):
+    def update(self, H, scheme="recursive", t_lo=None, t_hi=None, extrapolate=False):
         if scheme == "simple":
             self.s_cum = self.s_cum | (H > 0)
             self.lnW = simple_update(self.lnW, H)
         else:
             self.lnW, self.s_cum, self.phat = recursive_update(self.lnW, H, self.s_cum, self.phat)
+        if extrapolate:
+            self.lnW = extrapolate_edges(self.lnW, self.s_cum)
         tl = None if t_lo is None else t_lo - self.e_lo
         th = None if t_hi is None else t_hi - self.e_lo
         return flatness(H, self.s_cum, tl, th)
 
 
 def run_to_flat(system: System, sweeps, max_iter, scheme="recursive", t_lo=None, t_hi=None,
-                goal=0.5):
+                goal=0.5, extrapolate=False):
     """Iterate until flatness >= goal; returns (iterations used, last H, flatness)."""
     H = None
     f = -1.0
     for it in range(max_iter):
         H, _, _ = system.iterate(sweeps, it)
-        f = system.update(H, scheme, t_lo, t_hi)
+        f = system.update(H, scheme, t_lo, t_hi, extrapolate)
         if f >= goal:
             return it + 1, H, f
     return max_iter, H, f

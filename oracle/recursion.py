@@ -17,6 +17,13 @@ Readings of what the paper leaves open (each also listed in the design notes):
   The weights are rebuilt from the top member of S_cum downwards.  Bins
   outside S_cum keep their log-weight offset to the nearest member above
   them (below, if there is none above).
+* Optional edge continuation (a reading of the recursion's boundary
+  treatment, which the paper leaves open): after an update, bins below the
+  lowest member of S_cum and above the highest take lnW continued linearly
+  with the slope between the edge member and the k-th member counted inwards
+  from it (k = 8, or the last member if S_cum is smaller), i.e. canonical
+  weights at the microcanonical inverse temperature of the sampled edge,
+  instead of the flat continuation of the plain schemes.
 * After every update lnW is shifted so that its maximum over the window is 0.
 * Flatness: min over S_cum of H / max of H, or -1 while either end of the
   target window has not been visited (the flatness goal min/max >= 0.5).
@@ -83,6 +90,33 @@ def recursive_update(lnW: np.ndarray, H: np.ndarray, s_cum: np.ndarray, phat: np
         ref = above[0] if above else members[-1]
         new[b] = lnW[b] + (new[ref] - lnW[ref])
     return normalise(new), s_cum, phat
+
+
+EDGE_MEMBERS = 8
+
+
+def extrapolate_edges(lnW: np.ndarray, s_cum: np.ndarray, k: int = EDGE_MEMBERS) -> np.ndarray:
+    """Continue lnW linearly beyond both ends of the cumulative visited set:
+    below its lowest member with the slope from that member to the k-th
+    member above it, above its highest member with the slope from the k-th
+    member below it.  Bins between members are left as they are.  Returns
+    a new array shifted to max 0; unchanged (but shifted) with fewer than two
+    members."""
+    new = np.array(lnW, dtype=np.float64, copy=True)
+    members = [b for b in range(len(new)) if s_cum[b]]
+    if len(members) < 2:
+        return normalise(new)
+    kk = min(k, len(members) - 1)
+    first, last = members[0], members[-1]
+    inner_lo = members[kk]
+    inner_hi = members[len(members) - 1 - kk]
+    slope_lo = (new[inner_lo] - new[first]) / (inner_lo - first)
+    slope_hi = (new[last] - new[inner_hi]) / (last - inner_hi)
+    for b in range(0, first):
+        new[b] = new[first] + slope_lo * (b - first)
+    for b in range(last + 1, len(new)):
+        new[b] = new[last] + slope_hi * (b - last)
+    return normalise(new)
 
 
 def flatness(H: np.ndarray, s_cum: np.ndarray, t_lo_bin: int | None = None,

@@ -62,6 +62,7 @@ struct Context {
     bool measured = false;
     bool tunnel = false;                 // walker kernels with tunnelling bookkeeping
     int *d_next_item = nullptr;          // work-item counter of persistent launches
+    unsigned int *d_walk_err = nullptr;  // set by a walker kernel whose bounded wait ran out
     // CUDA-graph mode: one graph per (sweeps, launch shape, flavour, grid)
     bool graph_mode = false;
     cudaGraph_t graph = nullptr;         // kept: its nodes address the executable's
@@ -112,7 +113,8 @@ void build_thresholds(const System &s, uint32_t *T)
     const int half = 2 * s.p.d;
     for (int b = 0; b < nb; ++b) {
         const double from = s.lnW[b];
-        uint32_t *row = T + (size_t)b * width;
+        uint32_t *row = T + (size_t)b * s.p.tstride;
+        for (int j = width; j < s.p.tstride; ++j) row[j] = 0u;   // row padding, never read
         for (int j = 0; j < width; ++j) {
             const int to = b + (j - half);
             if (to < 0 || to >= nb) {
@@ -198,6 +200,48 @@ void recursive_step(int nb, const int64_t *H, double *w, uint8_t *visited, doubl
     normalise_max_zero(w, nb);
 }
 
+// Edge continuation of the weights (MUCAL_SCHEME_EXTRAPOLATE): bins below
+// the lowest visited bin and above the highest take lnW continued linearly
+// with the slope between that edge and the kEdgeMembers-th visited bin
+// counted inwards (canonical weights at the sampled edge's microcanonical
+// temperature), so that walkers keep moving into the unsampled range.
+constexpr int kEdgeMembers = 8;
+
+void extrapolate_edges(int nb, double *w, const uint8_t *visited)
+{
+    std::vector<int> mem;
+    for (int b = 0; b < nb; ++b)
+        if (visited[b]) mem.push_back(b);
+    if (mem.size() >= 2) {
+        const size_t k = std::min<size_t>(kEdgeMembers, mem.size() - 1);
+        const int first = mem.front(), last = mem.back();
+        const int in_lo = mem[k], in_hi = mem[mem.size() - 1 - k];
+        const double slope_lo = (w[in_lo] - w[first]) / (double)(in_lo - first);
+        const double slope_hi = (w[last] - w[in_hi]) / (double)(last - in_hi);
+        for (int b = 0; b < first; ++b) w[b] = w[first] + slope_lo * (double)(b - first);
+        for (int b = last + 1; b < nb; ++b) w[b] = w[last] + slope_hi * (double)(b - last);
+    }
+    normalise_max_zero(w, nb);
+}
+
+// One weight update: the simple or the recursive step, then (flag) the edge
+// continuation.
+void update_step(int scheme, int nb, const int64_t *H, double *lnW, uint8_t *visited, double *pacc)
+{
+    if ((scheme & 0xF) == MUCAL_SCHEME_SIMPLE)
+        simple_step(nb, H, lnW, visited);
+    else
+        recursive_step(nb, H, lnW, visited, pacc);
+    if (scheme & MUCAL_SCHEME_EXTRAPOLATE) extrapolate_edges(nb, lnW, visited);
+}
+
+bool scheme_ok(int scheme)
+{
+    const int base = scheme & 0xF;
+    return (base == MUCAL_SCHEME_SIMPLE || base == MUCAL_SCHEME_RECURSIVE) &&
+           (scheme & ~(0xF | MUCAL_SCHEME_EXTRAPOLATE)) == 0;
+}
+
 // min/max of H over the visited bins of the target window [lo, hi] (bins;
 // lo < 0 selects the visited range), -1 while an end of it is unvisited.
 double flatness_of(int nb, const int64_t *H, const uint8_t *visited, int t_lo, int t_hi)
@@ -220,13 +264,6 @@ double flatness_of(int nb, const int64_t *H, const uint8_t *visited, int t_lo, i
         mx = std::max(mx, h);
     }
     return mx > 0.0 ? mn / mx : 0.0;
-}
-
-void update_simple(System &s) { simple_step(s.p.n_bins, s.H.data(), s.lnW.data(), s.visited.data()); }
-
-void update_recursive(System &s)
-{
-    recursive_step(s.p.n_bins, s.H.data(), s.lnW.data(), s.visited.data(), s.pacc.data());
 }
 
 double flatness(const System &s)
@@ -287,6 +324,7 @@ void destroy_context(Context *c)
     cudaFree(c->d_xacc);
     if (c->xthr_pinned) cudaFreeHost(c->xthr_pinned);
     cudaFree(c->d_next_item);
+    cudaFree(c->d_walk_err);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->ev_it0) cudaEventDestroy(c->ev_it0);
@@ -306,6 +344,9 @@ size_t smem_for(const LaunchShape &sh, const SysParams &p)
         bytes += (size_t)sh.walkers_per_block * mucal::field_smem_bytes(p);
     else if (sh.bits_in_smem)
         bytes += (size_t)sh.walkers_per_block * (size_t)p.words * sizeof(uint32_t);
+    // the windows start on the next 16-byte boundary behind the bitsets or fields
+    if (!sh.thr_in_smem && sh.thr_window && sh.kernel != MUCAL_KERNEL_THREAD)
+        bytes += 16 + (size_t)sh.walkers_per_block * mucal::thr_window_bytes(p);
     return bytes;
 }
 
@@ -374,6 +415,9 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     sh.walkers_per_block = cfg.walkers_per_block;
     sh.bits_in_smem = cfg.bits_in_smem ? 1 : 0;
     sh.persistent = cfg.persistent ? 1 : 0;
+    if (cfg.thr_window < 0 || cfg.thr_window > 2)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "thr_window must be 0, 1 or 2");
+    sh.thr_window = cfg.kernel != MUCAL_KERNEL_THREAD ? cfg.thr_window : 0;
     if (sh.kernel == MUCAL_KERNEL_THREAD) {
         if (sh.lanes != 1)
             return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
@@ -400,8 +444,16 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     sh.thr_in_smem = 1;
     for (auto &s : c->sys)
         if (smem_for(sh, s.p) > (size_t)c->max_smem) sh.thr_in_smem = 0;
+    if (cfg.thr_window == 2 && sh.thr_window) sh.thr_in_smem = 0;   // windows even if the table fits
     size_t smem = 0;
     for (auto &s : c->sys) smem = std::max(smem, smem_for(sh, s.p));
+    if (smem > (size_t)c->max_smem && sh.thr_window) {
+        // the threshold-row windows do not fit next to this block of walkers:
+        // read the thresholds from global memory instead
+        sh.thr_window = 0;
+        smem = 0;
+        for (auto &s : c->sys) smem = std::max(smem, smem_for(sh, s.p));
+    }
     if (smem > (size_t)c->max_smem)
         return fail(c, MUCAL_ERR_INVALID_ARG, "launch needs %zu bytes of shared memory, limit %d",
                     smem, c->max_smem);
@@ -426,9 +478,16 @@ int fetch_histogram(Context *c, System &s)
 {
     if (!c->ran) return fail(c, MUCAL_ERR_NOT_READY, "no iteration has been run");
     if (!s.hist_on_host) {
+        unsigned int err = 0;
         CUDA_TRY(c, cudaMemcpyAsync(s.H.data(), s.p.H, s.H.size() * sizeof(int64_t),
                                     cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_walk_err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (err) {
+            CUDA_TRY(c, cudaMemsetAsync(c->d_walk_err, 0, sizeof err, c->stream));
+            return fail(c, MUCAL_ERR_STATE, "a walker kernel's wait for its threshold rows ran out "
+                                            "(flag %u); the iteration's results are not valid", err);
+        }
         s.hist_on_host = true;
     }
     return MUCAL_OK;
@@ -616,6 +675,7 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
         }
         p.n_bins = s.desc.e_hi - p.e_lo + 1;
         p.width = 4 * p.d + 1;
+        p.tstride = (p.width + 3) & ~3;
         p.words = (p.V + 31) / 32;
         p.idx16 = p.V <= 65536 ? 1 : 0;
         p.n_walkers = sys[i].n_walkers;
@@ -639,7 +699,7 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
         ALLOC(S, nw * (size_t)p.V * ib);
         ALLOC(E, nw * sizeof(int32_t));
         ALLOC(hist, nw * (size_t)p.n_bins * sizeof(unsigned long long));
-        ALLOC(thr, (size_t)p.n_bins * p.width * sizeof(uint32_t));
+        ALLOC(thr, (size_t)p.n_bins * p.tstride * sizeof(uint32_t));
         ALLOC(accepts, nw * sizeof(unsigned long long));
         ALLOC(H, (size_t)p.n_bins * sizeof(unsigned long long));
         ALLOC(tun_state, nw * sizeof(uint8_t));
@@ -647,7 +707,7 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
 #undef ALLOC
         p.tun_lo = 0;                    // tunnelling ends: the window's ends
         p.tun_hi = p.n_bins - 1;
-        s.thr_count = (size_t)p.n_bins * p.width;
+        s.thr_count = (size_t)p.n_bins * p.tstride;
         if (cudaMallocHost(&s.thr_pinned, s.thr_count * sizeof(uint32_t)) != cudaSuccess) {
             s.thr_pinned = nullptr;
             return bail(fail(nullptr, MUCAL_ERR_OOM, "pinned host allocation failed"));
@@ -680,6 +740,10 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
     }
     if (cudaMalloc(&c->d_next_item, sizeof(int)) != cudaSuccess)
         return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of the work-item counter failed"));
+    if (cudaMalloc(&c->d_walk_err, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemsetAsync(c->d_walk_err, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
+        return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of the walker error flag failed"));
+    for (auto &s : c->sys) s.p.err = c->d_walk_err;
     if (cudaMalloc(&c->d_drop_err, sizeof(int)) != cudaSuccess ||
         cudaMemsetAsync(c->d_drop_err, 0, sizeof(int), c->stream) != cudaSuccess)
         return bail(fail(nullptr, MUCAL_ERR_OOM, "cudaMalloc of the droplet error flag failed"));
@@ -715,7 +779,7 @@ int mucal_init_systems(void **out, const mucal_system_desc *sys, int32_t n_sys, 
     // default launch: the field kernel when every system's fields fit in
     // shared memory, else the group kernel with the bitsets in shared memory
     // when they fit, else in global memory (8 lanes, 16 walkers per block)
-    mucal_launch_config def{MUCAL_KERNEL_FIELD, 8, 16, 1, 0};
+    mucal_launch_config def{MUCAL_KERNEL_FIELD, 8, 16, 1, 0, 1};
     for (auto &s : c->sys)
         if (smem_for(LaunchShape{MUCAL_KERNEL_FIELD, 8, 16, 1, 0, 0, 0}, s.p) > (size_t)c->max_smem)
             def.kernel = MUCAL_KERNEL_GROUP;
@@ -765,9 +829,13 @@ int mucal_get_thresholds(void *ctx, int32_t sys, uint32_t *T, int64_t n)
     int rc = check_sys(c, sys);
     if (rc != MUCAL_OK) return rc;
     const System &s = c->sys[sys];
-    if (!T || n != (int64_t)s.thr_count) return fail(c, MUCAL_ERR_INVALID_ARG, "bad threshold buffer size");
+    if (!T || n != (int64_t)s.p.n_bins * s.p.width)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "bad threshold buffer size");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    CUDA_TRY(c, cudaMemcpyAsync(T, s.p.thr, s.thr_count * 4, cudaMemcpyDeviceToHost, c->stream));
+    // the device rows are padded to tstride words; the caller gets width per row
+    CUDA_TRY(c, cudaMemcpy2DAsync(T, (size_t)s.p.width * 4, s.p.thr, (size_t)s.p.tstride * 4,
+                                  (size_t)s.p.width * 4, (size_t)s.p.n_bins, cudaMemcpyDeviceToHost,
+                                  c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return MUCAL_OK;
 }
@@ -790,6 +858,8 @@ int mucal_get_launch_config(void *ctx, mucal_launch_config *cfg)
     cfg->walkers_per_block = c->shape.walkers_per_block;
     cfg->bits_in_smem = c->shape.bits_in_smem;
     cfg->persistent = c->shape.persistent;
+    // with the whole table in shared memory the window setting has no effect
+    cfg->thr_window = c->shape.thr_in_smem ? 0 : c->shape.thr_window;
     return MUCAL_OK;
 }
 
@@ -825,7 +895,8 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
                           a.kernel == b.kernel && a.lanes == b.lanes &&
                           a.walkers_per_block == b.walkers_per_block &&
                           a.bits_in_smem == b.bits_in_smem && a.thr_in_smem == b.thr_in_smem &&
-                          a.smem_bytes == b.smem_bytes && a.persistent == b.persistent;
+                          a.smem_bytes == b.smem_bytes && a.persistent == b.persistent &&
+                          a.thr_window == b.thr_window;
         if (!same) {
             int rc = capture_iteration(c, (uint64_t)sweeps, iteration, grid);
             if (rc != MUCAL_OK) return rc;
@@ -887,16 +958,12 @@ int mucal_update_weights(void *ctx, int32_t sys, int32_t scheme, double *lnW_out
     Context *c = as_ctx(ctx);
     int rc = check_sys(c, sys);
     if (rc != MUCAL_OK) return rc;
-    if (scheme != MUCAL_SCHEME_SIMPLE && scheme != MUCAL_SCHEME_RECURSIVE)
-        return fail(c, MUCAL_ERR_INVALID_ARG, "unknown scheme %d", scheme);
+    if (!scheme_ok(scheme)) return fail(c, MUCAL_ERR_INVALID_ARG, "unknown scheme %d", scheme);
     System &s = c->sys[sys];
     CUDA_TRY(c, cudaSetDevice(c->device));
     rc = fetch_histogram(c, s);
     if (rc != MUCAL_OK) return rc;
-    if (scheme == MUCAL_SCHEME_SIMPLE)
-        update_simple(s);
-    else
-        update_recursive(s);
+    update_step(scheme, s.p.n_bins, s.H.data(), s.lnW.data(), s.visited.data(), s.pacc.data());
     const double f = flatness(s);
     rc = upload_thresholds(c, s);
     if (rc != MUCAL_OK) return rc;
@@ -943,9 +1010,8 @@ int mucal_weight_update(int32_t scheme, int32_t n_bins, const int64_t *H, double
                         uint8_t *visited, double *pacc, int32_t t_lo, int32_t t_hi,
                         double *flatness_out)
 {
-    if (scheme != MUCAL_SCHEME_SIMPLE && scheme != MUCAL_SCHEME_RECURSIVE)
-        return fail(nullptr, MUCAL_ERR_INVALID_ARG, "unknown scheme %d", scheme);
-    if (n_bins < 1 || !H || !lnW || !visited || (scheme == MUCAL_SCHEME_RECURSIVE && !pacc))
+    if (!scheme_ok(scheme)) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "unknown scheme %d", scheme);
+    if (n_bins < 1 || !H || !lnW || !visited || ((scheme & 0xF) == MUCAL_SCHEME_RECURSIVE && !pacc))
         return fail(nullptr, MUCAL_ERR_INVALID_ARG, "need n_bins >= 1 and H, lnW, visited (and pacc)");
     if (t_lo >= 0 && (t_hi < t_lo || t_hi >= n_bins))
         return fail(nullptr, MUCAL_ERR_INVALID_ARG, "target bins must satisfy 0 <= t_lo <= t_hi < n_bins");
@@ -953,10 +1019,7 @@ int mucal_weight_update(int32_t scheme, int32_t n_bins, const int64_t *H, double
         if (H[b] < 0) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "H[%d] is negative", b);
         if (!std::isfinite(lnW[b])) return fail(nullptr, MUCAL_ERR_INVALID_ARG, "lnW[%d] is not finite", b);
     }
-    if (scheme == MUCAL_SCHEME_SIMPLE)
-        simple_step(n_bins, H, lnW, visited);
-    else
-        recursive_step(n_bins, H, lnW, visited, pacc);
+    update_step(scheme, n_bins, H, lnW, visited, pacc);
     if (flatness_out) *flatness_out = flatness_of(n_bins, H, visited, t_lo < 0 ? -1 : t_lo, t_hi);
     return MUCAL_OK;
 }

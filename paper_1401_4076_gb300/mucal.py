@@ -29,6 +29,7 @@ MUCAL_ERR_STATE = -6
 MUCAL_FLAG_PER_WALKER_HIST = 0x1
 MUCAL_SCHEME_SIMPLE = 0
 MUCAL_SCHEME_RECURSIVE = 1
+MUCAL_SCHEME_EXTRAPOLATE = 0x10
 MUCAL_KERNEL_THREAD = 0
 MUCAL_KERNEL_GROUP = 1
 MUCAL_KERNEL_FIELD = 2
@@ -62,7 +63,7 @@ class mucal_system_desc(ctypes.Structure):
 class mucal_launch_config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
                 ("walkers_per_block", ctypes.c_int32), ("bits_in_smem", ctypes.c_int32),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("thr_window", ctypes.c_int32)]
 
 
 class mucal_system_info(ctypes.Structure):
@@ -218,9 +219,9 @@ def mucal_get_thresholds(ctx, sys, n_bins, width):
 
 
 def mucal_set_launch_config(ctx, kernel=MUCAL_KERNEL_THREAD, lanes_per_walker=1,
-                            walkers_per_block=32, bits_in_smem=1, persistent=0):
+                            walkers_per_block=32, bits_in_smem=1, persistent=0, thr_window=1):
     cfg = mucal_launch_config(kernel, lanes_per_walker, walkers_per_block, bits_in_smem,
-                              int(persistent))
+                              int(persistent), int(thr_window))
     _check(load_library().mucal_set_launch_config(ctx, ctypes.byref(cfg)), ctx)
 
 
@@ -229,7 +230,7 @@ def mucal_get_launch_config(ctx):
     _check(load_library().mucal_get_launch_config(ctx, ctypes.byref(cfg)), ctx)
     return {"kernel": cfg.kernel, "lanes_per_walker": cfg.lanes_per_walker,
             "walkers_per_block": cfg.walkers_per_block, "bits_in_smem": cfg.bits_in_smem,
-            "persistent": cfg.persistent}
+            "persistent": cfg.persistent, "thr_window": cfg.thr_window}
 
 
 def mucal_set_graph_mode(ctx, enable):

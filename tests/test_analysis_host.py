@@ -295,3 +295,29 @@ def test_ln_omega_normalise_of_multi_histogram_matches_oracle():
     v = ~np.isnan(ref)
     shift = (math.lgamma(1001) - math.lgamma(101) - math.lgamma(901)) - np.logaddexp.reduce(ref[v])
     np.testing.assert_allclose(got[v], ref[v] + shift, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("base", ["simple", "recursive"])
+def test_weight_update_with_edge_continuation_matches_oracle(base):
+    """MUCAL_SCHEME_EXTRAPOLATE or-ed with either scheme against the oracle's
+    update followed by its edge continuation, over a sequence whose visited
+    range grows at both ends."""
+    from oracle.recursion import extrapolate_edges, recursive_update, simple_update
+    nb = 201
+    seq = _histogram_sequence(nb, 15, 77)
+    scheme = (m.MUCAL_SCHEME_SIMPLE if base == "simple" else m.MUCAL_SCHEME_RECURSIVE)
+    st = m.WeightState(nb)
+    lnW = np.zeros(nb)
+    s_cum = np.zeros(nb, bool)
+    phat = np.zeros(nb)
+    for H in seq:
+        m.mucal_weight_update(st, H, scheme | m.MUCAL_SCHEME_EXTRAPOLATE)
+        if base == "simple":
+            s_cum = s_cum | (H > 0)
+            lnW = simple_update(lnW, H)
+        else:
+            lnW, s_cum, phat = recursive_update(lnW, H, s_cum, phat)
+        lnW = extrapolate_edges(lnW, s_cum)
+        np.testing.assert_allclose(st.lnW, lnW, rtol=1e-12, atol=1e-12 * max(1, np.abs(lnW).max()))
+    with pytest.raises(m.MucalError):
+        m.mucal_weight_update(m.WeightState(nb), seq[0], 0x20)

@@ -223,3 +223,58 @@ def _run_pin(kind, lib, tmp_path):
 def test_pin_catches_planted_mistake(tmp_path, mutant, pin):
     assert _run_pin(pin, _build(tmp_path, "clean", None), tmp_path)
     assert not _run_pin(pin, _build(tmp_path, mutant, MUTATIONS[mutant]), tmp_path)
+
+
+# ---- the Python part of the oracle: the edge continuation of the weights ----
+
+RECURSION_SRC = os.path.join(os.path.dirname(obuild.__file__), "recursion.py")
+
+PY_MUTATIONS = {
+    "edge slope sign flipped": ("new[b] = new[first] + slope_lo * (b - first)",
+                                "new[b] = new[first] - slope_lo * (b - first)"),
+    "edge slope from the wrong member": ("inner_lo = members[kk]", "inner_lo = members[kk - 1]"),
+    "upper edge continued flat": ("new[b] = new[last] + slope_hi * (b - last)", "new[b] = new[last]"),
+}
+
+
+def _mutant_recursion(mutation):
+    import types
+    src = open(RECURSION_SRC).read()
+    if mutation is not None:
+        old, new = mutation
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    mod = types.ModuleType("recursion_mutant")
+    exec(compile(src, "recursion_mutant", "exec"), mod.__dict__)
+    return mod
+
+
+def _edge_pins(mod):
+    """The two edge-continuation pins of test_oracle_recursion, on a module."""
+    rng = np.random.default_rng(3)
+    nb, lo, hi, beta = 60, 10, 45, 0.7
+    s_cum = np.zeros(nb, bool)
+    s_cum[lo:hi + 1] = True
+    E = np.arange(nb) - nb
+    lnW = np.where(s_cum, -beta * E, rng.normal(size=nb))
+    out = mod.extrapolate_edges(lnW, s_cum)
+    shift = out[lo] - lnW[lo]
+    ok = (np.allclose(out[:lo] - shift, -beta * E[:lo], atol=1e-9) and
+          np.allclose(out[hi + 1:] - shift, -beta * E[hi + 1:], atol=1e-9))
+    lnW = np.zeros(12)
+    s_cum = np.zeros(12, bool)
+    s_cum[[2, 3, 4, 5, 9]] = True
+    lnW[[2, 3, 4, 5, 9]] = [7.0, 5.0, 4.0, 3.0, 0.0]
+    out1 = mod.extrapolate_edges(lnW, s_cum, k=1)
+    expect1 = np.array([11, 9, 7, 5, 4, 3, 0, 0, 0, 0, -0.75, -1.5]) - 11.0
+    return ok and np.allclose(out1, expect1, atol=1e-12)
+
+
+def test_edge_pins_pass_on_the_oracle():
+    assert _edge_pins(_mutant_recursion(None))
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_edge_pins_catch_planted_mistakes(name):
+    with np.errstate(all="ignore"):          # a mutant may divide by zero
+        assert not _edge_pins(_mutant_recursion(PY_MUTATIONS[name])), name

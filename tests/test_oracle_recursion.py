@@ -228,3 +228,70 @@ def test_reweight_observable_is_canonical_enumeration():
         w = np.array([math.exp(-beta * e) for e, _ in configs])
         ref = float((w * np.array([v for _, v in configs])).sum() / w.sum())
         assert muca.reweight_observable(lnW, H, E_LO, beta, obs) == pytest.approx(ref, rel=1e-10)
+
+
+# ------------------------------------------------ edge continuation (flag) --
+
+def test_edge_continuation_extends_canonical_weights_exactly():
+    """Canonical weights lnW = -beta E on the visited members (with gaps and
+    arbitrary values between members) continue as the same line beyond both
+    ends: the continuation is the canonical weight at the edge's slope."""
+    from oracle.recursion import extrapolate_edges
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        nb = int(rng.integers(20, 200))
+        beta = float(rng.normal(scale=2.0))
+        s_cum = np.zeros(nb, bool)
+        lo = int(rng.integers(1, nb // 3))
+        hi = int(rng.integers(2 * nb // 3, nb - 1))
+        s_cum[lo:hi + 1] = rng.random(hi - lo + 1) < 0.8
+        s_cum[lo] = s_cum[hi] = True
+        E = np.arange(nb) - nb
+        lnW = np.where(s_cum, -beta * E, rng.normal(size=nb))
+        out = extrapolate_edges(lnW, s_cum)
+        shift = out[lo] - lnW[lo]
+        np.testing.assert_allclose(out[:lo] - shift, -beta * E[:lo], rtol=0, atol=1e-9)
+        np.testing.assert_allclose(out[hi + 1:] - shift, -beta * E[hi + 1:], rtol=0, atol=1e-9)
+        # members and interior gaps keep their values (up to the common shift)
+        np.testing.assert_allclose(out[lo:hi + 1] - shift, lnW[lo:hi + 1], rtol=0, atol=1e-9)
+        assert out.max() == 0.0
+
+
+def test_edge_continuation_by_hand():
+    """Members 2..5 and 9 of 12 bins with k = 8 > members: the slopes come
+    from the far ends of the member set (bins 2 and 9)."""
+    from oracle.recursion import extrapolate_edges
+    lnW = np.zeros(12)
+    s_cum = np.zeros(12, bool)
+    s_cum[[2, 3, 4, 5, 9]] = True
+    lnW[[2, 3, 4, 5, 9]] = [7.0, 5.0, 4.0, 3.0, 0.0]
+    out = extrapolate_edges(lnW, s_cum)
+    # below: slope (lnW[9] - lnW[2]) / 7 = -1 -> bins 0, 1 take 9, 8
+    # above: slope (lnW[9] - lnW[2]) / 7 = -1 -> bins 10, 11 take -1, -2
+    expect = np.array([9, 8, 7, 5, 4, 3, 0, 0, 0, 0, -1, -2], dtype=float) - 9.0
+    np.testing.assert_allclose(out, expect, atol=1e-12)
+    # with k = 1 the slopes come from the neighbouring members
+    out1 = extrapolate_edges(lnW, s_cum, k=1)
+    expect1 = np.array([11, 9, 7, 5, 4, 3, 0, 0, 0, 0, -0.75, -1.5]) - 11.0
+    np.testing.assert_allclose(out1, expect1, atol=1e-12)
+
+
+def test_edge_continuation_needs_two_members():
+    from oracle.recursion import extrapolate_edges
+    lnW = np.array([3.0, 1.0, 2.0])
+    s = np.array([False, True, False])
+    np.testing.assert_array_equal(extrapolate_edges(lnW, s), lnW - 3.0)
+
+
+@pytest.mark.slow
+def test_multicanonical_run_with_edge_continuation_recovers_ln_omega_4x4():
+    """The full method with the simple iteration and the edge continuation
+    (from lnW = 0, 4x4, N = 8): flat, then ln Omega within 0.02 of the
+    enumeration on every bin."""
+    sysm = muca.System(2, 4, 8, 32, 300)
+    iters, H, f = muca.run_to_flat(sysm, 2000, 40, "simple", t_lo=-12, t_hi=0, extrapolate=True)
+    assert f >= 0.5, (iters, f)
+    H, _, _ = sysm.iterate(80000, 1000)
+    est = ln_omega(sysm.lnW, H, 16, 8)
+    for e, c in OM.items():
+        assert abs(est[e - E_LO] - math.log(c)) < 0.02, (e, est[e - E_LO], math.log(c))
