@@ -56,7 +56,7 @@ def ln_omega_multi(history, V: int, N: int) -> np.ndarray:
 def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None, goal=0.5,
                     scheme=m.MUCAL_SCHEME_RECURSIVE, cuda_stream=None, launch=None,
                     final_sweeps: int = 0, relax_iters: int = 0, relax_tol: float = 0.0,
-                    history: int = 0):
+                    history: int = 0, sweeps_growth: int = 1, stall: int = 10):
     """Run the weight iteration of Sec. 2 for several systems in one context
     (one launch per iteration) until each reaches flatness >= goal inside its
     target window (t_lo, t_hi) or max_iter iterations.  A system that has
@@ -76,6 +76,12 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
     history: keep the histograms of the last `history` updating iterations of
     each system with the weights they were sampled with, in
     RunResult.extra["history"] (for ``ln_omega_multi``).
+
+    sweeps_growth > 1: the sweeps per iteration double whenever no system's
+    flatness has improved by more than 0.02 over its best for `stall`
+    iterations, up to sweeps_growth times the starting value (more
+    statistics per histogram once the weights are close; the systems of one
+    context share one launch and therefore one sweep count).
     """
     n = len(systems)
     t0 = time.perf_counter()
@@ -97,8 +103,13 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
         relaxed = [0] * n
         last_mean = [None] * n
         hist_keep = [[] for _ in range(n)]
+        sw0 = sweeps
+        best = [-1.0] * n
+        since = 0
+        sweeps_used = []
         for it in range(max_iter):
             mc.run_iteration(sweeps, it)
+            sweeps_used.append(sweeps)
             for i in range(n):
                 if done[i]:
                     continue
@@ -129,6 +140,17 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
                     walls[i] = time.perf_counter() - t0
             if all(done):
                 break
+            if sweeps_growth > 1:
+                improved = False
+                for i in range(n):
+                    if not done[i] and flat[i] and flat[i][-1] == flat[i][-1] and flat[i][-1] > best[i] + 0.02:
+                        best[i] = flat[i][-1]
+                        improved = True
+                since = 0 if improved else since + 1
+                if since >= stall and sweeps < sw0 * sweeps_growth:
+                    sweeps *= 2
+                    since = 0
+                    best = [-1.0] * n
         for i in range(n):
             if not done[i]:
                 walls[i] = time.perf_counter() - t0
@@ -143,44 +165,73 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
             for i in range(n):
                 final_H[i] = mc.histogram(i)
         for i in range(n):
+            extra = {"history": hist_keep[i]} if history else {}
+            extra["sweeps"] = sweeps_used[:iters[i]]
             results.append(RunResult(tuple(systems[i]), iters[i], flat[i], done[i], walls[i],
                                      lnWs[i], final_H[i] if final_sweeps else Hs[i],
-                                     attempts[i], {"history": hist_keep[i]} if history else {}))
+                                     attempts[i], extra))
     return results
 
 
 
 
 def main(argv=None):
+    """Iterate one system to a flat histogram, for one or several walker
+    seeds; one JSON line per run and one summary line."""
     import argparse
     import json
     ap = argparse.ArgumentParser(description="iterate one system to a flat histogram")
     ap.add_argument("--system", required=True, help="d:L:N:walkers")
     ap.add_argument("--window", default="0:0", help="simulation window lo:hi (0:0 = [-dN, 0])")
     ap.add_argument("--target", default="", help="flatness target window lo:hi (default: visited range)")
+    ap.add_argument("--tempering-target", type=float, default=0.0,
+                    help="take the flatness target window from a parallel-tempering run at this "
+                         "temperature (Sec. 3): from the energy below which the coldest replicas "
+                         "spent 1%% of their time to the highest energy of the replica at T")
     ap.add_argument("--sweeps", type=int, default=1000)
     ap.add_argument("--max-iter", type=int, default=200)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--seeds", type=int, default=1, help="runs with consecutive walker seed blocks")
     ap.add_argument("--scheme", choices=["recursive", "simple"], default="recursive")
+    ap.add_argument("--extrapolate", action="store_true",
+                    help="or MUCAL_SCHEME_EXTRAPOLATE into the scheme (edge continuation)")
+    ap.add_argument("--sweeps-growth", type=int, default=1)
     args = ap.parse_args(argv)
     d, L, N, W = (int(x) for x in args.system.split(":"))
     lo, hi = (int(x) for x in args.window.split(":"))
     target = [tuple(int(x) for x in args.target.split(":"))] if args.target else None
+    temper = None
+    if args.tempering_target > 0:
+        from . import tempering
+        _, _, info = tempering.energy_range(d, L, N, args.tempering_target)
+        target = [(info["cold_q01"], info["target_max"])]
+        temper = {"T": args.tempering_target, "cold_q01": info["cold_q01"],
+                  "target_max": info["target_max"], "cold_min": info["cold_min"]}
     scheme = m.MUCAL_SCHEME_RECURSIVE if args.scheme == "recursive" else m.MUCAL_SCHEME_SIMPLE
-    r = iterate_to_flat([(d, L, N, W, lo, hi, args.seed)], args.sweeps, args.max_iter,
-                        targets=target, scheme=scheme)[0]
+    if args.extrapolate:
+        scheme |= m.MUCAL_SCHEME_EXTRAPOLATE
     e_lo = -d * N if (lo == 0 and hi == 0) else lo
-    vis = np.nonzero(r.H > 0)[0]
-    print(json.dumps({"system": {"d": d, "L": L, "N": N, "walkers": W,
-                                 "window": [e_lo, e_lo + len(r.H) - 1]},
-                      "target": target[0] if target else "visited range",
-                      "sweeps_per_iteration": args.sweeps, "scheme": args.scheme,
-                      "iterations": r.iterations, "converged": r.converged,
-                      "wall_s": round(r.wall_s, 3), "attempts": r.attempts,
-                      "attempts_per_s": r.attempts / max(r.wall_s, 1e-9),
-                      "final_flatness": r.flatness[-1] if r.flatness else None,
-                      "lowest_energy_visited": int(e_lo + vis.min()) if len(vis) else None,
-                      "flatness_every_10": [round(x, 4) for x in r.flatness[::10]]}))
+    rows = []
+    for k in range(args.seeds):
+        r = iterate_to_flat([(d, L, N, W, lo, hi, args.seed + k * W)], args.sweeps, args.max_iter,
+                            targets=target, scheme=scheme, sweeps_growth=args.sweeps_growth)[0]
+        vis = np.nonzero(r.H > 0)[0]
+        row = {"system": {"d": d, "L": L, "N": N, "walkers": W,
+                          "window": [e_lo, e_lo + len(r.H) - 1], "seed_base": args.seed + k * W},
+               "target": target[0] if target else "visited range", "tempering": temper,
+               "sweeps_per_iteration": args.sweeps, "sweeps_last": r.extra["sweeps"][-1],
+               "scheme": args.scheme + (" + edge continuation" if args.extrapolate else ""),
+               "iterations": r.iterations, "converged": r.converged,
+               "wall_s": round(r.wall_s, 3), "attempts": r.attempts,
+               "final_flatness": r.flatness[-1] if r.flatness else None,
+               "lowest_energy_visited": int(e_lo + vis.min()) if len(vis) else None,
+               "flatness_every_10": [round(x, 4) for x in r.flatness[::10]]}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"summary": True, "runs": len(rows),
+                      "converged": sum(r["converged"] for r in rows),
+                      "mean_iterations": float(np.mean([r["iterations"] for r in rows])),
+                      "mean_wall_s": float(np.mean([r["wall_s"] for r in rows]))}), flush=True)
 
 
 if __name__ == "__main__":

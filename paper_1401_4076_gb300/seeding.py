@@ -106,10 +106,10 @@ def small_training_systems(frac: float = 0.5, walkers: int = 512, seed_base: int
 
 def compare_plain_and_seeded(net, desc, sweeps: int, max_iter: int, relax_iters: int = 30,
                              relax_tol: float = 0.002, seeded_scheme=m.MUCAL_SCHEME_SIMPLE,
-                             cuda_stream=None):
-    """Iterations and wall time to flatness from lnW = 0 with the recursive
-    scheme (the plain method, the reference) and from the network's seed,
-    same system, seeds, sweeps and window.
+                             cuda_stream=None, plain_scheme=m.MUCAL_SCHEME_RECURSIVE):
+    """Iterations and wall time to flatness from lnW = 0 with plain_scheme
+    (the plain method, the reference) and from the network's seed, same
+    system, seeds, sweeps and window.
 
     The seeded run updates with the simple scheme W/H: its first histograms
     come from walkers still relaxing towards the seeded weights, and the
@@ -118,7 +118,7 @@ def compare_plain_and_seeded(net, desc, sweeps: int, max_iter: int, relax_iters:
     recursive scheme after a seed is slower than either plain start)."""
     d, L, N, W, lo, hi, seed = desc
     seedW = seed_weights(net, d, L, N, lo, hi)
-    plain = iterate_to_flat([desc], sweeps, max_iter, cuda_stream=cuda_stream)[0]
+    plain = iterate_to_flat([desc], sweeps, max_iter, scheme=plain_scheme, cuda_stream=cuda_stream)[0]
     seeded = iterate_to_flat([desc], sweeps, max_iter, lnW0=[seedW], relax_iters=relax_iters,
                              relax_tol=relax_tol, scheme=seeded_scheme, cuda_stream=cuda_stream)[0]
     return plain, seeded, seedW
@@ -196,7 +196,17 @@ def main(argv=None):
                     help="rungs d:L:rho separated by commas, climbed after training")
     ap.add_argument("--ladder-walkers", type=int, default=4096)
     ap.add_argument("--ladder-sweeps", type=int, default=50)
+    ap.add_argument("--train-steps-only", type=int, default=0,
+                    help="only run this many training steps of the network on the 8192-row "
+                         "test batch (a fixed workload for profiling the training kernels)")
     args = ap.parse_args(argv)
+    if args.train_steps_only:
+        from .workloads import mlp_initial_params, mlp_test_batch
+        X, t = mlp_test_batch(8192, 1)
+        with m.Mlp(mlp_initial_params(0)) as net:
+            loss = net.train(X, t, steps=args.train_steps_only, lr=1e-3)
+        print(json.dumps({"train_steps": args.train_steps_only, "rows": 8192, "loss": loss}))
+        return
     t0 = time.perf_counter()
     small = small_training_systems(args.frac)
     res = iterate_to_flat(small, sweeps=100, max_iter=200, final_sweeps=1000)
