@@ -64,13 +64,37 @@ def alg_ops_per_attempt(d: int) -> int:
 TRAFFIC_MEASURED = {
     "2d-L64-N410-w4096": {"bytes": 33.89e6 + 954.13e6, "kernel_sha": "a476ebb38f79900c",
                           "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28}},
+    # one full 200-sweep launch (profiles/walker_update_group_batched-27-systems-w16384.md)
+    "batched-27-systems-w16384": {"bytes": 705.094e9 + 300.382e9, "kernel_sha": "f802b33f069290ef",
+                                  "launch": {"kernel": 1, "lanes_per_walker": 16,
+                                             "walkers_per_block": 8, "bits_in_smem": 1,
+                                             "thr_window": 0}},
+    # a 5-sweep launch scaled by 40 to the workload's 200 sweeps (the list reads and
+    # writes grow with the attempts; profiles/walker_update_group_3d-L32-N3277-w8192.md)
+    "3d-L32-N3277-w8192": {"bytes": 40 * (18.4516e9 + 7.0474e9), "kernel_sha": "f802b33f069290ef",
+                           "launch": {"kernel": 1, "lanes_per_walker": 4, "walkers_per_block": 56,
+                                      "bits_in_smem": 1, "thr_window": 0}},
 }
 
 # Executed instructions per attempted move of the walker-update kernel, from
 # one ncu capture of a launch of the workload (smsp__inst_executed.sum x 32
 # and smsp__thread_inst_executed.sum, divided by the launch's attempts), under
 # the same validity rule as the traffic record: launch shape and kernel source.
-INSTR_MEASURED = {}
+INSTR_MEASURED = {
+    # 2-sweep launch, same shape as the traffic record (instructions per attempt do not
+    # depend on the sweep count beyond the per-block set-up)
+    "batched-27-systems-w16384": {"warp_inst_per_attempt": 4.215209e9 / 72.3314e6,
+                                  "thread_inst_per_attempt": 1.21995e11 / 72.3314e6,
+                                  "kernel_sha": "f802b33f069290ef", "any_sweeps": True,
+                                  "launch": {"kernel": 1, "lanes_per_walker": 16,
+                                             "walkers_per_block": 8, "bits_in_smem": 1,
+                                             "thr_window": 0}},
+    "3d-L32-N3277-w8192": {"warp_inst_per_attempt": 2.895069e9 / 134.2259e6,
+                           "thread_inst_per_attempt": 8.64865e10 / 134.2259e6,
+                           "kernel_sha": "f802b33f069290ef", "any_sweeps": True,
+                           "launch": {"kernel": 1, "lanes_per_walker": 4, "walkers_per_block": 56,
+                                      "bits_in_smem": 1, "thr_window": 0}},
+}
 
 KERNEL_NAMES = {0: "walker_update_thread", 1: "walker_update_group", 2: "walker_update_field"}
 
@@ -84,7 +108,7 @@ def _kernel_sha() -> str:
 
 def _record_for(table: dict, workload: str, sweeps_default: bool, launch: dict):
     rec = table.get(workload)
-    if rec is None or not sweeps_default:
+    if rec is None or not (sweeps_default or rec.get("any_sweeps")):
         return None
     if any(launch.get(k) != v for k, v in rec["launch"].items()):
         return None
@@ -297,6 +321,9 @@ def main(argv=None):
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--wpb", type=int, default=0)
     ap.add_argument("--smem", type=int, default=-1)
+    ap.add_argument("--thr-window", type=int, default=-1,
+                    help="0: thresholds from global memory when the table does not fit in "
+                         "shared memory, 1: per-walker row windows, 2: windows always")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run after the warm-up steps)")
     ap.add_argument("--tune-sweeps", type=int, default=20)
@@ -406,7 +433,8 @@ def main(argv=None):
 
 
 def _explicit_launch(args):
-    return args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0
+    return (args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0
+            or args.thr_window >= 0)
 
 
 def measure(wl, args, systems, stream, device, world, flush, clocks_rank0=True, ceiling=True):
@@ -427,7 +455,8 @@ def measure(wl, args, systems, stream, device, world, flush, clocks_rank0=True, 
                    lanes_per_walker=args.lanes or cur["lanes_per_walker"],
                    walkers_per_block=args.wpb or cur["walkers_per_block"],
                    bits_in_smem=args.smem if args.smem >= 0 else cur["bits_in_smem"],
-                   persistent=args.persistent if args.persistent >= 0 else cur["persistent"])
+                   persistent=args.persistent if args.persistent >= 0 else cur["persistent"],
+                   thr_window=args.thr_window if args.thr_window >= 0 else 1)
         mc.set_launch(**cfg)
     if args.graph:
         mc.set_graph_mode(True)
