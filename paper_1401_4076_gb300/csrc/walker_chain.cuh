@@ -992,8 +992,11 @@ __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &
                                (SB ? (uint32_t)wpb * (uint32_t)p.words * 4u : 0u);
         window_addrs(p, after, wpb, active ? lw : 0, ring_s, mbar_s);
     }
-    // slot compare for G = 8, site compare otherwise (measured on GB300)
-    constexpr bool kSlot = (G == 8);
+    // slot compare for G = 4 and 8, site compare otherwise (measured on GB300:
+    // 3D L=32 at 4 lanes 1.098e10 -> 1.119e10 with slot compare, which does not
+    // wait for the next batch's list reads; the batch at 16 lanes 8.56e9 ->
+    // 8.13e9, where the extra shuffle per round costs more)
+    constexpr bool kSlot = (G == 4 || G == 8);
     if (p.d == 2) {
         if (p.idx16) chain_rounds<2, uint16_t, G, TM, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);
         else chain_rounds<2, uint32_t, G, TM, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);

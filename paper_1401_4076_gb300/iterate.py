@@ -175,6 +175,114 @@ def iterate_to_flat(systems, sweeps: int, max_iter: int, targets=None, lnW0=None
 
 
 
+@dataclass
+class StagedResult:
+    desc: tuple
+    converged: bool
+    iterations: int             # updating iterations of both stages (relaxation counted too)
+    range_iterations: int       # stage 1 (or relaxation after a seed)
+    wall_s: float
+    flatness: list
+    lnW: np.ndarray
+    span: tuple                 # sampled energy range when stage 2 began
+    tunnel_events: int          # end-to-end travels during stage 2 (Sec. 4) between the
+                                # target's ends, else those of the sampled range
+    sweeps: int                 # attempted sweeps of all iterations, discards included
+
+
+def iterate_staged(desc, lnW0=None, range_sweeps: int = 1000, sweeps: int = 4000,
+                   discard: int = 1000, max_iter: int = 200, stable: int = 5, goal: float = 0.5,
+                   target=None, scheme=m.MUCAL_SCHEME_SIMPLE | m.MUCAL_SCHEME_EXTRAPOLATE,
+                   relax_max: int = 10, cuda_stream=None, launch=None) -> StagedResult:
+    """The iteration of Sec. 2 in two stages for one system.
+
+    Stage 1 (from lnW = 0): short iterations of `range_sweeps` with the simple
+    update and the edge continuation, until the sampled energy range has not
+    changed for `stable` iterations.  With a starting lnW0 (a learned seed)
+    stage 1 is replaced by relaxation: iterations of `range_sweeps` with the
+    seed held fixed inside the sampled range and continued at the sampled
+    range's edges as the edge continuation does (so that the walkers reach
+    energies where the seed is too steep), until the sampled range has not
+    changed for `stable` iterations (at most `relax_max`); random placements
+    are equilibrium states of lnW = 0 only.  Stage 2: iterations of `sweeps` measured sweeps, each after a
+    discarded run of `discard` sweeps (Sec. 2 asks for equilibrium runs with
+    fixed weights: the discard lets the walkers follow the last update),
+    updated with `scheme`, until the flatness over the target window (default:
+    the sampled range) reaches `goal`.  Tunnelling events over the sampled
+    range (Sec. 4's criterion) are counted during stage 2."""
+    d, L, N, W, lo, hi, seed = desc
+    t0 = time.perf_counter()
+    it_no = 0
+    total_sweeps = 0
+    flat = []
+    with m.Mucal([desc], cuda_stream=cuda_stream) as mc:
+        if launch:
+            mc.set_launch(**launch)
+        if lnW0 is not None:
+            mc.set_weights(0, lnW0)
+        if target is not None:
+            mc.set_target_window(0, *target)
+        e_lo = mc.info[0]["e_lo"]
+        nb = mc.info[0]["n_bins"]
+        span, same, n1 = None, 0, 0
+        cap1 = max_iter if lnW0 is None else relax_max
+        while same < stable and n1 < cap1:
+            sw = range_sweeps
+            mc.run_iteration(sw, it_no)
+            it_no += 1
+            n1 += 1
+            total_sweeps += sw
+            H = mc.histogram(0)
+            vis = np.nonzero(H > 0)[0]
+            sp = (int(vis.min()), int(vis.max()))
+            if span is not None:
+                sp = (min(sp[0], span[0]), max(sp[1], span[1]))
+            same = same + 1 if sp == span else 0
+            span = sp
+            if lnW0 is None:
+                _, f = mc.update_weights(0, scheme)
+                flat.append(f)
+            else:
+                # the seed inside the sampled range, continued beyond it
+                st = m.WeightState(nb, lnW0)
+                st.visited[sp[0]:sp[1] + 1] = 1
+                m.mucal_weight_update(st, np.zeros(nb, dtype=np.int64),
+                                      m.MUCAL_SCHEME_SIMPLE | m.MUCAL_SCHEME_EXTRAPOLATE)
+                mc.set_weights(0, st.lnW)
+                if target is not None:
+                    mc.set_target_window(0, *target)
+                flat.append(float("nan"))
+        lnW = mc.weights(0)
+        # stage 2 starts with a fresh recursion memory (the stage-1 histograms
+        # come from walkers far from equilibrium)
+        mc.set_weights(0, lnW)
+        if target is not None:
+            mc.set_target_window(0, *target)
+        # tunnelling events between the target's ends (else the sampled range's)
+        mc.set_tunnel_window(0, *(target if target is not None else
+                                  (e_lo + span[0], e_lo + span[1])))
+        converged = False
+        n2 = 0
+        while n1 + n2 < max_iter:
+            if discard:
+                mc.run_iteration(discard, it_no)
+                it_no += 1
+                total_sweeps += discard
+            mc.run_iteration(sweeps, it_no)
+            it_no += 1
+            n2 += 1
+            total_sweeps += sweeps
+            _, f = mc.update_weights(0, scheme)
+            flat.append(f)
+            if f >= goal:
+                converged = True
+                break
+        tun = mc.tunnel_counts(0)[0]
+        lnW = mc.weights(0)
+    return StagedResult(tuple(desc), converged, n1 + n2, n1, time.perf_counter() - t0, flat, lnW,
+                        (e_lo + span[0], e_lo + span[1]), int(tun), total_sweeps)
+
+
 def main(argv=None):
     """Iterate one system to a flat histogram, for one or several walker
     seeds; one JSON line per run and one summary line."""
@@ -196,6 +304,11 @@ def main(argv=None):
     ap.add_argument("--extrapolate", action="store_true",
                     help="or MUCAL_SCHEME_EXTRAPOLATE into the scheme (edge continuation)")
     ap.add_argument("--sweeps-growth", type=int, default=1)
+    ap.add_argument("--staged", action="store_true",
+                    help="two stages (iterate_staged): range with --range-sweeps, then --sweeps "
+                         "measured after --discard discarded sweeps per iteration")
+    ap.add_argument("--range-sweeps", type=int, default=1000)
+    ap.add_argument("--discard", type=int, default=1000)
     args = ap.parse_args(argv)
     d, L, N, W = (int(x) for x in args.system.split(":"))
     lo, hi = (int(x) for x in args.window.split(":"))
@@ -213,7 +326,25 @@ def main(argv=None):
     e_lo = -d * N if (lo == 0 and hi == 0) else lo
     rows = []
     for k in range(args.seeds):
-        r = iterate_to_flat([(d, L, N, W, lo, hi, args.seed + k * W)], args.sweeps, args.max_iter,
+        desc = (d, L, N, W, lo, hi, args.seed + k * W)
+        if args.staged:
+            r = iterate_staged(desc, range_sweeps=args.range_sweeps, sweeps=args.sweeps,
+                               discard=args.discard, max_iter=args.max_iter,
+                               target=target[0] if target else None, scheme=scheme)
+            row = {"system": {"d": d, "L": L, "N": N, "walkers": W, "seed_base": desc[-1]},
+                   "target": target[0] if target else "sampled range", "tempering": temper,
+                   "scheme": args.scheme + (" + edge continuation" if args.extrapolate else ""),
+                   "stages": {"range_sweeps": args.range_sweeps, "sweeps": args.sweeps,
+                              "discard": args.discard},
+                   "iterations": r.iterations, "range_iterations": r.range_iterations,
+                   "converged": r.converged, "wall_s": round(r.wall_s, 3),
+                   "sampled_range": r.span, "tunnel_events_stage2": r.tunnel_events,
+                   "total_sweeps": r.sweeps, "final_flatness": r.flatness[-1],
+                   "flatness_every_5": [round(x, 4) for x in r.flatness[::5]]}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            continue
+        r = iterate_to_flat([desc], args.sweeps, args.max_iter,
                             targets=target, scheme=scheme, sweeps_growth=args.sweeps_growth)[0]
         vis = np.nonzero(r.H > 0)[0]
         row = {"system": {"d": d, "L": L, "N": N, "walkers": W,

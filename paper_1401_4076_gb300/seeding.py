@@ -24,7 +24,8 @@ import time
 import numpy as np
 
 from . import mucal as m
-from .iterate import RunResult, iterate_to_flat, ln_binomial, ln_omega_estimate  # noqa: F401
+from .iterate import (RunResult, iterate_staged, iterate_to_flat, ln_binomial,  # noqa: F401
+                      ln_omega_estimate)
 
 
 def features(d: int, L: int, N: int, E: np.ndarray) -> np.ndarray:
@@ -121,6 +122,23 @@ def compare_plain_and_seeded(net, desc, sweeps: int, max_iter: int, relax_iters:
     plain = iterate_to_flat([desc], sweeps, max_iter, scheme=plain_scheme, cuda_stream=cuda_stream)[0]
     seeded = iterate_to_flat([desc], sweeps, max_iter, lnW0=[seedW], relax_iters=relax_iters,
                              relax_tol=relax_tol, scheme=seeded_scheme, cuda_stream=cuda_stream)[0]
+    return plain, seeded, seedW
+
+
+def compare_staged(net, desc, **kw):
+    """The two-stage iteration (iterate_staged) from lnW = 0 and from the
+    network's seed, same system, walker seeds and stage parameters; the seed
+    replaces stage 1 by a relaxation with the seeded weights held fixed.
+    Both are judged on the same target window: the one given, else the
+    range the plain run's stage 1 sampled.  Returns (plain, seeded, seed
+    weights)."""
+    d, L, N, W, lo, hi, seed = desc
+    e_lo, e_hi = (-d * N, 0) if (lo == 0 and hi == 0) else (lo, hi)
+    seedW = seed_weights(net, d, L, N, e_lo, e_hi)
+    plain = iterate_staged(desc, **kw)
+    if kw.get("target") is None:
+        kw = dict(kw, target=plain.span)
+    seeded = iterate_staged(desc, lnW0=seedW, **kw)
     return plain, seeded, seedW
 
 
