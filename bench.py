@@ -656,6 +656,26 @@ def aux_measure(stream, device):
     except Exception as exc:
         out["droplet_error"] = repr(exc)[:200]
     try:
+        # the same labelling on the 3D L=32 system: 8192 walkers, 87 MB per measurement
+        d3, L3, N3, W3, _, _, _ = workloads.LARGE_3D.systems[0]
+        V3 = L3 ** d3
+        with m.Mucal(workloads.LARGE_3D.systems, cuda_stream=stream.cuda_stream) as mc:
+            mc.set_weights(0, -1.2 * np.arange(d3 * N3 + 1, dtype=np.float64))
+            mc.run_iteration(5, 0)
+            ms = _events_ms(stream, mc.measure_droplets, 5)
+            bytes_ = W3 * (N3 * 2 + V3 // 8 + 4 + 4)
+            vd = mc.largest_droplets(0)
+            out["droplet_labelling_3d"] = {
+                "system": "3D L=32, N=3277, 8192 walkers",
+                "ms_per_measurement": ms, "walkers_per_s": W3 / (ms / 1e3),
+                "mean_V_D": float(vd.mean()),
+                "roofline": {"bound": "hbm", "alg_bytes": bytes_,
+                             "achieved": bytes_ / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": bytes_ / (ms / 1e3) / 1e9 / hbm,
+                             "peak_source": f"{kind} hbm_gbs"}}
+    except Exception as exc:
+        out["droplet_3d_error"] = repr(exc)[:200]
+    try:
         K = 8
         ladder = [(d, L, N, W, 0, 0, 10 ** 7 + k * W) for k in range(K)]
         with m.Mucal(ladder, cuda_stream=stream.cuda_stream) as mc:

@@ -193,7 +193,8 @@ class StagedResult:
 def iterate_staged(desc, lnW0=None, range_sweeps: int = 1000, sweeps: int = 4000,
                    discard: int = 1000, max_iter: int = 200, stable: int = 5, goal: float = 0.5,
                    target=None, scheme=m.MUCAL_SCHEME_SIMPLE | m.MUCAL_SCHEME_EXTRAPOLATE,
-                   relax_max: int = 10, cuda_stream=None, launch=None) -> StagedResult:
+                   relax_max: int = 10, cuda_stream=None, launch=None,
+                   seed_range_stage: bool = False) -> StagedResult:
     """The iteration of Sec. 2 in two stages for one system.
 
     Stage 1 (from lnW = 0): short iterations of `range_sweeps` with the simple
@@ -204,7 +205,9 @@ def iterate_staged(desc, lnW0=None, range_sweeps: int = 1000, sweeps: int = 4000
     range's edges as the edge continuation does (so that the walkers reach
     energies where the seed is too steep), until the sampled range has not
     changed for `stable` iterations (at most `relax_max`); random placements
-    are equilibrium states of lnW = 0 only.  Stage 2: iterations of `sweeps` measured sweeps, each after a
+    are equilibrium states of lnW = 0 only; with seed_range_stage the
+    relaxation is followed by stage 1 itself, started from the relaxed seed.
+    Stage 2: iterations of `sweeps` measured sweeps, each after a
     discarded run of `discard` sweeps (Sec. 2 asks for equilibrium runs with
     fixed weights: the discard lets the walkers follow the last update),
     updated with `scheme`, until the flatness over the target window (default:
@@ -252,6 +255,26 @@ def iterate_staged(desc, lnW0=None, range_sweeps: int = 1000, sweeps: int = 4000
                 if target is not None:
                     mc.set_target_window(0, *target)
                 flat.append(float("nan"))
+        if lnW0 is not None and seed_range_stage:
+            # stage 1 from the relaxed seed: the updates correct where the seed is wrong
+            mc.set_weights(0, mc.weights(0))
+            if target is not None:
+                mc.set_target_window(0, *target)
+            same = 0
+            k1 = 0
+            while same < stable and n1 + k1 < max_iter:
+                mc.run_iteration(range_sweeps, it_no)
+                it_no += 1
+                k1 += 1
+                total_sweeps += range_sweeps
+                H = mc.histogram(0)
+                vis = np.nonzero(H > 0)[0]
+                sp = (min(int(vis.min()), span[0]), max(int(vis.max()), span[1]))
+                same = same + 1 if sp == span else 0
+                span = sp
+                _, f = mc.update_weights(0, scheme)
+                flat.append(f)
+            n1 += k1
         lnW = mc.weights(0)
         # stage 2 starts with a fresh recursion memory (the stage-1 histograms
         # come from walkers far from equilibrium)

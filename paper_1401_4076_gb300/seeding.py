@@ -135,10 +135,11 @@ def compare_staged(net, desc, **kw):
     d, L, N, W, lo, hi, seed = desc
     e_lo, e_hi = (-d * N, 0) if (lo == 0 and hi == 0) else (lo, hi)
     seedW = seed_weights(net, d, L, N, e_lo, e_hi)
+    seed_range_stage = kw.pop("seed_range_stage", False)
     plain = iterate_staged(desc, **kw)
     if kw.get("target") is None:
         kw = dict(kw, target=plain.span)
-    seeded = iterate_staged(desc, lnW0=seedW, **kw)
+    seeded = iterate_staged(desc, lnW0=seedW, seed_range_stage=seed_range_stage, **kw)
     return plain, seeded, seedW
 
 
