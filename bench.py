@@ -882,6 +882,7 @@ def e2e_measure(wl, args, systems, stream, device, world):
     h2d = d2h = 0
     for it in range(args.steps):
         mc.run_iteration(sweeps, it)
+        allreduce_histograms(mc, len(systems), world, device)
         for s in range(len(systems)):
             H = mc.histogram(s)
             lnW, _ = mc.update_weights(s, m.MUCAL_SCHEME_RECURSIVE)
