@@ -65,12 +65,12 @@ TRAFFIC_MEASURED = {
     "2d-L64-N410-w4096": {"bytes": 33.89e6 + 954.13e6, "kernel_sha": "a476ebb38f79900c",
                           "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28}},
     # one full 200-sweep launch (profiles/walker_update_group_batched-27-systems-w16384.md)
-    "batched-27-systems-w16384": {"bytes": 705.094e9 + 300.382e9, "kernel_sha": "f802b33f069290ef",
+    "batched-27-systems-w16384": {"bytes": 705.264e9 + 300.448e9, "kernel_sha": "e79300d0c034eb7d",
                                   "launch": {"kernel": 1, "lanes_per_walker": 16,
                                              "bits_in_smem": 1, "thr_window": 0}},
     # a 5-sweep launch scaled by 40 to the workload's 200 sweeps (the list reads and
     # writes grow with the attempts; profiles/walker_update_group_3d-L32-N3277-w8192.md)
-    "3d-L32-N3277-w8192": {"bytes": 40 * (18.4516e9 + 7.0474e9), "kernel_sha": "f802b33f069290ef",
+    "3d-L32-N3277-w8192": {"bytes": 40 * (18.4670e9 + 7.0498e9), "kernel_sha": "e79300d0c034eb7d",
                            "launch": {"kernel": 1, "lanes_per_walker": 4,
                                       "bits_in_smem": 1, "thr_window": 0}},
 }
@@ -84,12 +84,12 @@ INSTR_MEASURED = {
     # depend on the sweep count beyond the per-block set-up)
     "batched-27-systems-w16384": {"warp_inst_per_attempt": 4.215209e9 / 72.3314e6,
                                   "thread_inst_per_attempt": 1.21995e11 / 72.3314e6,
-                                  "kernel_sha": "f802b33f069290ef", "any_sweeps": True,
+                                  "kernel_sha": "e79300d0c034eb7d", "any_sweeps": True,
                                   "launch": {"kernel": 1, "lanes_per_walker": 16,
                                              "bits_in_smem": 1, "thr_window": 0}},
-    "3d-L32-N3277-w8192": {"warp_inst_per_attempt": 2.895069e9 / 134.2259e6,
-                           "thread_inst_per_attempt": 8.64865e10 / 134.2259e6,
-                           "kernel_sha": "f802b33f069290ef", "any_sweeps": True,
+    "3d-L32-N3277-w8192": {"warp_inst_per_attempt": 2.974781e9 / 134.2259e6,
+                           "thread_inst_per_attempt": 8.90372e10 / 134.2259e6,
+                           "kernel_sha": "e79300d0c034eb7d", "any_sweeps": True,
                            "launch": {"kernel": 1, "lanes_per_walker": 4,
                                       "bits_in_smem": 1, "thr_window": 0}},
 }
