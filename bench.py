@@ -325,6 +325,9 @@ def main(argv=None):
     ap.add_argument("--thr-window", type=int, default=-1,
                     help="0: thresholds from global memory when the table does not fit in "
                          "shared memory, 1: per-walker row windows, 2: windows always")
+    ap.add_argument("--multi-commit", type=int, default=-1,
+                    help="1: several commits per round (group and field kernels, 4+ lanes), "
+                         "0: one commit per round")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run after the warm-up steps)")
     ap.add_argument("--tune-sweeps", type=int, default=20)
@@ -435,7 +438,7 @@ def main(argv=None):
 
 def _explicit_launch(args):
     return (args.kernel >= 0 or args.lanes or args.wpb or args.smem >= 0 or args.persistent >= 0
-            or args.thr_window >= 0)
+            or args.thr_window >= 0 or args.multi_commit >= 0)
 
 
 def measure(wl, args, systems, stream, device, world, flush, clocks_rank0=True, ceiling=True):
@@ -457,7 +460,8 @@ def measure(wl, args, systems, stream, device, world, flush, clocks_rank0=True, 
                    walkers_per_block=args.wpb or cur["walkers_per_block"],
                    bits_in_smem=args.smem if args.smem >= 0 else cur["bits_in_smem"],
                    persistent=args.persistent if args.persistent >= 0 else cur["persistent"],
-                   thr_window=args.thr_window if args.thr_window >= 0 else 1)
+                   thr_window=args.thr_window if args.thr_window >= 0 else 1,
+                   multi_commit=args.multi_commit if args.multi_commit >= 0 else 0)
         mc.set_launch(**cfg)
     if args.graph:
         mc.set_graph_mode(True)

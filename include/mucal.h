@@ -138,6 +138,16 @@ typedef struct mucal_launch_config {
                                   (mucal_get_launch_config then reports 0, as it does
                                   when the whole table is staged in shared memory).
                                   Ignored by THREAD.  Default 1 */
+    int32_t multi_commit;      /* GROUP and FIELD kernels with 4 or more lanes and the
+                                  thresholds in global or shared memory (no row
+                                  windows): 1 = one round of G proposals may commit
+                                  several accepted moves in order, each lane re-deciding
+                                  against the energy its predecessors left while its
+                                  move stays independent of theirs; 0 = one commit per
+                                  round.  Both give the same chain (Sec. 2's Metropolis
+                                  sequence, bit-identical).  With tunnelling events
+                                  recorded the one-commit rounds run.  Reported as 0
+                                  where it does not apply.  Default 0 */
 } mucal_launch_config;
 
 typedef struct mucal_system_info {

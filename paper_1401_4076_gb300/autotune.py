@@ -106,10 +106,13 @@ def autotune(systems, lnW=None, sweeps: int = 20, repeats: int = 3, cuda_stream=
 def with_threshold_modes(cands):
     """Every group and field candidate also with thr_window = 0 (thresholds
     read from global memory when the table does not fit in shared memory;
-    the default 1 keeps a window of rows per walker there instead)."""
+    the default 1 keeps a window of rows per walker there instead), and at
+    4 lanes or more with multi-commit rounds (which read the rows directly)."""
     out = []
     for c in cands:
         out.append(c)
         if c["kernel"] != m.MUCAL_KERNEL_THREAD:
             out.append(dict(c, thr_window=0))
+            if c["lanes_per_walker"] >= 4:
+                out.append(dict(c, thr_window=0, multi_commit=1))
     return out

@@ -418,6 +418,9 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     if (cfg.thr_window < 0 || cfg.thr_window > 2)
         return fail(c, MUCAL_ERR_INVALID_ARG, "thr_window must be 0, 1 or 2");
     sh.thr_window = cfg.kernel != MUCAL_KERNEL_THREAD ? cfg.thr_window : 0;
+    if (cfg.multi_commit < 0 || cfg.multi_commit > 1)
+        return fail(c, MUCAL_ERR_INVALID_ARG, "multi_commit must be 0 or 1");
+    sh.multi_commit = cfg.kernel != MUCAL_KERNEL_THREAD && cfg.lanes_per_walker >= 4 ? cfg.multi_commit : 0;
     if (sh.kernel == MUCAL_KERNEL_THREAD) {
         if (sh.lanes != 1)
             return fail(c, MUCAL_ERR_INVALID_ARG, "THREAD kernel needs lanes_per_walker = 1");
@@ -457,6 +460,7 @@ int apply_launch_config(Context *c, const mucal_launch_config &cfg)
     if (smem > (size_t)c->max_smem)
         return fail(c, MUCAL_ERR_INVALID_ARG, "launch needs %zu bytes of shared memory, limit %d",
                     smem, c->max_smem);
+    if (!sh.thr_in_smem && sh.thr_window) sh.multi_commit = 0;   // rounds read row windows
     sh.smem_bytes = smem;
     int rc = build_work(c, sh);
     if (rc != MUCAL_OK) return rc;
@@ -860,6 +864,7 @@ int mucal_get_launch_config(void *ctx, mucal_launch_config *cfg)
     cfg->persistent = c->shape.persistent;
     // with the whole table in shared memory the window setting has no effect
     cfg->thr_window = c->shape.thr_in_smem ? 0 : c->shape.thr_window;
+    cfg->multi_commit = c->shape.multi_commit;
     return MUCAL_OK;
 }
 
@@ -896,7 +901,7 @@ int mucal_run_iteration(void *ctx, int64_t sweeps, uint32_t iteration)
                           a.walkers_per_block == b.walkers_per_block &&
                           a.bits_in_smem == b.bits_in_smem && a.thr_in_smem == b.thr_in_smem &&
                           a.smem_bytes == b.smem_bytes && a.persistent == b.persistent &&
-                          a.thr_window == b.thr_window;
+                          a.thr_window == b.thr_window && a.multi_commit == b.multi_commit;
         if (!same) {
             int rc = capture_iteration(c, (uint64_t)sweeps, iteration, grid);
             if (rc != MUCAL_OK) return rc;

@@ -59,7 +59,8 @@ struct BlockWork {
 // shared or global memory and the thresholds in global memory, in shared
 // memory or in a per-walker row window, and the field kernel with the three
 // threshold modes.
-constexpr int kWalkerUpdateFns = 4 + 5 * 2 * 3 + 5 * 3;
+constexpr int kWalkerUpdateFns = 4 + 5 * 2 * 3 + 5 * 3 + 4 * 6;   // last: multi-commit
+                                                                // kernels (NULL where absent)
 
 struct LaunchShape {
     int kernel;             // MUCAL_KERNEL_THREAD / _GROUP / _FIELD
@@ -71,6 +72,8 @@ struct LaunchShape {
     int persistent;         // resident blocks pull work items from a counter
     int thr_window;         // (group and field kernels, when the table is not in shared
                             // memory) keep a window of rows per walker in shared memory
+    int multi_commit;       // (group and field kernels, 4+ lanes, no window, no tunnelling
+                            // bookkeeping) several commits per round
 };
 
 // Kernel launchers (walker_kernels.cu).  All are asynchronous on `stream`.

@@ -771,6 +771,232 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
 }
 
 // ---------------------------------------------------------------------------
+// Several commits per round (multi-commit rounds).  The rounds above commit
+// one accepted move per round and let every later lane evaluate again against
+// the new state.  A later lane whose two sites are not next to either site of
+// a committed move keeps its energy change; only its threshold changes with
+// the energy.  So after the first accepting lane f commits, the round goes on
+// through the later lanes in attempt order: each step takes the decisions of
+// the still-undecided lanes at the energy reached so far (every lane reads its
+// thresholds in the 4d + 1 rows around the round's energy once per round and
+// keeps the accept/reject outcomes as a bit mask, so a step reads no memory),
+// the first of them that accepts commits next, the undecided lanes
+// before it are rejected at that energy, and a lane stops the round (it and
+// every later lane evaluate again in the next round) when a committed move
+// touched one of its sites' neighbourhoods, moved one of its list slots, or
+// took the energy out of the loaded rows.  Every decision is the one the
+// serial chain takes, so the chain stays the one-thread chain.  Thresholds
+// from global memory or a table staged in shared memory (not the window);
+// no tunnelling bookkeeping.  A step issues more instructions than a
+// one-commit round (the neighbourhood test alone is 8d compares), so the
+// rounds pay off only where a round's loads are long: measured on GB300,
+// 3D L = 32 at 4 lanes with thresholds in L2 +2.4 %, the field kernel and
+// 16 lanes slower; the autotuner chooses per workload.
+// ---------------------------------------------------------------------------
+template <int D, typename IdxT, int G, int TM, typename View>
+__device__ __forceinline__ void chain_rounds_mc(const SysParams &p, int w, bool active, View v,
+                                                const uint32_t *thr, unsigned long long *hist,
+                                                uint64_t A, uint32_t iter)
+{
+    static_assert(TM == kThrGlobal || TM == kThrShared, "multi-commit rounds read rows directly");
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr unsigned GMASK = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    constexpr int O = 2 * D;             // rows bin - O .. bin + O are loaded per round
+    constexpr int NT = 2 * O + 1;
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (G - 1);
+    const int gbase = lane - j;
+    const unsigned gm = GMASK << gbase;
+    const unsigned me = 1u << lane;
+    IdxT *S = walker_S<IdxT>(p, w);
+    const uint32_t N = (uint32_t)p.N;
+    const uint32_t holes = (uint32_t)(p.V - p.N);
+    const uint64_t seed = p.seed_base + (uint64_t)w;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int nb = p.n_bins;
+    int bin = active ? p.E[w] - p.e_lo : 0;
+    const uint32_t thr_s = TM == kThrShared ? (uint32_t)__cvta_generic_to_shared(thr) : 0u;
+    const uint32_t rbase = thr_s + 8u * D;
+    const uint32_t w4 = 4u * (uint32_t)p.tstride;
+    uint32_t carry = 0;
+    uint32_t acc = 0;
+    constexpr bool PF = G <= 8;
+    uint32_t kn = 0, mn = 0, an = 0, bn = 0, r2n = 0;
+    uint32_t kq = 0, mq = 0, r2q = 0;
+    auto draw = [&](uint64_t t0) {
+        const uint64_t t = t0 + (uint64_t)j;
+        if (active && t < A) {
+            const uint4 r = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), iter, 0u), k0, k1);
+            if constexpr (PF) {
+                kq = __umulhi(r.x, N);
+                mq = __umulhi(r.y, holes);
+                r2q = r.z;
+                asm volatile("prefetch.L2 [%0];" ::"l"(S + kq));
+                asm volatile("prefetch.L2 [%0];" ::"l"(S + N + mq));
+            } else {
+                kn = __umulhi(r.x, N);
+                mn = __umulhi(r.y, holes);
+                r2n = r.z;
+                an = S[kn];
+                bn = S[N + mn];
+            }
+        }
+    };
+    auto read = [&](uint64_t t0) {
+        const uint64_t t = t0 + (uint64_t)j;
+        if (active && t < A) {
+            kn = kq;
+            mn = mq;
+            r2n = r2q;
+            an = S[kn];
+            bn = S[N + mn];
+        }
+    };
+    draw(0);
+    if constexpr (PF) {
+        read(0);
+        draw(G);
+    }
+    for (uint64_t t0 = 0; t0 < A; t0 += G) {
+        const uint64_t left = A - t0;
+        const int n_valid = left < (uint64_t)G ? (int)left : G;
+        const bool valid = active && (j < n_valid);
+        uint32_t k = kn, m = mn, a = an, b = bn;
+        const uint32_t r2p = (r2n == 0xFFFFFFFFu) ? r2n : r2n + 1u;
+        if constexpr (PF) {
+            read(t0 + G);
+            draw(t0 + 2 * G);
+        } else {
+            draw(t0 + G);
+        }
+        v.build(p, a, b, valid);
+        IdxT *pk = S + k;
+        IdxT *pm = S + N + m;
+        // the sites whose occupation this lane's energy change depends on:
+        // the neighbours of a and of b
+        uint32_t nbr[4 * D];
+        auto neighbourhood = [&]() {
+            uint32_t na[2 * D], nbb[2 * D];
+            neighbours<D>(p, valid ? a : 0u, na);
+            neighbours<D>(p, valid ? b : 0u, nbb);
+#pragma unroll
+            for (int i = 0; i < 2 * D; ++i) {
+                nbr[i] = na[i];
+                nbr[2 * D + i] = nbb[i];
+            }
+        };
+        neighbourhood();
+        v.load();
+        uint32_t radj = rbase + (uint32_t)v.adj4();
+        bool pend = valid;
+        int rs = gbase;
+        while (__any_sync(FULL, pend)) {
+            const int d4 = v.d4();
+            const int de4 = d4 + v.adj4();
+            // bit o: this lane's move is accepted at the energy bin + o - O
+            // (rows outside the table are never the walker's energy)
+            uint32_t accm = 0u;
+#pragma unroll
+            for (int o = 0; o < NT; ++o) {
+                const int rb = bin + o - O;
+                const bool in = rb >= 0 && rb < nb;
+                const uint32_t off = (uint32_t)(in ? rb : 0) * w4 + radj + (uint32_t)d4;
+                uint32_t t;
+                if constexpr (TM == kThrShared) {
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(off));
+                } else {
+                    t = __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(thr) + off));
+                }
+                accm |= (in && t >= r2p ? 1u : 0u) << o;
+            }
+            bool clean = pend;       // this lane's evaluation still holds
+            bool refresh = false;    // a commit moved one of this lane's list slots
+            int off = 0;             // energy change committed in this round
+            bool stepping = (__ballot_sync(FULL, pend) & gm) != 0u;
+            while (__any_sync(FULL, stepping)) {
+                // (a clean lane has |off| <= O)
+                const bool acc_now = stepping && pend && clean && ((accm >> ((off + O) & 31)) & 1u);
+                const unsigned bal = __ballot_sync(FULL, acc_now) & gm;
+                const unsigned unc = __ballot_sync(FULL, stepping && pend && !clean) & gm;
+                const unsigned fbit = bal & (0u - bal);
+                const unsigned ubit = unc & (0u - unc);
+                // an undecided lane before the next acceptance that cannot be
+                // decided here stops the round: it and all later lanes go again
+                const bool stop = stepping && unc != 0u && (bal == 0u || ubit < fbit);
+                // no acceptance among clean undecided lanes: all rejected here
+                const bool none = stepping && !stop && bal == 0u;
+                const bool step = stepping && !stop && !none;
+                if (stop) pend = pend && me >= ubit;
+                if (none) pend = false;
+                const int f = step ? (__ffs(bal) - 1) : lane;
+                if (step && lane == f) {
+                    v.commit();
+                    *pk = (IdxT)b;
+                    *pm = (IdxT)a;
+                    ++acc;
+                }
+                const int de_f = __shfl_sync(FULL, de4, f) >> 2;
+                uint32_t a_f, b_f, k_f, m_f;
+                shfl_pair<IdxT>(a, b, f, a_f, b_f);
+                shfl_pair<IdxT>(k, m, f, k_f, m_f);
+                if (step) {
+                    // a move ends the run at the energy before it
+                    const bool moved = de_f != 0;
+                    const uint32_t cnt = carry + (uint32_t)(f - rs);
+                    if (moved && j == 0 && cnt) atomicAdd(hist + bin + off, (unsigned long long)cnt);
+                    carry = moved ? 0u : carry;
+                    rs = moved ? f : rs;
+                    off += de_f;
+                    pend = pend && lane > f;
+                    // list slots the commit moved
+                    const bool fa = pend && k == k_f;
+                    const bool fb = pend && m == m_f;
+                    if (fa || fb) {
+                        a = fa ? b_f : a;
+                        b = fb ? a_f : b;
+                        refresh = true;
+                        clean = false;
+                    }
+                    // occupation the commit changed next to this lane's sites
+                    bool hit = false;
+#pragma unroll
+                    for (int i = 0; i < 4 * D; ++i) hit |= (nbr[i] == a_f) | (nbr[i] == b_f);
+                    clean = clean && !hit;
+                    // energies beyond the loaded rows are decided next round
+                    if (off > O || off < -O) clean = false;
+                    // the next batch's list reads see the moved slots
+                    an = (kn == k_f) ? b_f : an;
+                    bn = (mn == m_f) ? a_f : bn;
+                }
+                stepping = step;
+                __syncwarp(FULL);
+            }
+            bin += off;
+            if (refresh) {
+                v.build(p, a, b, true);
+                radj = rbase + (uint32_t)v.adj4();
+                pk = S + k;
+                pm = S + N + m;
+                neighbourhood();
+            }
+            v.load();
+        }
+        carry += (uint32_t)(gbase + n_valid - rs);
+        if (carry >= 0x40000000u) {
+            if (active && j == 0) atomicAdd(hist + bin, (unsigned long long)carry);
+            carry = 0;
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (active && j == 0) {
+        if (carry) atomicAdd(hist + bin, (unsigned long long)carry);
+        p.E[w] = bin + p.e_lo;
+        p.accepts[w] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One thread, one walker: A attempts in order, software-pipelined.  The
 // random numbers and list reads of the next PF attempts are in flight in a
 // register ring while the current attempt is evaluated (the slot just
@@ -972,7 +1198,7 @@ __device__ __forceinline__ void window_addrs(const SysParams &p, uint32_t after,
     mbar_s = base + (uint32_t)wpb * rb + (uint32_t)lw * 8u;
 }
 
-template <int G, bool SB, int TM, bool TUN>
+template <int G, bool SB, int TM, bool TUN, bool MC = false>
 __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
                                            uint64_t sweeps, uint32_t iter)
 {
@@ -997,6 +1223,16 @@ __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &
     // wait for the next batch's list reads; the batch at 16 lanes 8.56e9 ->
     // 8.13e9, where the extra shuffle per round costs more)
     constexpr bool kSlot = (G == 4 || G == 8);
+    if constexpr (MC) {
+        if (p.d == 2) {
+            if (p.idx16) chain_rounds_mc<2, uint16_t, G, TM>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter);
+            else chain_rounds_mc<2, uint32_t, G, TM>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter);
+        } else {
+            if (p.idx16) chain_rounds_mc<3, uint16_t, G, TM>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter);
+            else chain_rounds_mc<3, uint32_t, G, TM>(p, w, active, BitView<3, SB>(bits), thr, hist, A, iter);
+        }
+        return;
+    }
     if (p.d == 2) {
         if (p.idx16) chain_rounds<2, uint16_t, G, TM, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);
         else chain_rounds<2, uint32_t, G, TM, TUN, kSlot>(p, w, active, BitView<2, SB>(bits), thr, hist, A, iter, ring_s, mbar_s);
@@ -1006,7 +1242,7 @@ __device__ __forceinline__ void group_body(const SysParams &p, const BlockWork &
     }
 }
 
-template <int G, bool SB, int TM, bool TUN, bool PERSIST>
+template <int G, bool SB, int TM, bool TUN, bool PERSIST, bool MC = false>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
                     uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
@@ -1020,7 +1256,7 @@ walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restri
         const BlockWork wk = work[blockIdx.x];
         const SysParams &p = sys[wk.sys];
         const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, kTS);
-        group_body<G, SB, TM, TUN>(p, wk, smem, sweeps, iter);
+        group_body<G, SB, TM, TUN, MC>(p, wk, smem, sweeps, iter);
         block_finish(bs, SB ? 1 : 0);
     } else {
         __shared__ int s_item;
@@ -1028,7 +1264,7 @@ walker_update_group(const SysParams *__restrict__ sys, const BlockWork *__restri
             const BlockWork wk = work[item];
             const SysParams &p = sys[wk.sys];
             const BlockSetup bs = block_setup(p, wk, smem, SB ? 1 : 0, kTS);
-            group_body<G, SB, TM, TUN>(p, wk, smem, sweeps, iter);
+            group_body<G, SB, TM, TUN, MC>(p, wk, smem, sweeps, iter);
             block_finish(bs, SB ? 1 : 0);
             item = next_work_item(next_item, &s_item);
         }
@@ -1086,7 +1322,7 @@ __device__ __forceinline__ void field_finish(const SysParams &p, const BlockWork
     block_copy_words(p.bits + (size_t)wk.walker0 * words, fw, total);
 }
 
-template <int D, typename IdxT, int G, int TM, bool TUN>
+template <int D, typename IdxT, int G, int TM, bool TUN, bool MC = false>
 __device__ __forceinline__ void field_item(const SysParams &p, const BlockWork &wk, uint32_t *smem,
                                            uint64_t sweeps, uint32_t iter)
 {
@@ -1107,26 +1343,31 @@ __device__ __forceinline__ void field_item(const SysParams &p, const BlockWork &
                                (uint32_t)((size_t)wpb * field_bytes(p));
         window_addrs(p, after, wpb, active ? lw : 0, ring_s, mbar_s);
     }
-    // site compare for moved slots (measured on GB300: the faster one here for every G)
-    chain_rounds<D, IdxT, G, TM, TUN, false>(p, w, active, FieldView<D>(fbase), thr, hist,
-                                             sweeps * (uint64_t)p.N, iter, ring_s, mbar_s);
+    if constexpr (MC) {
+        chain_rounds_mc<D, IdxT, G, TM>(p, w, active, FieldView<D>(fbase), thr, hist,
+                                        sweeps * (uint64_t)p.N, iter);
+    } else {
+        // site compare for moved slots (measured on GB300: the faster one here for every G)
+        chain_rounds<D, IdxT, G, TM, TUN, false>(p, w, active, FieldView<D>(fbase), thr, hist,
+                                                 sweeps * (uint64_t)p.N, iter, ring_s, mbar_s);
+    }
     field_finish<IdxT>(p, wk, fw);
 }
 
-template <int G, int TM, bool TUN>
+template <int G, int TM, bool TUN, bool MC = false>
 __device__ __forceinline__ void field_body(const SysParams &p, const BlockWork &wk, uint32_t *smem,
                                            uint64_t sweeps, uint32_t iter)
 {
     if (p.d == 2) {
-        if (p.idx16) field_item<2, uint16_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
-        else field_item<2, uint32_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
+        if (p.idx16) field_item<2, uint16_t, G, TM, TUN, MC>(p, wk, smem, sweeps, iter);
+        else field_item<2, uint32_t, G, TM, TUN, MC>(p, wk, smem, sweeps, iter);
     } else {
-        if (p.idx16) field_item<3, uint16_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
-        else field_item<3, uint32_t, G, TM, TUN>(p, wk, smem, sweeps, iter);
+        if (p.idx16) field_item<3, uint16_t, G, TM, TUN, MC>(p, wk, smem, sweeps, iter);
+        else field_item<3, uint32_t, G, TM, TUN, MC>(p, wk, smem, sweeps, iter);
     }
 }
 
-template <int G, int TM, bool TUN, bool PERSIST>
+template <int G, int TM, bool TUN, bool PERSIST, bool MC = false>
 __global__ void __launch_bounds__(kGroupMaxThreads, 1)
 walker_update_field(const SysParams *__restrict__ sys, const BlockWork *__restrict__ work,
                     uint64_t sweeps, uint32_t iter, int n_items, int *next_item)
@@ -1137,12 +1378,12 @@ walker_update_field(const SysParams *__restrict__ sys, const BlockWork *__restri
         (void)n_items;
         (void)next_item;
         const BlockWork wk = work[blockIdx.x];
-        field_body<G, TM, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
+        field_body<G, TM, TUN, MC>(sys[wk.sys], wk, smem, sweeps, iter);
     } else {
         __shared__ int s_item;
         for (int item = blockIdx.x; item < n_items;) {
             const BlockWork wk = work[item];
-            field_body<G, TM, TUN>(sys[wk.sys], wk, smem, sweeps, iter);
+            field_body<G, TM, TUN, MC>(sys[wk.sys], wk, smem, sweeps, iter);
             item = next_work_item(next_item, &s_item);
         }
     }
@@ -1154,9 +1395,26 @@ inline int thr_mode(const LaunchShape &sh)
     return sh.thr_in_smem ? kThrShared : (sh.thr_window ? kThrWindow : kThrGlobal);
 }
 
+// Multi-commit rounds apply to the group and field kernels at 4 to 32 lanes
+// with the thresholds in global memory or a staged table, without the
+// tunnelling bookkeeping; other shapes run the one-commit rounds.
+template <int G, bool TUN>
+constexpr bool kMcFlavour = !TUN && G >= 4;
+
+inline bool use_mc(const LaunchShape &sh)
+{
+    return sh.multi_commit && thr_mode(sh) != kThrWindow;
+}
+
 template <int G, bool TUN, bool PE>
 const void *field_fn(const LaunchShape &sh)
 {
+    if constexpr (kMcFlavour<G, TUN>) {
+        if (use_mc(sh))
+            return thr_mode(sh) == kThrShared
+                       ? (const void *)walker_update_field<G, kThrShared, TUN, PE, true>
+                       : (const void *)walker_update_field<G, kThrGlobal, TUN, PE, true>;
+    }
     switch (thr_mode(sh)) {
     case kThrShared: return (const void *)walker_update_field<G, kThrShared, TUN, PE>;
     case kThrWindow: return (const void *)walker_update_field<G, kThrWindow, TUN, PE>;
@@ -1167,6 +1425,12 @@ const void *field_fn(const LaunchShape &sh)
 template <int G, bool SB, bool TUN, bool PE>
 const void *group_fn_sb(const LaunchShape &sh)
 {
+    if constexpr (kMcFlavour<G, TUN>) {
+        if (use_mc(sh))
+            return thr_mode(sh) == kThrShared
+                       ? (const void *)walker_update_group<G, SB, kThrShared, TUN, PE, true>
+                       : (const void *)walker_update_group<G, SB, kThrGlobal, TUN, PE, true>;
+    }
     switch (thr_mode(sh)) {
     case kThrShared: return (const void *)walker_update_group<G, SB, kThrShared, TUN, PE>;
     case kThrWindow: return (const void *)walker_update_group<G, SB, kThrWindow, TUN, PE>;
@@ -1245,6 +1509,23 @@ void walker_update_fns(const void *(&fns)[kWalkerUpdateFns])
     MUCAL_FIELD_FNS(16)
     MUCAL_FIELD_FNS(32)
 #undef MUCAL_FIELD_FNS
+    // multi-commit rounds (flavours without tunnelling bookkeeping only)
+#define MUCAL_MC_FNS(G)                                                                        \
+    if constexpr (kMcFlavour<G, TUN>) {                                                        \
+        fns[i++] = (const void *)walker_update_group<G, true, kThrShared, TUN, PE, true>;     \
+        fns[i++] = (const void *)walker_update_group<G, true, kThrGlobal, TUN, PE, true>;     \
+        fns[i++] = (const void *)walker_update_group<G, false, kThrShared, TUN, PE, true>;    \
+        fns[i++] = (const void *)walker_update_group<G, false, kThrGlobal, TUN, PE, true>;    \
+        fns[i++] = (const void *)walker_update_field<G, kThrShared, TUN, PE, true>;           \
+        fns[i++] = (const void *)walker_update_field<G, kThrGlobal, TUN, PE, true>;           \
+    } else {                                                                                   \
+        for (int q = 0; q < 6; ++q) fns[i++] = nullptr;                                        \
+    }
+    MUCAL_MC_FNS(4)
+    MUCAL_MC_FNS(8)
+    MUCAL_MC_FNS(16)
+    MUCAL_MC_FNS(32)
+#undef MUCAL_MC_FNS
 }
 
 }  // namespace

@@ -232,6 +232,7 @@ cudaError_t walker_update_max_smem(int *bytes)
     // thread kernel's tunnelling words)
     size_t max_static = 0;
     for (const void *fn : fns) {
+        if (!fn) continue;   // flavour without a multi-commit kernel
         cudaFuncAttributes attr{};
         e = cudaFuncGetAttributes(&attr, fn);
         if (e != cudaSuccess) return e;
@@ -239,6 +240,7 @@ cudaError_t walker_update_max_smem(int *bytes)
     }
     *bytes -= (int)max_static;
     for (const void *fn : fns) {
+        if (!fn) continue;
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, *bytes);
         if (e != cudaSuccess) return e;
     }

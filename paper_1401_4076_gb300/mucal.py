@@ -63,7 +63,8 @@ class mucal_system_desc(ctypes.Structure):
 class mucal_launch_config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
                 ("walkers_per_block", ctypes.c_int32), ("bits_in_smem", ctypes.c_int32),
-                ("persistent", ctypes.c_int32), ("thr_window", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("thr_window", ctypes.c_int32),
+                ("multi_commit", ctypes.c_int32)]
 
 
 class mucal_system_info(ctypes.Structure):
@@ -219,9 +220,10 @@ def mucal_get_thresholds(ctx, sys, n_bins, width):
 
 
 def mucal_set_launch_config(ctx, kernel=MUCAL_KERNEL_THREAD, lanes_per_walker=1,
-                            walkers_per_block=32, bits_in_smem=1, persistent=0, thr_window=1):
+                            walkers_per_block=32, bits_in_smem=1, persistent=0, thr_window=1,
+                            multi_commit=0):
     cfg = mucal_launch_config(kernel, lanes_per_walker, walkers_per_block, bits_in_smem,
-                              int(persistent), int(thr_window))
+                              int(persistent), int(thr_window), int(multi_commit))
     _check(load_library().mucal_set_launch_config(ctx, ctypes.byref(cfg)), ctx)
 
 
@@ -230,7 +232,8 @@ def mucal_get_launch_config(ctx):
     _check(load_library().mucal_get_launch_config(ctx, ctypes.byref(cfg)), ctx)
     return {"kernel": cfg.kernel, "lanes_per_walker": cfg.lanes_per_walker,
             "walkers_per_block": cfg.walkers_per_block, "bits_in_smem": cfg.bits_in_smem,
-            "persistent": cfg.persistent, "thr_window": cfg.thr_window}
+            "persistent": cfg.persistent, "thr_window": cfg.thr_window,
+            "multi_commit": cfg.multi_commit}
 
 
 def mucal_set_graph_mode(ctx, enable):

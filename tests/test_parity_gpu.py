@@ -542,3 +542,170 @@ def test_window_setting_falls_back_when_it_does_not_fit():
         mc.set_launch(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=4, walkers_per_block=32,
                       bits_in_smem=1, thr_window=1)
         assert mc.launch()["thr_window"] == 1
+
+
+# ------------------------------------------------- multi-commit rounds ------
+# One round may commit several accepted moves in attempt order (a later lane
+# re-decides at the energy its predecessors reached while its own energy
+# change still holds).  The chain must stay the one-thread chain: every lane
+# count that has the rounds, both views, bitsets in shared or global memory,
+# persistent launches, thresholds staged in shared memory (small tables) and
+# read from global memory (the full-size launches below), and weights that
+# make nearly every move accepted (lnW = 0: many commits per round) as well as
+# sloped ones (long runs, energies moving several rows in one round).
+
+MC_LAUNCHES = [
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=4, walkers_per_block=24, bits_in_smem=0),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=16, walkers_per_block=2, bits_in_smem=1,
+         persistent=1),
+    dict(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=32, walkers_per_block=3, bits_in_smem=0),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=4, walkers_per_block=8, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=12, bits_in_smem=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=16, walkers_per_block=2, bits_in_smem=1,
+         persistent=1),
+    dict(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=32, walkers_per_block=1, bits_in_smem=1),
+]
+
+
+@pytest.mark.parametrize("launch", MC_LAUNCHES, ids=_lid)
+@pytest.mark.parametrize("desc,sweeps,slope,scale", [
+    ((2, 16, 32, 40, 0, 0, 0), 200, None, 0.0),     # lnW = 0: every move with dE <= 0 taken
+    ((2, 24, 80, 37, 0, 0, 8), 40, -1.5, 0.3),      # weights favour low E: runs down
+    ((3, 10, 150, 29, 0, 0, 12), 15, 0.8, 0.3),     # 3D, weights favour high E
+    ((3, 6, 170, 21, 0, 0, 5), 30, 0.0, 1.0),       # 3D dense (rho 0.79): neighbourhoods overlap
+    ((2, 40, 300, 19, -450, -30, 16), 20, 0.3, 0.3),  # user window, walkers near its top
+    ((2, 8, 3, 9, 0, 0, 3), 7, 0.0, 0.5),           # 21 attempts per walker: ragged batches
+    ((2, 3, 1, 5, 0, 0, 77), 200, 0.0, 0.5),        # one particle on 3 x 3
+    ((3, 5, 124, 4, 0, 0, 9), 20, 0.0, 0.5),        # one hole
+])
+def test_multi_commit_bit_exact(desc, sweeps, slope, scale, launch):
+    d, L, N, W, lo, hi, seed = desc
+    e_lo, e_hi = _window(d, N, lo, hi)
+    nb = e_hi - e_lo + 1
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    if lo or hi:
+        if not ((E >= e_lo) & (E <= e_hi)).all():
+            pytest.skip("a random placement lies outside the user window")
+    if slope is None:
+        lnW = np.zeros(nb)
+    else:
+        lnW = workloads.random_log_weights(nb, 7, scale=scale) + slope * np.arange(nb)
+        lnW -= lnW.max()
+    with m.Mucal([desc], per_walker_hist=True) as mc:
+        try:
+            mc.set_launch(**dict(launch, multi_commit=1))
+        except m.MucalError:
+            # the fields of the block's walkers do not fit: one walker per block
+            mc.set_launch(**dict(launch, lanes_per_walker=32, walkers_per_block=1,
+                                 multi_commit=1))
+        assert mc.launch()["multi_commit"] == 1
+        mc.set_weights(0, lnW)
+        T = chain.thresholds(d, e_lo, e_hi, lnW)
+        for it in range(3):
+            mc.run_iteration(sweeps, it)
+            hist, _ = chain.run_walkers(d, L, N, seed, it, sweeps * N, e_lo, e_hi, T, S, occ, E)
+            H, per = mc.histogram(0, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+            np.testing.assert_array_equal(H, hist.sum(axis=0))
+        acc = mc.stats(0)
+        for w in range(W):
+            _assert_walker_equal(mc, 0, w, S[w], occ[w], E[w])
+        assert acc["attempts"] == W * sweeps * N
+
+
+def test_multi_commit_uint32_lists_bit_exact():
+    """V = 66049 > 65536 sites: 32-bit list entries (two shuffles per pair)."""
+    desc = (2, 257, 300, 3, 0, 0, 5)
+    d, L, N, W, lo, hi, seed = desc
+    nb = d * N + 1
+    lnW = workloads.random_log_weights(nb, 2, scale=0.3)
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    with m.Mucal([desc], per_walker_hist=True) as mc:
+        mc.set_launch(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=4,
+                      bits_in_smem=0, multi_commit=1)
+        mc.set_weights(0, lnW)
+        T = chain.thresholds(d, -d * N, 0, lnW)
+        for it in range(2):
+            mc.run_iteration(10, it)
+            hist, _ = chain.run_walkers(d, L, N, seed, it, 10 * N, -d * N, 0, T, S, occ, E)
+            _, per = mc.histogram(0, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+        for w in range(W):
+            _assert_walker_equal(mc, 0, w, S[w], occ[w], E[w])
+
+
+def test_multi_commit_reported_only_where_it_applies():
+    with m.Mucal([(2, 16, 32, 64, 0, 0, 0)]) as mc:
+        mc.set_launch(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=2, walkers_per_block=16,
+                      bits_in_smem=1, multi_commit=1)
+        assert mc.launch()["multi_commit"] == 0          # 2 lanes: one-commit rounds
+        mc.set_launch(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_block=32,
+                      bits_in_smem=1, multi_commit=1)
+        assert mc.launch()["multi_commit"] == 0
+        mc.set_launch(kernel=m.MUCAL_KERNEL_GROUP, lanes_per_walker=8, walkers_per_block=8,
+                      bits_in_smem=1, thr_window=2, multi_commit=1)
+        assert mc.launch()["multi_commit"] == 0          # row windows: one-commit rounds
+        assert mc.launch()["thr_window"] == 2
+        mc.set_launch(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=8,
+                      bits_in_smem=1, multi_commit=1)
+        assert mc.launch()["multi_commit"] == 1
+        with pytest.raises(m.MucalError):
+            mc.set_launch(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=8,
+                          bits_in_smem=1, multi_commit=2)
+
+
+def test_multi_commit_tunnel_flavour_runs_one_commit_rounds():
+    """With tunnelling events recorded the one-commit rounds run; the chain and
+    the events are the oracle's."""
+    d, L, N, W, seed = 2, 20, 60, 24, 31
+    nb = d * N + 1
+    lnW = workloads.random_log_weights(nb, 3, 0.6)
+    S, occ, E = _oracle_states(d, L, N, W, seed)
+    T = chain.thresholds(d, -d * N, 0, lnW)
+    tstate = np.zeros(W, np.uint8)
+    tcount = np.zeros(W, np.int64)
+    with m.Mucal([(d, L, N, W, 0, 0, seed)], per_walker_hist=True) as mc:
+        mc.set_launch(kernel=m.MUCAL_KERNEL_FIELD, lanes_per_walker=8, walkers_per_block=8,
+                      bits_in_smem=1, multi_commit=1)
+        mc.set_weights(0, lnW)
+        mc.set_tunnel_window(0, -60, -20)
+        for it in range(2):
+            mc.run_iteration(50, it)
+            hist = chain.run_walkers_tunnel(d, L, N, seed, it, 50 * N, -d * N, 0, T, S, occ, E,
+                                            -60, -20, tstate, tcount)
+            _, per = mc.histogram(0, per_walker=True)
+            np.testing.assert_array_equal(per, hist)
+        total, per_w, st = mc.tunnel_counts(0)
+        np.testing.assert_array_equal(per_w.astype(np.int64), tcount)
+
+
+@pytest.mark.parametrize("wl_name", ["3d-L32-N3277-w8192", "batched-27-systems-w16384"])
+def test_multi_commit_full_size_global_thresholds(wl_name):
+    """The benchmark shapes with multi-commit rounds: thresholds read from
+    global memory (the tables do not fit beside the bitsets), sampled walkers
+    of every system against the oracle, sum H counts every attempt."""
+    if wl_name.startswith("batched"):
+        wl = workloads.batched_uneven()
+    else:
+        wl = workloads.LARGE_3D
+    launch = dict(BENCH_SHAPES[wl_name], thr_window=0, multi_commit=1)
+    lnWs = [workloads.random_log_weights(s[0] * s[2] + 1, 300 + i, scale=0.05)
+            for i, s in enumerate(wl.systems)]
+    sweeps, it = 5, 3
+    with m.Mucal(wl.systems) as mc:
+        mc.set_launch(**launch)
+        cfg = mc.launch()
+        assert cfg["multi_commit"] == 1 and cfg["thr_window"] == 0
+        for i, lnW in enumerate(lnWs):
+            mc.set_weights(i, lnW)
+        mc.run_iteration(sweeps, it)
+        for i, (d, L, N, W, lo, hi, seed) in enumerate(wl.systems):
+            H = mc.histogram(i)
+            assert H.sum() == W * sweeps * N
+            pick = sorted({0, W // 3, W - 1})
+            S, occ, E = _oracle_states(d, L, N, W, seed, pick)
+            T = chain.thresholds(d, -d * N, 0, lnWs[i])
+            chain.run_walkers(d, L, N, seed, it, sweeps * N, -d * N, 0, T, S, occ, E, walkers=pick)
+            for q, w in enumerate(pick):
+                _assert_walker_equal(mc, i, w, S[q], occ[q], E[q])
