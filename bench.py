@@ -62,17 +62,26 @@ def alg_ops_per_attempt(d: int) -> int:
 # the shape here: when every block is resident at once (147 blocks of 28
 # walkers on 152 SMs) the persistent launch runs the same blocks.
 TRAFFIC_MEASURED = {
-    "2d-L64-N410-w4096": {"bytes": 33.89e6 + 954.13e6, "kernel_sha": "a476ebb38f79900c",
-                          "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28}},
+    # one full 1000-sweep launch (profiles/walker_update_field_2d-L64-N410-w4096.md)
+    "2d-L64-N410-w4096": {"bytes": 33.984e6 + 901.007e6, "kernel_sha": "87f4d1b77f8f1ef5",
+                          "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28,
+                                     "thr_window": 0, "multi_commit": 0}},
     # one full 200-sweep launch (profiles/walker_update_group_batched-27-systems-w16384.md)
-    "batched-27-systems-w16384": {"bytes": 705.264e9 + 300.448e9, "kernel_sha": "e79300d0c034eb7d",
+    "batched-27-systems-w16384": {"bytes": 704.923e9 + 300.214e9, "kernel_sha": "87f4d1b77f8f1ef5",
                                   "launch": {"kernel": 1, "lanes_per_walker": 16,
-                                             "bits_in_smem": 1, "thr_window": 0}},
+                                             "bits_in_smem": 1, "thr_window": 0,
+                                             "multi_commit": 0}},
     # a 5-sweep launch scaled by 40 to the workload's 200 sweeps (the list reads and
-    # writes grow with the attempts; profiles/walker_update_group_3d-L32-N3277-w8192.md)
-    "3d-L32-N3277-w8192": {"bytes": 40 * (18.4670e9 + 7.0498e9), "kernel_sha": "e79300d0c034eb7d",
-                           "launch": {"kernel": 1, "lanes_per_walker": 4,
-                                      "bits_in_smem": 1, "thr_window": 0}},
+    # writes grow with the attempts; profiles/walker_update_group_3d-L32-N3277-w8192.md),
+    # with multi-commit rounds and with one commit per round
+    "3d-L32-N3277-w8192": [
+        {"bytes": 40 * (18.6217e9 + 7.0699e9), "kernel_sha": "87f4d1b77f8f1ef5",
+         "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
+                    "multi_commit": 1}},
+        {"bytes": 40 * (18.4584e9 + 7.0481e9), "kernel_sha": "87f4d1b77f8f1ef5",
+         "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
+                    "multi_commit": 0}},
+    ],
 }
 
 # Executed instructions per attempted move of the walker-update kernel, from
@@ -80,18 +89,32 @@ TRAFFIC_MEASURED = {
 # and smsp__thread_inst_executed.sum, divided by the launch's attempts), under
 # the same validity rule as the traffic record: launch shape and kernel source.
 INSTR_MEASURED = {
+    # the full 1000-sweep launch of the traffic record
+    "2d-L64-N410-w4096": {"warp_inst_per_attempt": 4.0031106e10 / 1.67936e9,
+                          "thread_inst_per_attempt": 1.0419877e12 / 1.67936e9,
+                          "kernel_sha": "87f4d1b77f8f1ef5",
+                          "launch": {"kernel": 2, "lanes_per_walker": 8, "thr_window": 0,
+                                     "multi_commit": 0}},
     # 2-sweep launch, same shape as the traffic record (instructions per attempt do not
     # depend on the sweep count beyond the per-block set-up)
     "batched-27-systems-w16384": {"warp_inst_per_attempt": 4.215209e9 / 72.3314e6,
                                   "thread_inst_per_attempt": 1.21995e11 / 72.3314e6,
-                                  "kernel_sha": "e79300d0c034eb7d", "any_sweeps": True,
+                                  "kernel_sha": "87f4d1b77f8f1ef5", "any_sweeps": True,
                                   "launch": {"kernel": 1, "lanes_per_walker": 16,
-                                             "bits_in_smem": 1, "thr_window": 0}},
-    "3d-L32-N3277-w8192": {"warp_inst_per_attempt": 2.974781e9 / 134.2259e6,
-                           "thread_inst_per_attempt": 8.90372e10 / 134.2259e6,
-                           "kernel_sha": "e79300d0c034eb7d", "any_sweeps": True,
-                           "launch": {"kernel": 1, "lanes_per_walker": 4,
-                                      "bits_in_smem": 1, "thr_window": 0}},
+                                             "bits_in_smem": 1, "thr_window": 0,
+                                             "multi_commit": 0}},
+    "3d-L32-N3277-w8192": [
+        {"warp_inst_per_attempt": 4.743839e9 / 134.2259e6,
+         "thread_inst_per_attempt": 1.414610e11 / 134.2259e6,
+         "kernel_sha": "87f4d1b77f8f1ef5", "any_sweeps": True,
+         "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
+                    "multi_commit": 1}},
+        {"warp_inst_per_attempt": 2.974781e9 / 134.2259e6,
+         "thread_inst_per_attempt": 8.90372e10 / 134.2259e6,
+         "kernel_sha": "87f4d1b77f8f1ef5", "any_sweeps": True,
+         "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
+                    "multi_commit": 0}},
+    ],
 }
 
 KERNEL_NAMES = {0: "walker_update_thread", 1: "walker_update_group", 2: "walker_update_field"}
@@ -105,15 +128,21 @@ def _kernel_sha() -> str:
 
 
 def _record_for(table: dict, workload: str, sweeps_default: bool, launch: dict):
-    rec = table.get(workload)
-    if rec is None or not (sweeps_default or rec.get("any_sweeps")):
+    recs = table.get(workload)
+    if recs is None:
         return None
-    # the launch keys a record names must match (records name the kernel, the
-    # lanes per walker, the bitset staging and the threshold mode; the split
-    # into blocks does not change the per-attempt work or access pattern)
-    if any(launch.get(k) != v for k, v in rec["launch"].items()):
-        return None
-    return rec if _kernel_sha() == rec["kernel_sha"] else None
+    for rec in (recs if isinstance(recs, list) else [recs]):
+        if not (sweeps_default or rec.get("any_sweeps")):
+            continue
+        # the launch keys a record names must match (records name the kernel,
+        # the lanes per walker, the bitset staging, the threshold mode and the
+        # rounds; the split into blocks does not change the per-attempt work
+        # or access pattern)
+        if any(launch.get(k) != v for k, v in rec["launch"].items()):
+            continue
+        if _kernel_sha() == rec["kernel_sha"]:
+            return rec
+    return None
 
 
 def _measured_traffic(workload: str, sweeps_default: bool, launch: dict):

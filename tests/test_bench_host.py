@@ -60,3 +60,19 @@ def test_instruction_record_follows_shape_and_source():
     assert bench._record_for(rec, "x", False, {"kernel": 1, "lanes_per_walker": 4}) is None
     rec["x"]["kernel_sha"] = "0" * 16
     assert bench._record_for(rec, "x", True, {"kernel": 1, "lanes_per_walker": 4}) is None
+
+
+def test_records_per_round_mode():
+    """A workload may hold one record per launch variant (the 3D workload:
+    multi-commit and one-commit rounds); the launch picks its own."""
+    name = "3d-L32-N3277-w8192"
+    recs = bench.TRAFFIC_MEASURED[name]
+    assert isinstance(recs, list) and len(recs) == 2
+    base = dict(kernel=1, lanes_per_walker=4, walkers_per_block=56, bits_in_smem=1,
+                persistent=1, thr_window=0)
+    current = recs[0]["kernel_sha"] == bench._kernel_sha()
+    for mc, rec in ((1, recs[0]), (0, recs[1])):
+        assert rec["launch"]["multi_commit"] == mc
+        got = bench._measured_traffic(name, True, dict(base, multi_commit=mc))
+        assert got == (rec["bytes"] if current else None)
+    assert bench._measured_traffic(name, True, dict(base, multi_commit=1, thr_window=1)) is None
