@@ -197,6 +197,37 @@ def ladder(net, rungs, frac: float, walkers: int, sweeps: int, max_iter: int, X,
     return net, records
 
 
+def full_range_trials(trainings: int, seeds: int, train_steps: int, log):
+    """The plain start against the learned seed on 2D L=64, N=410, 4096
+    walkers over its whole sampled range (two-stage iteration, flatness
+    over [-778, 0]), with the network trained `trainings` times on the same
+    rows: the training sums gradients with float atomics, so each training
+    gives a slightly different network.  The plain runs are the same for
+    every training (the chain is deterministic) and run once per seed."""
+    from .iterate import iterate_staged
+    scheme = m.MUCAL_SCHEME_SIMPLE | m.MUCAL_SCHEME_EXTRAPOLATE
+    small = small_training_systems(1.0)
+    res = iterate_to_flat(small, sweeps=100, max_iter=300, final_sweeps=1000, scheme=scheme)
+    X, t = training_set([r for r in res if r.converged])
+    d, L, N, W = 2, 64, 410, 4096
+    walker_seeds = [7 * 10 ** 6 + k * W for k in range(seeds)]
+    for k, s in enumerate(walker_seeds):
+        r = iterate_staged((d, L, N, W, 0, 0, s), max_iter=150, target=(-778, 0))
+        log({"start": "plain", "seed": k, "iterations": r.iterations,
+             "wall_s": round(r.wall_s, 2), "converged": r.converged})
+    for rep in range(trainings):
+        t0 = time.perf_counter()
+        net, loss = train(X, t, steps=train_steps, lr=1e-3)
+        tt = time.perf_counter() - t0
+        seedW = seed_weights(net, d, L, N, -d * N, 0)
+        for k, s in enumerate(walker_seeds):
+            r = iterate_staged((d, L, N, W, 0, 0, s), lnW0=seedW, max_iter=150, target=(-778, 0))
+            log({"start": "learned", "training": rep, "train_s": round(tt, 2), "loss": loss,
+                 "seed": k, "iterations": r.iterations, "wall_s": round(r.wall_s, 2),
+                 "converged": r.converged})
+        net.close()
+
+
 def main(argv=None):
     """Train on small systems, then compare plain and seeded convergence on
     larger ones; prints one JSON line per target system."""
@@ -215,6 +246,13 @@ def main(argv=None):
                     help="rungs d:L:rho separated by commas, climbed after training")
     ap.add_argument("--ladder-walkers", type=int, default=4096)
     ap.add_argument("--ladder-sweeps", type=int, default=50)
+    ap.add_argument("--full-range-trainings", type=int, default=0,
+                    help="train the network this many times on small lattices run over their "
+                         "whole ranges, and compare the two-stage iteration from lnW = 0 and "
+                         "from each network's seed on 2D L=64, N=410, 4096 walkers (flatness "
+                         "over [-778, 0])")
+    ap.add_argument("--full-range-seeds", type=int, default=4,
+                    help="walker seeds of that comparison")
     ap.add_argument("--train-steps-only", type=int, default=0,
                     help="only run this many training steps of the network on the 8192-row "
                          "test batch (a fixed workload for profiling the training kernels)")
@@ -225,6 +263,10 @@ def main(argv=None):
         with m.Mlp(mlp_initial_params(0)) as net:
             loss = net.train(X, t, steps=args.train_steps_only, lr=1e-3)
         print(json.dumps({"train_steps": args.train_steps_only, "rows": 8192, "loss": loss}))
+        return
+    if args.full_range_trainings:
+        full_range_trials(args.full_range_trainings, args.full_range_seeds, args.train_steps,
+                          lambda r: print(json.dumps(r), flush=True))
         return
     t0 = time.perf_counter()
     small = small_training_systems(args.frac)
