@@ -63,16 +63,16 @@ def alg_ops_per_attempt(d: int) -> int:
 # walkers on 152 SMs) the persistent launch runs the same blocks.
 TRAFFIC_MEASURED = {
     # one full 1000-sweep launch (profiles/walker_update_field_2d-L64-N410-w4096.md)
-    "2d-L64-N410-w4096": {"bytes": 33.968e6 + 798.450e6, "kernel_sha": "432338d4ad2ed795",
+    "2d-L64-N410-w4096": {"bytes": 34.239e6 + 802.815e6, "kernel_sha": "4f112a9b4d61e7f4",
                           "launch": {"kernel": 2, "lanes_per_walker": 8, "walkers_per_block": 28,
                                      "thr_window": 0, "multi_commit": 0}},
     # one full 200-sweep launch (profiles/walker_update_group_batched-27-systems-w16384.md)
     # (and the multi-commit shape the autotuner also picks there, by under 1 %)
     "batched-27-systems-w16384": [
-        {"bytes": 704.796e9 + 300.201e9, "kernel_sha": "432338d4ad2ed795",
+        {"bytes": 704.779e9 + 300.284e9, "kernel_sha": "4f112a9b4d61e7f4",
          "launch": {"kernel": 1, "lanes_per_walker": 16, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 0}},
-        {"bytes": 761.578e9 + 317.775e9, "kernel_sha": "432338d4ad2ed795",
+        {"bytes": 761.331e9 + 317.758e9, "kernel_sha": "4f112a9b4d61e7f4",
          "launch": {"kernel": 1, "lanes_per_walker": 8, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 1}},
     ],
@@ -80,10 +80,10 @@ TRAFFIC_MEASURED = {
     # writes grow with the attempts; profiles/walker_update_group_3d-L32-N3277-w8192.md),
     # with multi-commit rounds and with one commit per round
     "3d-L32-N3277-w8192": [
-        {"bytes": 40 * (18.5963e9 + 7.0703e9), "kernel_sha": "432338d4ad2ed795",
+        {"bytes": 40 * (18.5970e9 + 7.0710e9), "kernel_sha": "4f112a9b4d61e7f4",
          "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 1}},
-        {"bytes": 40 * (18.4748e9 + 7.0511e9), "kernel_sha": "432338d4ad2ed795",
+        {"bytes": 40 * (18.4596e9 + 7.0481e9), "kernel_sha": "4f112a9b4d61e7f4",
          "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 0}},
     ],
@@ -97,7 +97,7 @@ INSTR_MEASURED = {
     # the full 1000-sweep launch of the traffic record
     "2d-L64-N410-w4096": {"warp_inst_per_attempt": 4.0031106e10 / 1.67936e9,
                           "thread_inst_per_attempt": 1.0419877e12 / 1.67936e9,
-                          "kernel_sha": "432338d4ad2ed795",
+                          "kernel_sha": "4f112a9b4d61e7f4",
                           "launch": {"kernel": 2, "lanes_per_walker": 8, "thr_window": 0,
                                      "multi_commit": 0}},
     # 2-sweep launch, same shape as the traffic record (instructions per attempt do not
@@ -105,24 +105,24 @@ INSTR_MEASURED = {
     "batched-27-systems-w16384": [
         {"warp_inst_per_attempt": 4.215209e9 / 72.3314e6,
          "thread_inst_per_attempt": 1.21995e11 / 72.3314e6,
-         "kernel_sha": "432338d4ad2ed795", "any_sweeps": True,
+         "kernel_sha": "4f112a9b4d61e7f4", "any_sweeps": True,
          "launch": {"kernel": 1, "lanes_per_walker": 16, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 0}},
         {"warp_inst_per_attempt": 3.788915e9 / 72.3314e6,
          "thread_inst_per_attempt": 1.0942e11 / 72.3314e6,
-         "kernel_sha": "432338d4ad2ed795", "any_sweeps": True,
+         "kernel_sha": "4f112a9b4d61e7f4", "any_sweeps": True,
          "launch": {"kernel": 1, "lanes_per_walker": 8, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 1}},
     ],
     "3d-L32-N3277-w8192": [
         {"warp_inst_per_attempt": 4.781667e9 / 134.2259e6,
          "thread_inst_per_attempt": 1.426715e11 / 134.2259e6,
-         "kernel_sha": "432338d4ad2ed795", "any_sweeps": True,
+         "kernel_sha": "4f112a9b4d61e7f4", "any_sweeps": True,
          "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 1}},
         {"warp_inst_per_attempt": 2.974781e9 / 134.2259e6,
          "thread_inst_per_attempt": 8.90372e10 / 134.2259e6,
-         "kernel_sha": "432338d4ad2ed795", "any_sweeps": True,
+         "kernel_sha": "4f112a9b4d61e7f4", "any_sweeps": True,
          "launch": {"kernel": 1, "lanes_per_walker": 4, "bits_in_smem": 1, "thr_window": 0,
                     "multi_commit": 0}},
     ],

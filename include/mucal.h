@@ -574,7 +574,10 @@ int mucal_mlp_forward_tcgen05(void *mlp, const float *X, int64_t B, float *y);
  * mucal_mlp_train: enable = 1 runs every 128x128 contraction (Z2 = H1 W2^T,
  * dH1 = dZ2 W2 and dW2 = dZ2^T H1 over each 128-row tile) with tcgen05.mma
  * on tensor memory (the default); 0 uses mma.sync.  The numerics are the
- * same (bf16 operands, fp32 accumulation) up to the order of fp32 sums. */
+ * same (bf16 operands, fp32 accumulation) up to the order of fp32 sums.
+ * The tensor-core path sums the gradients of its 128-row tiles in tile order
+ * (run to run the same bits); the mma.sync path adds them with atomics, in
+ * whatever order its blocks finish. */
 int mucal_mlp_use_tcgen05(void *mlp, int32_t enable);
 
 /* One forward and backward pass of the mean squared error against t[B]:

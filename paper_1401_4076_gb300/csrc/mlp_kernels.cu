@@ -425,6 +425,8 @@ struct Mlp {
     float *X = nullptr, *t = nullptr, *y = nullptr;
     __nv_bfloat16 *h1T = nullptr, *dz2T = nullptr;
     int *d_err = nullptr;      // error flag of the tcgen05 kernels
+    float *part = nullptr;     // per-CTA gradient rows of the tcgen05 training kernel
+    size_t part_floats = 0;
     bool use_tc = true;        // forward, gradients and training on tcgen05 (else mma.sync)
     int64_t step = 0;
     std::string err;
@@ -511,8 +513,17 @@ int enqueue_grad(Mlp *m, int64_t B)
     if (m->use_tc) {
         int rc = ensure_err(m);
         if (rc != MUCAL_OK) return rc;
-        MLP_TRY(m, mucal::mlp_train_tcgen05(m->wq, m->X, m->t, B, m->grad, m->loss, m->d_err,
-                                            m->stream));
+        const size_t need = mucal::mlp_train_tcgen05_partial_floats(B);
+        if (need > m->part_floats) {
+            MLP_TRY(m, cudaStreamSynchronize(m->stream));
+            cudaFree(m->part);
+            m->part = nullptr;
+            m->part_floats = 0;
+            MLP_TRY(m, cudaMalloc(&m->part, need * sizeof(float)));
+            m->part_floats = need;
+        }
+        MLP_TRY(m, mucal::mlp_train_tcgen05(m->wq, m->X, m->t, B, m->part, m->grad, m->loss,
+                                            m->d_err, m->stream));
         return MUCAL_OK;
     }
     mlp_rows_kernel<true><<<blocks, WARPS * 32, rows_smem(), m->stream>>>(
@@ -592,7 +603,7 @@ void mucal_mlp_destroy(void *mlp)
     cudaStreamSynchronize(m->stream);
     cudaFree(m->w); cudaFree(m->grad); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->wq);
     cudaFree(m->loss); cudaFree(m->X); cudaFree(m->t); cudaFree(m->y); cudaFree(m->h1T);
-    cudaFree(m->dz2T);
+    cudaFree(m->dz2T); cudaFree(m->part);
     cudaFree(m->d_err);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;

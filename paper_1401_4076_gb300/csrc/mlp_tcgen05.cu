@@ -268,13 +268,19 @@ constexpr int TR_NRED = TC_H * 4 + TC_H + TC_H + TC_H + 2;     // dW1, db1, db2,
 constexpr uint32_t TR_BAR = TR_RED + ((TR_NRED * 4 + 15) / 16) * 16;
 constexpr uint32_t TR_YP = TR_BAR + 16;        // partial outputs of the two column halves
 constexpr uint32_t TR_X = TR_YP + 2 * TC_ROWS * 4;   // x of the CTA's rows, [128][4]
-constexpr uint32_t TR_TOTAL = TR_X + TC_ROWS * 4 * 4;
+constexpr uint32_t TR_WS = TR_X + TC_ROWS * 4 * 4;   // loss and db3 of warps 0-3
+constexpr uint32_t TR_TOTAL = TR_WS + 8 * 4;
+// Each CTA writes its gradients (and, last, its loss) as one row of a
+// partial buffer; a second kernel sums the rows in CTA order, so that the
+// gradients do not depend on the order in which CTAs finish.
+constexpr int TC_NPARAM = TC_OFF_B3 + 1;
+constexpr int TC_PSTRIDE = ((TC_NPARAM + 1 + 3) / 4) * 4;
 constexpr uint32_t TR_COLS = 512;
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
 mlp_train_tc_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restrict__ X,
                     const float *__restrict__ target, int64_t B, float inv_b,
-                    float *__restrict__ grad, float *__restrict__ loss_out, int *err)
+                    float *__restrict__ part, int *err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -284,7 +290,7 @@ mlp_train_tc_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restric
     float *s_b3 = s_w3 + TC_H;
     float *red = reinterpret_cast<float *>(smem + TR_RED);
     float *r_w1 = red, *r_b1 = red + TC_H * 4, *r_b2 = r_b1 + TC_H, *r_w3 = r_b2 + TC_H;
-    float *r_b3 = r_w3 + TC_H, *r_loss = r_b3 + 1;
+    float *ws = reinterpret_cast<float *>(smem + TR_WS);
     const uint32_t bar = sbase + TR_BAR;
     const uint32_t tmem_slot = sbase + TR_BAR + 8;
     uint32_t *tmem_slot_ptr = reinterpret_cast<uint32_t *>(smem + TR_BAR + 8);
@@ -306,6 +312,7 @@ mlp_train_tc_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restric
     }
     if (tid == 0) *s_b3 = __bfloat162float(wq[TC_OFF_B3]);
     for (int i = tid; i < TR_NRED; i += TC_THREADS) red[i] = 0.f;
+    if (tid < 8) ws[tid] = 0.f;
     // W2 [out][in] and W2^T [in][out], 16-byte chunks of 8 consecutive k
     for (int c = tid; c < TC_H * TC_H / 8; c += TC_THREADS) {
         const int n = c >> 4, kg = c & 15;
@@ -399,9 +406,9 @@ mlp_train_tc_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restric
         dy_row = dy;
         if (half == 0) {
             const float l = warp_sum(e * e * inv_b), sdy = warp_sum(dy);
-            if (lane == 0) {
-                atomicAdd(r_loss, l);
-                atomicAdd(r_b3, sdy);
+            if (lane == 0) {       // warps 0-3; summed in warp order at the end
+                ws[warp] = l;
+                ws[4 + warp] = sdy;
             }
         }
         // pass 2: dz2 = dy w3 gelu'(z2) in bf16 as dZ2 and dZ2^T for the tensor cores
@@ -476,6 +483,7 @@ mlp_train_tc_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restric
         __syncthreads();
         float a = 0.f;
         for (int r = ch * 64; r < ch * 64 + 64; ++r) a += s_at(r, cn);
+        // two addends (the two row halves) onto zero: the same sum in either order
         atomicAdd((q == 0 ? r_b2 : r_w3) + cn, a);
         __syncthreads();
     }
@@ -517,13 +525,15 @@ mlp_train_tc_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restric
         atomicAdd(r_w1 + cn * 4 + 3, g3);
         atomicAdd(r_b1 + cn, gb);
         // this CTA's share of dW2: TMEM lane = out, column = in
+        float *prow = part + (size_t)blockIdx.x * TC_PSTRIDE;
 #pragma unroll 1
         for (int cb = half * 2; cb < half * 2 + 2; ++cb) {
             float v[32];
             tmem_ld32(tmem + lane_base + 256u + (uint32_t)(cb * 32), v);
             const int out = (warp & 3) * 32 + lane;
+            float4 *dst = reinterpret_cast<float4 *>(prow + TC_OFF_W2 + out * TC_H + cb * 32);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) atomicAdd(grad + TC_OFF_W2 + out * TC_H + cb * 32 + i, v[i]);
+            for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
     } else if (tid == 0) {
         atomicExch(err, 1);
@@ -531,19 +541,33 @@ mlp_train_tc_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restric
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (ok) {
-        for (int i = tid; i < TC_H * 4; i += TC_THREADS) atomicAdd(grad + TC_OFF_W1 + i, r_w1[i]);
+        float *prow = part + (size_t)blockIdx.x * TC_PSTRIDE;
+        for (int i = tid; i < TC_H * 4; i += TC_THREADS) prow[TC_OFF_W1 + i] = r_w1[i];
         for (int i = tid; i < TC_H; i += TC_THREADS) {
-            atomicAdd(grad + TC_OFF_B1 + i, r_b1[i]);
-            atomicAdd(grad + TC_OFF_B2 + i, r_b2[i]);
-            atomicAdd(grad + TC_OFF_W3 + i, r_w3[i]);
+            prow[TC_OFF_B1 + i] = r_b1[i];
+            prow[TC_OFF_B2 + i] = r_b2[i];
+            prow[TC_OFF_W3 + i] = r_w3[i];
         }
         if (tid == 0) {
-            atomicAdd(grad + TC_OFF_B3, *r_b3);
-            atomicAdd(loss_out, *r_loss);
+            prow[TC_OFF_B3] = ((ws[4] + ws[5]) + ws[6]) + ws[7];
+            prow[TC_NPARAM] = ((ws[0] + ws[1]) + ws[2]) + ws[3];
         }
     }
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TR_COLS));
+}
+
+// grad[i] (and, for i = TC_NPARAM, the loss) = the sum of the CTAs' rows in
+// CTA order.
+__global__ void mlp_tc_grad_reduce_kernel(const float *__restrict__ part, int n_cta,
+                                          float *__restrict__ grad, float *__restrict__ loss_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > TC_NPARAM) return;
+    float s = 0.f;
+    for (int b = 0; b < n_cta; ++b) s += part[(size_t)b * TC_PSTRIDE + i];
+    if (i < TC_NPARAM) grad[i] = s;
+    else *loss_out = s;
 }
 
 }  // namespace
@@ -565,8 +589,13 @@ cudaError_t mlp_forward_tcgen05(const void *wq, const float *X, float *y, int64_
 
 namespace mucal {
 
+size_t mlp_train_tcgen05_partial_floats(int64_t B)
+{
+    return (size_t)((B + TC_ROWS - 1) / TC_ROWS) * TC_PSTRIDE;
+}
+
 cudaError_t mlp_train_tcgen05(const void *wq, const float *X, const float *target, int64_t B,
-                              float *grad, float *loss, int *err, cudaStream_t stream)
+                              float *part, float *grad, float *loss, int *err, cudaStream_t stream)
 {
     static_assert(TR_TOTAL <= 227 * 1024, "shared memory");
     cudaError_t e = cudaFuncSetAttribute(mlp_train_tc_kernel,
@@ -574,7 +603,10 @@ cudaError_t mlp_train_tcgen05(const void *wq, const float *X, const float *targe
     if (e != cudaSuccess) return e;
     const int blocks = (int)((B + TC_ROWS - 1) / TC_ROWS);
     mlp_train_tc_kernel<<<blocks, TC_THREADS, TR_TOTAL, stream>>>(
-        static_cast<const __nv_bfloat16 *>(wq), X, target, B, 1.0f / (float)B, grad, loss, err);
+        static_cast<const __nv_bfloat16 *>(wq), X, target, B, 1.0f / (float)B, part, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mlp_tc_grad_reduce_kernel<<<(TC_NPARAM + 1 + 255) / 256, 256, 0, stream>>>(part, blocks, grad, loss);
     return cudaGetLastError();
 }
 

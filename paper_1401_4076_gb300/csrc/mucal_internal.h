@@ -144,10 +144,13 @@ cudaError_t launch_droplets(const SysParams &p, const DropletOut &o, const Dropl
 // non-zero if a tensor-core wait ran out.
 cudaError_t mlp_forward_tcgen05(const void *wq, const float *X, float *y, int64_t B, int *err,
                                 cudaStream_t stream);
-// Gradients of the mean squared error against target[B] added to grad
-// (fp32[17281]) and the loss added to *loss, every contraction on tcgen05.
+// Gradients of the mean squared error against target[B] written to grad
+// (fp32[17281]) and the loss to *loss, every contraction on tcgen05.  part
+// holds mlp_train_tcgen05_partial_floats(B) floats: one row per CTA, summed
+// in CTA order, so the result does not depend on the CTAs' finishing order.
+size_t mlp_train_tcgen05_partial_floats(int64_t B);
 cudaError_t mlp_train_tcgen05(const void *wq, const float *X, const float *target, int64_t B,
-                              float *grad, float *loss, int *err, cudaStream_t stream);
+                              float *part, float *grad, float *loss, int *err, cudaStream_t stream);
 
 // Error message of calls that have no context (mucal_host.cu).
 void set_init_error(const char *msg);

@@ -790,8 +790,9 @@ __device__ __forceinline__ void chain_rounds(const SysParams &p, int w, bool act
 // no tunnelling bookkeeping.  A step issues more instructions than a
 // one-commit round (the neighbourhood test alone is 8d compares), so the
 // rounds pay off only where a round's loads are long: measured on GB300,
-// 3D L = 32 at 4 lanes with thresholds in L2 +2.4 %, the field kernel and
-// 16 lanes slower; the autotuner chooses per workload.
+// 3D L = 32 at 4 lanes with thresholds in L2 +10 % (with the list entries
+// read through L2 only), the field kernel and 16 lanes slower; the
+// autotuner chooses per workload.
 // ---------------------------------------------------------------------------
 template <int D, typename IdxT, int G, int TM, typename View>
 __device__ __forceinline__ void chain_rounds_mc(const SysParams &p, int w, bool active, View v,

@@ -82,3 +82,22 @@ def test_tcgen05_training_lowers_the_loss_like_mma():
     for tc, (first, last) in losses.items():
         assert last < 0.5 * first, (tc, first, last)
     assert losses[True][1] == pytest.approx(losses[False][1], rel=0.2)
+
+
+@pytest.mark.parametrize("B", [300, 8192])
+def test_tcgen05_training_is_deterministic(B):
+    """Each CTA writes its gradient row and the rows are summed in CTA order,
+    so two trainings from the same parameters on the same rows give the same
+    parameters to the bit (and so the same seeded weights)."""
+    params = workloads.mlp_initial_params(11)
+    X, t = workloads.mlp_test_batch(B, 12)
+    out = []
+    for _ in range(2):
+        with m.Mlp(params) as net:
+            loss = net.train(X, t, steps=300, lr=2e-3)
+            g_loss, g = net.gradients(X, t)
+            out.append((loss, net.params(), g_loss, g))
+    (l0, p0, gl0, g0), (l1, p1, gl1, g1) = out
+    assert l0 == l1 and gl0 == gl1
+    np.testing.assert_array_equal(p0, p1)
+    np.testing.assert_array_equal(g0, g1)
