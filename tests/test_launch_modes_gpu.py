@@ -20,6 +20,8 @@ THREADP = dict(kernel=m.MUCAL_KERNEL_THREAD, lanes_per_walker=1, walkers_per_blo
                bits_in_smem=0, persistent=1)
 GROUP8 = dict(GROUP8P, persistent=0)
 FIELD8P = dict(GROUP8P, kernel=m.MUCAL_KERNEL_FIELD)
+GROUP8MC = dict(GROUP8, multi_commit=1)
+FIELD8PMC = dict(FIELD8P, multi_commit=1)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,9 +35,11 @@ def _built():
 
 
 @pytest.mark.parametrize("launch,graph", [(GROUP8P, False), (GROUP8P, True), (THREADP, True),
-                                          (GROUP8, True), (FIELD8P, False), (FIELD8P, True)],
+                                          (GROUP8, True), (FIELD8P, False), (FIELD8P, True),
+                                          (GROUP8MC, True), (FIELD8PMC, True)],
                          ids=["G8-persistent", "G8-persistent-graph", "thread-persistent-graph",
-                              "G8-graph", "field-G8-persistent", "field-G8-persistent-graph"])
+                              "G8-graph", "field-G8-persistent", "field-G8-persistent-graph",
+                              "G8-multi-commit-graph", "field-G8-persistent-multi-commit-graph"])
 def test_small_2d_iterations_bit_exact(launch, graph):
     """2D L=16, N=32, 64 walkers (16 blocks of 4 walkers, or 10 blocks of 7
     for the thread kernel), 6 iterations of 500 sweeps with the recursion."""
@@ -64,9 +68,9 @@ def test_small_2d_iterations_bit_exact(launch, graph):
 
 
 def test_graph_recaptures_on_changes():
-    """Graph mode across a change of sweeps, of launch shape and of the
-    kernel flavour (tunnelling switched on): every iteration still equals the
-    oracle."""
+    """Graph mode across a change of sweeps, of launch shape, of the rounds
+    (multi-commit on and off) and of the kernel flavour (tunnelling switched
+    on): every iteration still equals the oracle."""
     desc = (3, 6, 40, 21, 0, 0, 40)
     d, L, N, W, lo, hi, seed = desc
     nb = d * N + 1
@@ -75,14 +79,14 @@ def test_graph_recaptures_on_changes():
     S, occ, E = chain.init_walkers(d, L, N, W, seed)
     st = np.zeros(W, np.uint8)
     cnt = np.zeros(W, np.int64)
-    plan = [(20, GROUP8, False), (20, GROUP8, False), (35, GROUP8, False), (35, GROUP8P, False),
-            (35, GROUP8P, True), (10, THREADP, True)]
+    plan = [(20, GROUP8, False), (20, GROUP8, False), (35, GROUP8, False), (35, GROUP8MC, False),
+            (35, GROUP8, False), (35, GROUP8P, False), (35, GROUP8P, True), (10, THREADP, True)]
     with m.Mucal([desc], per_walker_hist=True) as mc:
         mc.set_weights(0, lnW)
         mc.set_graph_mode(True)
         for it, (sweeps, launch, tun) in enumerate(plan):
             mc.set_launch(**launch)
-            if tun and it == 4:
+            if tun and it == 6:
                 mc.set_tunnel_window(0, -60, -20)
             mc.run_iteration(sweeps, it)
             if tun:

@@ -274,7 +274,13 @@ def test_large_3d_first_iteration_sampled(launch):
 
 # ------------------------------------- production mode (per-block rows) -----
 
-@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP8, GROUP32, FIELD8], ids=_lid)
+def _lid_mc(c):
+    return _lid(c) + ("-mc" if c.get("multi_commit") else "")
+
+
+@pytest.mark.parametrize("launch", [LAUNCHES[0], LAUNCHES[3], GROUP8, GROUP32, FIELD8,
+                                    dict(GROUP8, multi_commit=1), dict(FIELD8, multi_commit=1),
+                                    dict(LAUNCHES[3], multi_commit=1)], ids=_lid_mc)
 def test_production_histogram_equals_oracle_sum(launch):
     """Without per-walker histograms the rows are per block; H must still be the
     exact sum of every walker's histogram (Eq. 2)."""
