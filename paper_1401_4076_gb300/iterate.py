@@ -194,7 +194,7 @@ def iterate_staged(desc, lnW0=None, range_sweeps: int = 1000, sweeps: int = 4000
                    discard: int = 1000, max_iter: int = 200, stable: int = 5, goal: float = 0.5,
                    target=None, scheme=m.MUCAL_SCHEME_SIMPLE | m.MUCAL_SCHEME_EXTRAPOLATE,
                    relax_max: int = 10, cuda_stream=None, launch=None,
-                   seed_range_stage: bool = False) -> StagedResult:
+                   seed_range_stage: bool = False, progress=None) -> StagedResult:
     """The iteration of Sec. 2 in two stages for one system.
 
     Stage 1 (from lnW = 0): short iterations of `range_sweeps` with the simple
@@ -212,7 +212,10 @@ def iterate_staged(desc, lnW0=None, range_sweeps: int = 1000, sweeps: int = 4000
     fixed weights: the discard lets the walkers follow the last update),
     updated with `scheme`, until the flatness over the target window (default:
     the sampled range) reaches `goal`.  Tunnelling events over the sampled
-    range (Sec. 4's criterion) are counted during stage 2."""
+    range (Sec. 4's criterion) are counted during stage 2.  `progress`, if
+    given, is called after every stage-2 iteration with a dict (iteration,
+    flatness, tunnelling events so far, wall time), so that a run cut short
+    still leaves its trajectory."""
     d, L, N, W, lo, hi, seed = desc
     t0 = time.perf_counter()
     it_no = 0
@@ -297,6 +300,10 @@ def iterate_staged(desc, lnW0=None, range_sweeps: int = 1000, sweeps: int = 4000
             total_sweeps += sweeps
             _, f = mc.update_weights(0, scheme)
             flat.append(f)
+            if progress is not None:
+                progress({"iteration": n1 + n2, "stage2_iteration": n2, "flatness": f,
+                          "tunnel_events_stage2": int(mc.tunnel_counts(0)[0]),
+                          "wall_s": round(time.perf_counter() - t0, 3)})
             if f >= goal:
                 converged = True
                 break
@@ -332,6 +339,8 @@ def main(argv=None):
                          "measured after --discard discarded sweeps per iteration")
     ap.add_argument("--range-sweeps", type=int, default=1000)
     ap.add_argument("--discard", type=int, default=1000)
+    ap.add_argument("--progress", type=int, default=0,
+                    help="with --staged: print a JSON line every this many stage-2 iterations")
     args = ap.parse_args(argv)
     d, L, N, W = (int(x) for x in args.system.split(":"))
     lo, hi = (int(x) for x in args.window.split(":"))
@@ -351,9 +360,14 @@ def main(argv=None):
     for k in range(args.seeds):
         desc = (d, L, N, W, lo, hi, args.seed + k * W)
         if args.staged:
+            def report(p, k=k):
+                if p["stage2_iteration"] % args.progress == 0:
+                    print(json.dumps(dict(p, run=k, flatness=round(p["flatness"], 4))), flush=True)
+
             r = iterate_staged(desc, range_sweeps=args.range_sweeps, sweeps=args.sweeps,
                                discard=args.discard, max_iter=args.max_iter,
-                               target=target[0] if target else None, scheme=scheme)
+                               target=target[0] if target else None, scheme=scheme,
+                               progress=report if args.progress > 0 else None)
             row = {"system": {"d": d, "L": L, "N": N, "walkers": W, "seed_base": desc[-1]},
                    "target": target[0] if target else "sampled range", "tempering": temper,
                    "scheme": args.scheme + (" + edge continuation" if args.extrapolate else ""),
