@@ -76,3 +76,25 @@ def test_records_per_round_mode():
         got = bench._measured_traffic(name, True, dict(base, multi_commit=mc))
         assert got == (rec["bytes"] if current else None)
     assert bench._measured_traffic(name, True, dict(base, multi_commit=1, thr_window=1)) is None
+
+
+def test_reference_arm_line(capsys):
+    """`--impl reference` on rank 0: one JSON line timing the oracle on a
+    bounded sample of the workload, with the keys the line must carry."""
+    import json
+    from paper_1401_4076_gb300 import workloads
+
+    class A:
+        steps, warmup, gpus, sweeps = 1, 1, 1, 0
+
+    wl = workloads.batched_uneven(total_walkers=256)
+    assert bench.run_reference(A, wl, 1, 0) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["unit"] == "attempts/s" and line["higher_is_better"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert "walkers" in cb["sample"] and "sweeps" in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "attempts/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == wl.name
