@@ -154,3 +154,41 @@ def test_rounds_reproduce_the_serial_chain(d, L, N, G, slope, noise, batches, se
         # several moves committed in one round somewhere in the run, or
         # never where every commit invalidates the later lanes
         assert (multi > 0) == several
+
+
+@pytest.mark.parametrize("d,L,N,G", [(2, 5, 6, 8), (2, 6, 30, 16), (3, 4, 40, 32), (2, 4, 15, 4)])
+def test_moved_slots_found_by_index_or_by_site(d, L, N, G):
+    """A commit moves list slots k_f (particle) and N + m_f (empty site).  A
+    later lane of the batch holds the entries it read, patched by earlier
+    commits; its slot is one the commit moved exactly when its site is the
+    committed one (every site sits in exactly one slot), so the kernels may
+    find such lanes either way."""
+    rng = np.random.default_rng(7 * d + L + N + G)
+    V = L ** d
+    S0, occ0, E0 = chain.init_walkers(d, L, N, 1, 5 + N)
+    S, occ = S0[0].copy(), occ0[0].copy()
+    holes = V - N
+    checked = 0
+    for _ in range(200):
+        att = [(int(rng.integers(N)), int(rng.integers(holes))) for _ in range(G)]
+        a = [int(S[k]) for k, _ in att]
+        b = [int(S[N + m]) for _, m in att]
+        for f in range(G):
+            if rng.random() < 0.3:
+                continue                          # this attempt is rejected
+            kf, mf = att[f]
+            af, bf = a[f], b[f]
+            assert S[kf] == af and S[N + mf] == bf
+            occ[af], occ[bf] = 0, 1
+            S[kf], S[N + mf] = bf, af
+            for j in range(f + 1, G):
+                kj, mj = att[j]
+                assert (kj == kf) == (a[j] == af)
+                assert (mj == mf) == (b[j] == bf)
+                checked += 1
+                if kj == kf:
+                    a[j] = bf
+                if mj == mf:
+                    b[j] = af
+                assert a[j] == S[kj] and b[j] == S[N + mj]
+    assert checked > 0
