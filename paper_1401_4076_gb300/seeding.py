@@ -201,9 +201,11 @@ def full_range_trials(trainings: int, seeds: int, train_steps: int, log):
     """The plain start against the learned seed on 2D L=64, N=410, 4096
     walkers over its whole sampled range (two-stage iteration, flatness
     over [-778, 0]), with the network trained `trainings` times on the same
-    rows: the training sums gradients with float atomics, so each training
-    gives a slightly different network.  The plain runs are the same for
-    every training (the chain is deterministic) and run once per seed."""
+    rows.  On the tensor cores (the default) the training's sums run in a
+    fixed order, so every training gives the same network and the repeats
+    check that; with the mma.sync path (atomic sums) they differ slightly.
+    The plain runs are the same for every training (the chain is
+    deterministic) and run once per seed."""
     from .iterate import iterate_staged
     scheme = m.MUCAL_SCHEME_SIMPLE | m.MUCAL_SCHEME_EXTRAPOLATE
     small = small_training_systems(1.0)
