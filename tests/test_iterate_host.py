@@ -127,3 +127,98 @@ def test_cli_progress_lines(fake, capsys):
     # the command line keeps stable = 5: ranges (4,6), (3,7), then (2,8) six times
     assert run["range_iterations"] == 8
     assert run["converged"] and run["iterations"] == 8 + 3 and lines[-1]["summary"]
+
+
+class FakeMulti:
+    """Several systems in one context; system i reports the flatness values
+    of its script, and histograms whose mean energy bin is scripted too."""
+
+    scripts = {}
+    means = {}
+
+    def __init__(self, systems, cuda_stream=None):
+        self.systems = systems
+        self.nb = 9
+        self.it = [0] * len(systems)
+        self.runs = []
+        self.updates = [0] * len(systems)
+        self.w = [np.zeros(self.nb) for _ in systems]
+        FakeMulti.last = self
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def set_launch(self, **kw):
+        pass
+
+    def set_weights(self, i, w):
+        self.w[i] = np.asarray(w, float).copy()
+
+    def weights(self, i):
+        return self.w[i].copy()
+
+    def set_target_window(self, i, lo, hi):
+        pass
+
+    def run_iteration(self, sweeps, it):
+        self.runs.append((sweeps, it))
+
+    def histogram(self, i):
+        k = len(self.runs)
+        c = FakeMulti.means.get(i, lambda k: 4)(k)
+        H = np.zeros(self.nb, dtype=np.int64)
+        H[c] = 10
+        return H
+
+    def update_weights(self, i, scheme):
+        s = FakeMulti.scripts[i]
+        f = s[min(self.updates[i], len(s) - 1)]
+        self.updates[i] += 1
+        return self.w[i], f
+
+
+@pytest.fixture
+def multi(monkeypatch):
+    monkeypatch.setattr(iterate.m, "Mucal", FakeMulti)
+    FakeMulti.scripts, FakeMulti.means = {}, {}
+    return FakeMulti
+
+
+def test_iterate_to_flat_per_system_convergence(multi):
+    multi.scripts = {0: [0.1, 0.6], 1: [0.1, 0.2, 0.3, 0.7]}
+    sysd = [(2, 8, 5, 4, 0, 0, 0), (2, 8, 6, 4, 0, 0, 4)]
+    res = iterate.iterate_to_flat(sysd, sweeps=10, max_iter=20, scheme=0, final_sweeps=30)
+    assert [r.converged for r in res] == [True, True]
+    assert [r.iterations for r in res] == [2, 4]
+    assert res[0].flatness == [0.1, 0.6] and res[1].flatness == [0.1, 0.2, 0.3, 0.7]
+    # a converged system keeps running with frozen weights (no more updates)
+    assert multi.last.updates == [2, 4]
+    # one launch per iteration for all systems, then the final run
+    assert [sw for sw, _ in multi.last.runs] == [10, 10, 10, 10, 30]
+    assert res[0].attempts == 2 * 10 * 5 * 4 and res[1].attempts == 4 * 10 * 6 * 4
+
+
+def test_iterate_to_flat_sweeps_double_on_stalls(multi):
+    multi.scripts = {0: [0.1] * 40}
+    res = iterate.iterate_to_flat([(2, 8, 5, 4, 0, 0, 0)], sweeps=10, max_iter=12, scheme=0,
+                                  sweeps_growth=4, stall=3)
+    sw = res[0].extra["sweeps"]
+    # best improves once (first value), then 3 stalled iterations double the sweeps,
+    # twice, up to 4 times the start
+    assert sw[0] == 10 and max(sw) == 40 and sorted(set(sw)) == [10, 20, 40]
+    assert not res[0].converged and res[0].iterations == 12
+
+
+def test_iterate_to_flat_relaxation_ends_when_the_mean_settles(multi):
+    multi.scripts = {0: [0.9]}
+    # mean energy bin 6, 5, 4, 4, ...: settles at the fourth iteration
+    multi.means = {0: lambda k: max(4, 7 - k)}
+    res = iterate.iterate_to_flat([(2, 8, 5, 4, 0, 0, 0)], sweeps=10, max_iter=20, scheme=0,
+                                  lnW0=[np.linspace(0, -1, 9)], relax_iters=10, relax_tol=0.05)
+    fl = res[0].flatness
+    n_relax = sum(1 for x in fl if x != x)
+    assert n_relax == 4 and fl[-1] == 0.9 and res[0].converged
+    assert res[0].iterations == n_relax + 1
